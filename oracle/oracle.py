@@ -1,0 +1,201 @@
+"""ctypes front end of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this module. It converts a workload description (``paper_2004_02276_gb300.inputs.Case``, or any
+object with the same attributes) into the oracle's own configuration struct and calls the C
+functions of ``strm_oracle.c``. Arrays are interior-only, SoA ``[5, nz, ny, nx]`` float64.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcCfg(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("y_map", ctypes.c_int), ("beta", ctypes.c_double), ("bc_y", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double), ("r_gas", ctypes.c_double),
+        ("visc_law", ctypes.c_int), ("mu_ref", ctypes.c_double), ("t_ref", ctypes.c_double),
+        ("visc_exp", ctypes.c_double), ("suth_s", ctypes.c_double),
+        ("t_wall", ctypes.c_double), ("forcing", ctypes.c_int),
+        ("L", ctypes.c_int), ("weno_mode", ctypes.c_int), ("theta_thr", ctypes.c_double),
+        ("weno_eps", ctypes.c_double), ("u0", ctypes.c_double), ("l0", ctypes.c_double),
+        ("convective", ctypes.c_int), ("viscous", ctypes.c_int),
+    ]
+
+
+WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
+VISC_LAWS = {"power": 0, "sutherland": 1}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        d, i = ctypes.c_double, ctypes.c_int
+        dp = P(d)
+        u8p = P(ctypes.c_ubyte)
+        cp = P(OrcCfg)
+        _lib.orc_rhs.argtypes = [cp, dp, dp]
+        _lib.orc_rk_step.argtypes = [cp, dp, d, d, dp]
+        _lib.orc_rk_stage_update.argtypes = [i, d, dp, dp, dp, ctypes.c_long]
+        _lib.orc_rk_stage_update.restype = None
+        _lib.orc_cfl_dt.argtypes = [cp, dp, d]
+        _lib.orc_cfl_dt.restype = d
+        _lib.orc_totals.argtypes = [cp, dp, dp]
+        _lib.orc_sensor.argtypes = [cp, dp, dp, dp, u8p, u8p, u8p]
+        _lib.orc_fill_ghosts.argtypes = [cp, dp, dp]
+        _lib.orc_metrics.argtypes = [cp, dp, dp, dp]
+        _lib.orc_metrics.restype = None
+        _lib.orc_eigvecs.argtypes = [i, d, d, d, d, d, dp, dp]
+        _lib.orc_eigvecs.restype = None
+        _lib.orc_weno5.argtypes = [dp, d]
+        _lib.orc_weno5.restype = d
+        _lib.orc_ghosts.restype = i
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+
+
+def make_cfg(case, **over) -> OrcCfg:
+    """Oracle configuration from a workload description; keyword overrides win."""
+    get = lambda k, dflt=None: over.get(k, getattr(case, k, dflt))
+    c = OrcCfg()
+    c.nx, c.ny, c.nz = get("nx"), get("ny"), get("nz")
+    c.lx, c.ly, c.lz = get("lx"), get("ly"), get("lz")
+    beta = get("beta", 0.0)
+    c.y_map = 1 if beta and beta > 0 else 0
+    c.beta = beta if beta else 0.0
+    c.bc_y = 1 if get("y_wall", True) else 0
+    c.gamma, c.prandtl = get("gamma"), get("prandtl")
+    c.r_gas = get("r_gas")
+    c.visc_law = VISC_LAWS[get("visc_law", "power")]
+    c.mu_ref, c.t_ref = get("mu_ref"), get("t_ref", 1.0)
+    c.visc_exp, c.suth_s = get("visc_exp", 0.76), get("suth_s", 0.0)
+    c.t_wall = get("t_wall", 1.0)
+    c.forcing = int(bool(get("forcing", False)))
+    c.L = get("L", 3)
+    wm = get("weno_mode", "sensor")
+    c.weno_mode = WENO_MODES[wm] if isinstance(wm, str) else int(wm)
+    c.theta_thr, c.weno_eps = get("theta_thr", 0.05), get("weno_eps", 1e-6)
+    c.u0, c.l0 = get("u0", 1.0), get("l0", 1.0)
+    c.convective = int(bool(get("convective", True)))
+    c.viscous = int(bool(get("viscous", True)))
+    return c
+
+
+def _state(cfg, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    assert w.shape == (5, cfg.nz, cfg.ny, cfg.nx), w.shape
+    return w
+
+
+def rhs(cfg, w):
+    w = _state(cfg, w)
+    r = np.empty_like(w)
+    if lib().orc_rhs(ctypes.byref(cfg), _dp(w), _dp(r)):
+        raise ValueError("orc_rhs: invalid configuration")
+    return r
+
+
+def rk_step(cfg, w, dt=0.0, cfl=0.8):
+    """One RK3 step; returns (new state, dt used)."""
+    w = _state(cfg, w).copy()
+    used = ctypes.c_double(0.0)
+    if lib().orc_rk_step(ctypes.byref(cfg), _dp(w), float(dt), float(cfl), ctypes.byref(used)):
+        raise ValueError("orc_rk_step: invalid configuration")
+    return w, used.value
+
+
+def advance(cfg, w, nsteps, dt=0.0, cfl=0.8):
+    """n RK3 steps; returns (state, elapsed time, list of dt)."""
+    t, dts = 0.0, []
+    for _ in range(nsteps):
+        w, h = rk_step(cfg, w, dt, cfl)
+        t += h
+        dts.append(h)
+    return w, t, dts
+
+
+def rk_stage_update(stage, dt, w, r_old, r):
+    w = np.ascontiguousarray(w, dtype=np.float64).copy()
+    r_old = np.ascontiguousarray(r_old, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    lib().orc_rk_stage_update(int(stage), float(dt), _dp(w), _dp(r_old), _dp(r), w.size)
+    return w
+
+
+def cfl_dt(cfg, w, cfl=0.8):
+    w = _state(cfg, w)
+    return lib().orc_cfl_dt(ctypes.byref(cfg), _dp(w), float(cfl))
+
+
+def totals(cfg, w):
+    w = _state(cfg, w)
+    out = np.zeros(5)
+    lib().orc_totals(ctypes.byref(cfg), _dp(w), _dp(out))
+    return out
+
+
+def sensor(cfg, w):
+    """Returns (theta, div, flags_x, flags_y, flags_z); see strm_oracle.h for flag layout."""
+    w = _state(cfg, w)
+    nx, ny, nz = cfg.nx, cfg.ny, cfg.nz
+    th = np.empty((nz, ny, nx))
+    dv = np.empty((nz, ny, nx))
+    fx = np.zeros((nz, ny, nx + 1), np.uint8)
+    fy = np.zeros((nz, ny + 1, nx), np.uint8)
+    fz = np.zeros((nz + 1, ny, nx), np.uint8)
+    if lib().orc_sensor(ctypes.byref(cfg), _dp(w), _dp(th), _dp(dv), _u8(fx), _u8(fy), _u8(fz)):
+        raise ValueError("orc_sensor: invalid configuration")
+    return th, dv, fx, fy, fz
+
+
+def fill_ghosts(cfg, w):
+    w = _state(cfg, w)
+    G = lib().orc_ghosts()
+    out = np.empty((5, cfg.nz + 2 * G, cfg.ny + 2 * G, cfg.nx + 2 * G))
+    lib().orc_fill_ghosts(ctypes.byref(cfg), _dp(w), _dp(out))
+    return out
+
+
+def ghosts():
+    return lib().orc_ghosts()
+
+
+def metrics(cfg):
+    y, ye, yee = np.empty(cfg.ny), np.empty(cfg.ny), np.empty(cfg.ny)
+    lib().orc_metrics(ctypes.byref(cfg), _dp(y), _dp(ye), _dp(yee))
+    return y, ye, yee
+
+
+def eigvecs(direction, gamma, u, v, w, H):
+    Lm, Rm = np.empty(25), np.empty(25)
+    lib().orc_eigvecs(int(direction), gamma, u, v, w, H, _dp(Lm), _dp(Rm))
+    return Lm.reshape(5, 5), Rm.reshape(5, 5)
+
+
+def weno5(f, eps=1e-6):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    assert f.size == 5
+    return lib().orc_weno5(_dp(f), float(eps))
+
+
+def threads():
+    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else all cores)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env else os.cpu_count()

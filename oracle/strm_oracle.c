@@ -1,0 +1,792 @@
+/*
+ * FP64 CPU oracle: right-hand side of the compressible Navier-Stokes equations and
+ * Wray's low-storage RK3, following STREAmS (arXiv 2004.02276) Section 2 step by step.
+ *
+ * TEST INFRASTRUCTURE ONLY: the reference the CUDA path is checked against. Only the
+ * tests, the smoke check and the benchmark's CPU baseline leg may load this library.
+ * It is compiled with -ffp-contract=off and without fast-math.
+ *
+ * Order of one right-hand-side evaluation (Section 2.1):
+ *   ghost fill of w  ->  primitives at every node  ->  Ducros sensor (Eq. sensor) at the
+ *   interior, ghost fill of theta and of the node divergence  ->  per direction: interface
+ *   flags, central energy-consistent flux (Eqs. avg_operator, encflux) or characteristic
+ *   Lax-Friedrichs WENO5 flux, wall interfaces, flux difference (Eq. num_flux)  ->  viscous
+ *   terms in Laplacian form (Section 2.1, last equation)  ->  mass-flow forcing (Eqs. 1b-c).
+ * Time integration: Eq. RK with alpha = (0, -17/60, -5/12), beta = (8/15, 5/12, 3/4).
+ *
+ * Readings taken where the paper is silent or garbled (each repeated at its use):
+ *   - RK alpha_1 is printed +17/60; only -17/60 is first-order consistent.
+ *   - The viscous formula's first sum is garbled; it is read as (D1 mu)(D1 u) + mu (D2 u).
+ *   - The sensor's u_0^2/L_0 is read as (u_0/L_0)^2 (dimensionally required).
+ *   - Pressure enters the momentum flux through the same conservative central form.
+ *   - WENO is used at interface i+1/2 iff max theta over nodes i-L+1..i+L exceeds the threshold.
+ *   - Staggered isothermal wall: mirrored ghosts, zero convective flux of mass, x/z momentum
+ *     and energy through the wall interface.
+ *   - Forcing is applied at every RK stage; the CFL step uses the convective limit only.
+ */
+#include "strm_oracle.h"
+
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define G 3 /* ghost layers: enough for L <= 3 and for the six-node WENO5 stencil */
+
+typedef struct {
+  const orc_cfg* c;
+  int nx, ny, nz;
+  ptrdiff_t nxg, nyg, nzg, ng;
+  ptrdiff_t sx, sy, sz; /* strides along x, y, z in ghosted arrays */
+  double dx, deta, dz;
+  double* y;
+  double* yeta;
+  double* yetaeta;
+  double cv, cp;
+  double a[4], b[4]; /* central first- and second-derivative coefficients, index 1..L */
+} grid_t;
+
+typedef struct {
+  double *rho, *u, *v, *w, *p, *T, *H, *c, *mu;
+} prims_t;
+
+int orc_ghosts(void) { return G; }
+
+static ptrdiff_t gidx(const grid_t* g, int i, int j, int k) {
+  return ((ptrdiff_t)(k + G) * g->nyg + (ptrdiff_t)(j + G)) * g->nxg + (ptrdiff_t)(i + G);
+}
+
+static ptrdiff_t iidx(const grid_t* g, int i, int j, int k) {
+  return ((ptrdiff_t)k * g->ny + j) * g->nx + i;
+}
+
+static int wrap(int i, int n) { return ((i % n) + n) % n; }
+
+/* Standard central coefficients of order 2L (Section 2.1): first derivative a_l and second
+ * derivative b_l, with f'' ~ sum_l b_l (f_{i+l} - 2 f_i + f_{i-l}) / dx^2. */
+static int central_coeffs(int L, double* a, double* b) {
+  memset(a, 0, 4 * sizeof(double));
+  memset(b, 0, 4 * sizeof(double));
+  if (L == 3) {
+    a[1] = 3.0 / 4.0; a[2] = -3.0 / 20.0; a[3] = 1.0 / 60.0;
+    b[1] = 3.0 / 2.0; b[2] = -3.0 / 20.0; b[3] = 1.0 / 90.0;
+    return 0;
+  }
+  if (L == 2) {
+    a[1] = 2.0 / 3.0; a[2] = -1.0 / 12.0;
+    b[1] = 4.0 / 3.0; b[2] = -1.0 / 12.0;
+    return 0;
+  }
+  return -1;
+}
+
+/* Wall-normal mapping y(eta), eta in [0,1], nodes at eta_j = (j+1/2)/ny (staggered: the
+ * walls eta = 0, 1 are interfaces). Tanh clustering toward both walls, y in [-ly/2, ly/2]. */
+void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
+  for (int j = 0; j < c->ny; ++j) {
+    double eta = (j + 0.5) / c->ny;
+    if (c->y_map == ORC_MAP_TANH) {
+      double s = c->beta * (2.0 * eta - 1.0);
+      double A = 0.5 * c->ly / tanh(c->beta);
+      double th = tanh(s);
+      double sech2 = 1.0 - th * th;
+      y[j] = A * th;
+      yeta[j] = 2.0 * c->beta * A * sech2;
+      yetaeta[j] = -8.0 * c->beta * c->beta * A * sech2 * th;
+    } else {
+      y[j] = c->ly * (eta - 0.5);
+      yeta[j] = c->ly;
+      yetaeta[j] = 0.0;
+    }
+  }
+}
+
+static int grid_init(grid_t* g, const orc_cfg* c) {
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return -1;
+  if (c->bc_y == ORC_BC_WALL && c->ny < G) return -1;
+  g->c = c;
+  g->nx = c->nx; g->ny = c->ny; g->nz = c->nz;
+  g->nxg = c->nx + 2 * G; g->nyg = c->ny + 2 * G; g->nzg = c->nz + 2 * G;
+  g->ng = g->nxg * g->nyg * g->nzg;
+  g->sx = 1; g->sy = g->nxg; g->sz = g->nxg * g->nyg;
+  g->dx = c->lx / c->nx;
+  g->deta = 1.0 / c->ny;
+  g->dz = c->lz / c->nz;
+  g->cv = c->r_gas / (c->gamma - 1.0);
+  g->cp = c->gamma * c->r_gas / (c->gamma - 1.0);
+  if (central_coeffs(c->L, g->a, g->b)) return -1;
+  g->y = malloc(sizeof(double) * c->ny);
+  g->yeta = malloc(sizeof(double) * c->ny);
+  g->yetaeta = malloc(sizeof(double) * c->ny);
+  orc_metrics(c, g->y, g->yeta, g->yetaeta);
+  return 0;
+}
+
+static void grid_free(grid_t* g) {
+  free(g->y); free(g->yeta); free(g->yetaeta);
+}
+
+static double* alloc_nan(ptrdiff_t n) {
+  double* p = malloc(sizeof(double) * (size_t)n);
+  for (ptrdiff_t q = 0; q < n; ++q) p[q] = NAN; /* unfilled corners stay NaN */
+  return p;
+}
+
+/* Viscosity law: power law mu_ref (T/t_ref)^exp, or Sutherland (Section 2). */
+static double viscosity(const orc_cfg* c, double T) {
+  double tr = T / c->t_ref;
+  if (c->visc_law == ORC_VISC_SUTHERLAND)
+    return c->mu_ref * pow(tr, 1.5) * (1.0 + c->suth_s) / (tr + c->suth_s);
+  return c->mu_ref * pow(tr, c->visc_exp);
+}
+
+/* ---------------------------------------------------------------- ghost fill of w */
+
+/* Isothermal no-slip wall on the staggered mesh: the ghost node mirrors an interior node
+ * across the wall interface; velocity changes sign, T_g = 2 T_w - T, p_g = p, rho_g from the
+ * equation of state, E from E = cv T + |u|^2/2. */
+static void wall_ghost(const grid_t* g, const double* win, double* wout) {
+  const orc_cfg* c = g->c;
+  double rho = win[0];
+  double u = win[1] / rho, v = win[2] / rho, w = win[3] / rho;
+  double E = win[4] / rho;
+  double T = (E - 0.5 * (u * u + v * v + w * w)) / g->cv;
+  double p = rho * c->r_gas * T;
+  double Tg = 2.0 * c->t_wall - T;
+  double pg = p;
+  double rhog = pg / (c->r_gas * Tg);
+  double ug = -u, vg = -v, wg = -w;
+  wout[0] = rhog;
+  wout[1] = rhog * ug;
+  wout[2] = rhog * vg;
+  wout[3] = rhog * wg;
+  wout[4] = rhog * (g->cv * Tg + 0.5 * (ug * ug + vg * vg + wg * wg));
+}
+
+/* Fill the ghost layers of the five ghosted conserved arrays. Only the faces are filled
+ * (no edges or corners): every stencil of the method runs along one grid line. */
+static void fill_ghosts_w(const grid_t* g, double* wg[5]) {
+  int nx = g->nx, ny = g->ny, nz = g->nz;
+  for (int m = 0; m < 5; ++m) {
+    double* f = wg[m];
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int q = 1; q <= G; ++q) {
+          f[gidx(g, -q, j, k)] = f[gidx(g, wrap(-q, nx), j, k)];
+          f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, wrap(nx - 1 + q, nx), j, k)];
+        }
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        for (int q = 1; q <= G; ++q) {
+          f[gidx(g, i, j, -q)] = f[gidx(g, i, j, wrap(-q, nz))];
+          f[gidx(g, i, j, nz - 1 + q)] = f[gidx(g, i, j, wrap(nz - 1 + q, nz))];
+        }
+    if (g->c->bc_y == ORC_BC_PERIODIC)
+      for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nx; ++i)
+          for (int q = 1; q <= G; ++q) {
+            f[gidx(g, i, -q, k)] = f[gidx(g, i, wrap(-q, ny), k)];
+            f[gidx(g, i, ny - 1 + q, k)] = f[gidx(g, i, wrap(ny - 1 + q, ny), k)];
+          }
+  }
+  if (g->c->bc_y == ORC_BC_WALL) {
+    for (int k = 0; k < nz; ++k)
+      for (int i = 0; i < nx; ++i)
+        for (int q = 0; q < G; ++q) {
+          double in[5], out[5];
+          /* lower wall: ghost j = -1-q mirrors j = q */
+          for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, q, k)];
+          wall_ghost(g, in, out);
+          for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, -1 - q, k)] = out[m];
+          /* upper wall: ghost j = ny+q mirrors j = ny-1-q */
+          for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, ny - 1 - q, k)];
+          wall_ghost(g, in, out);
+          for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, ny + q, k)] = out[m];
+        }
+  }
+}
+
+/* Ghost fill of a node scalar (sensor theta, node divergence): periodic copy, and an even
+ * mirror across a wall. */
+static void fill_ghosts_scalar(const grid_t* g, double* f) {
+  int nx = g->nx, ny = g->ny, nz = g->nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int q = 1; q <= G; ++q) {
+        f[gidx(g, -q, j, k)] = f[gidx(g, wrap(-q, nx), j, k)];
+        f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, wrap(nx - 1 + q, nx), j, k)];
+      }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int q = 1; q <= G; ++q) {
+        f[gidx(g, i, j, -q)] = f[gidx(g, i, j, wrap(-q, nz))];
+        f[gidx(g, i, j, nz - 1 + q)] = f[gidx(g, i, j, wrap(nz - 1 + q, nz))];
+      }
+  for (int k = 0; k < nz; ++k)
+    for (int i = 0; i < nx; ++i)
+      for (int q = 0; q < G; ++q) {
+        if (g->c->bc_y == ORC_BC_WALL) {
+          f[gidx(g, i, -1 - q, k)] = f[gidx(g, i, q, k)];
+          f[gidx(g, i, ny + q, k)] = f[gidx(g, i, ny - 1 - q, k)];
+        } else {
+          f[gidx(g, i, -1 - q, k)] = f[gidx(g, i, wrap(-1 - q, ny), k)];
+          f[gidx(g, i, ny + q, k)] = f[gidx(g, i, wrap(ny + q, ny), k)];
+        }
+      }
+}
+
+static void load_interior(const grid_t* g, const double* w, double* wg[5]) {
+  for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < g->nz; ++k)
+      for (int j = 0; j < g->ny; ++j)
+        for (int i = 0; i < g->nx; ++i)
+          wg[m][gidx(g, i, j, k)] = w[(ptrdiff_t)m * g->nx * g->ny * g->nz + iidx(g, i, j, k)];
+}
+
+/* ---------------------------------------------------------------- primitives */
+
+/* Primitive variables at every node from w = [rho, rho u, rho v, rho w, rho E]:
+ * E = cv T + |u|^2/2, p = rho R T, H = E + p/rho (Section 2), c = sqrt(gamma p / rho). */
+static void primitives(const grid_t* g, double* const wg[5], prims_t* P) {
+  const orc_cfg* c = g->c;
+#pragma omp parallel for schedule(static)
+  for (ptrdiff_t n = 0; n < g->ng; ++n) {
+    double rho = wg[0][n];
+    double u = wg[1][n] / rho, v = wg[2][n] / rho, w = wg[3][n] / rho;
+    double E = wg[4][n] / rho;
+    double T = (E - 0.5 * (u * u + v * v + w * w)) / g->cv;
+    double p = rho * c->r_gas * T;
+    P->rho[n] = rho;
+    P->u[n] = u; P->v[n] = v; P->w[n] = w;
+    P->T[n] = T;
+    P->p[n] = p;
+    P->H[n] = E + p / rho;
+    P->c[n] = sqrt(c->gamma * p / rho);
+    P->mu[n] = (T == T) ? viscosity(c, T) : NAN;
+  }
+}
+
+static void prims_alloc(const grid_t* g, prims_t* P) {
+  P->rho = alloc_nan(g->ng); P->u = alloc_nan(g->ng); P->v = alloc_nan(g->ng);
+  P->w = alloc_nan(g->ng); P->p = alloc_nan(g->ng); P->T = alloc_nan(g->ng);
+  P->H = alloc_nan(g->ng); P->c = alloc_nan(g->ng); P->mu = alloc_nan(g->ng);
+}
+
+static void prims_free(prims_t* P) {
+  free(P->rho); free(P->u); free(P->v); free(P->w); free(P->p);
+  free(P->T); free(P->H); free(P->c); free(P->mu);
+}
+
+/* ---------------------------------------------------------------- derivatives */
+
+static ptrdiff_t dir_stride(const grid_t* g, int dir) {
+  return dir == 0 ? g->sx : (dir == 1 ? g->sy : g->sz);
+}
+
+/* First derivative of order 2L at interior node (i,j,k) along dir, in physical space:
+ * sum_l a_l (f_{+l} - f_{-l}) / h, with h = dx, y_eta(j) deta, dz. */
+static double d1(const grid_t* g, const double* f, int i, int j, int k, int dir) {
+  ptrdiff_t n = gidx(g, i, j, k), st = dir_stride(g, dir);
+  double s = 0.0;
+  for (int l = 1; l <= g->c->L; ++l) s += g->a[l] * (f[n + l * st] - f[n - l * st]);
+  if (dir == 0) return s / g->dx;
+  if (dir == 1) return s / (g->deta * g->yeta[j]);
+  return s / g->dz;
+}
+
+/* Second derivative of order 2L along dir in physical space. Along y (stretched):
+ * d2f/dy2 = (f_etaeta - (y_etaeta / y_eta) f_eta) / y_eta^2. */
+static double d2(const grid_t* g, const double* f, int i, int j, int k, int dir) {
+  ptrdiff_t n = gidx(g, i, j, k), st = dir_stride(g, dir);
+  double s2 = 0.0, s1 = 0.0;
+  for (int l = 1; l <= g->c->L; ++l) {
+    s2 += g->b[l] * ((f[n + l * st] + f[n - l * st]) - 2.0 * f[n]);
+    s1 += g->a[l] * (f[n + l * st] - f[n - l * st]);
+  }
+  if (dir == 0) return s2 / (g->dx * g->dx);
+  if (dir == 2) return s2 / (g->dz * g->dz);
+  double fee = s2 / (g->deta * g->deta);
+  double fe = s1 / g->deta;
+  double ye = g->yeta[j];
+  return (fee - (g->yetaeta[j] / ye) * fe) / (ye * ye);
+}
+
+/* ---------------------------------------------------------------- sensor */
+
+/* Ducros sensor (Eq. sensor) at the interior nodes, theta = max(-div / sqrt(div^2 +
+ * |curl u|^2 + (u0/L0)^2), 0); the node divergence is kept for the viscous terms. Both are
+ * then ghost filled. */
+static void sensor(const grid_t* g, const prims_t* P, double* theta, double* divg) {
+  const orc_cfg* c = g->c;
+  double eps = (c->u0 / c->l0) * (c->u0 / c->l0);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        double ux = d1(g, P->u, i, j, k, 0), uy = d1(g, P->u, i, j, k, 1), uz = d1(g, P->u, i, j, k, 2);
+        double vx = d1(g, P->v, i, j, k, 0), vy = d1(g, P->v, i, j, k, 1), vz = d1(g, P->v, i, j, k, 2);
+        double wx = d1(g, P->w, i, j, k, 0), wy = d1(g, P->w, i, j, k, 1), wz = d1(g, P->w, i, j, k, 2);
+        double div = ux + vy + wz;
+        double o1 = wy - vz, o2 = uz - wx, o3 = vx - uy;
+        double curl2 = o1 * o1 + o2 * o2 + o3 * o3;
+        double th = -div / sqrt(div * div + curl2 + eps);
+        ptrdiff_t n = gidx(g, i, j, k);
+        theta[n] = th > 0.0 ? th : 0.0;
+        divg[n] = div;
+      }
+  fill_ghosts_scalar(g, theta);
+  fill_ghosts_scalar(g, divg);
+}
+
+/* Hybrid switch: WENO at the interface between nodes (n) and (n + st) iff the largest theta
+ * over nodes n-L+1 .. n+L exceeds the threshold (or WENO is forced everywhere). */
+static int interface_flag(const grid_t* g, const double* theta, ptrdiff_t n, ptrdiff_t st) {
+  const orc_cfg* c = g->c;
+  if (c->weno_mode == ORC_WENO_ALL) return 1;
+  if (c->weno_mode == ORC_WENO_OFF) return 0;
+  double tmax = 0.0;
+  for (int q = -c->L + 1; q <= c->L; ++q)
+    if (theta[n + q * st] > tmax) tmax = theta[n + q * st];
+  return tmax > c->theta_thr;
+}
+
+/* ---------------------------------------------------------------- fluxes */
+
+/* Three-point averaging operator (Eq. avg_operator). */
+static double tilde(double Fa, double Fb, double Ga, double Gb, double Ha, double Hb) {
+  return 0.125 * (Fa + Fb) * (Ga + Gb) * (Ha + Hb);
+}
+
+/* Energy-consistent central flux at the interface between node n and n+st (Eq. encflux):
+ * f = 2 sum_l a_l sum_{m<l} (rho, u_d, phi)~_{n-m, l}, phi = 1, u, v, w, H; the pressure is
+ * added to the momentum component along dir as sum_l a_l sum_{m<l} (p_{n-m} + p_{n-m+l}). */
+static void central_flux(const grid_t* g, const prims_t* P, ptrdiff_t n, ptrdiff_t st, int dir,
+                         double* f) {
+  const double* ud = dir == 0 ? P->u : (dir == 1 ? P->v : P->w);
+  const double* rho = P->rho;
+  double acc[5] = {0, 0, 0, 0, 0}, accp = 0.0;
+  for (int l = 1; l <= g->c->L; ++l) {
+    double s[5] = {0, 0, 0, 0, 0}, sp = 0.0;
+    for (int m = 0; m < l; ++m) {
+      ptrdiff_t a = n - m * st, b = n + (l - m) * st;
+      s[0] += tilde(rho[a], rho[b], ud[a], ud[b], 1.0, 1.0);
+      s[1] += tilde(rho[a], rho[b], ud[a], ud[b], P->u[a], P->u[b]);
+      s[2] += tilde(rho[a], rho[b], ud[a], ud[b], P->v[a], P->v[b]);
+      s[3] += tilde(rho[a], rho[b], ud[a], ud[b], P->w[a], P->w[b]);
+      s[4] += tilde(rho[a], rho[b], ud[a], ud[b], P->H[a], P->H[b]);
+      sp += P->p[a] + P->p[b];
+    }
+    for (int q = 0; q < 5; ++q) acc[q] += g->a[l] * s[q];
+    accp += g->a[l] * sp;
+  }
+  for (int q = 0; q < 5; ++q) f[q] = 2.0 * acc[q];
+  f[1 + dir] += accp;
+}
+
+/* Left (rows) and right (columns) eigenvectors of the Euler flux Jacobian along dir, in
+ * conserved variables, eigenvalues (u_n - c, u_n, u_n, u_n, u_n + c). Textbook form with
+ * b1 = (gamma-1)/c^2, b2 = b1 |u|^2 / 2; the two shear waves carry the tangential
+ * velocities in increasing index order. */
+void orc_eigvecs(int dir, double gamma, double u, double v, double w, double H, double* Lm,
+                 double* Rm) {
+  double vel[3] = {u, v, w};
+  double q2 = u * u + v * v + w * w;
+  double c = sqrt((gamma - 1.0) * (H - 0.5 * q2));
+  double un = vel[dir];
+  double b1 = (gamma - 1.0) / (c * c);
+  double b2 = 0.5 * q2 * b1;
+  int t1 = dir == 0 ? 1 : 0;
+  int t2 = dir == 2 ? 1 : 2;
+  double nrm[3] = {0, 0, 0};
+  nrm[dir] = 1.0;
+  for (int q = 0; q < 25; ++q) Lm[q] = Rm[q] = 0.0;
+  /* right eigenvectors: column r of Rm is Rm[row*5 + r] */
+  Rm[0 * 5 + 0] = 1.0;
+  Rm[0 * 5 + 1] = 1.0;
+  Rm[0 * 5 + 4] = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    Rm[(1 + d) * 5 + 0] = vel[d] - c * nrm[d];
+    Rm[(1 + d) * 5 + 1] = vel[d];
+    Rm[(1 + d) * 5 + 4] = vel[d] + c * nrm[d];
+  }
+  Rm[4 * 5 + 0] = H - un * c;
+  Rm[4 * 5 + 1] = 0.5 * q2;
+  Rm[4 * 5 + 4] = H + un * c;
+  Rm[(1 + t1) * 5 + 2] = 1.0;
+  Rm[4 * 5 + 2] = vel[t1];
+  Rm[(1 + t2) * 5 + 3] = 1.0;
+  Rm[4 * 5 + 3] = vel[t2];
+  /* left eigenvectors: row l of Lm is Lm[l*5 + col] */
+  Lm[0 * 5 + 0] = 0.5 * (b2 + un / c);
+  Lm[4 * 5 + 0] = 0.5 * (b2 - un / c);
+  for (int d = 0; d < 3; ++d) {
+    Lm[0 * 5 + 1 + d] = 0.5 * (-b1 * vel[d] - nrm[d] / c);
+    Lm[4 * 5 + 1 + d] = 0.5 * (-b1 * vel[d] + nrm[d] / c);
+    Lm[1 * 5 + 1 + d] = b1 * vel[d];
+  }
+  Lm[0 * 5 + 4] = 0.5 * b1;
+  Lm[4 * 5 + 4] = 0.5 * b1;
+  Lm[1 * 5 + 0] = 1.0 - b2;
+  Lm[1 * 5 + 4] = -b1;
+  Lm[2 * 5 + 0] = -vel[t1];
+  Lm[2 * 5 + 1 + t1] = 1.0;
+  Lm[3 * 5 + 0] = -vel[t2];
+  Lm[3 * 5 + 1 + t2] = 1.0;
+}
+
+/* WENO5 reconstruction of Jiang and Shu at i+1/2 from f_{i-2..i+2} (left-biased). */
+double orc_weno5(const double* f, double eps) {
+  double fm2 = f[0], fm1 = f[1], f0 = f[2], fp1 = f[3], fp2 = f[4];
+  double b0 = 13.0 / 12.0 * (fm2 - 2.0 * fm1 + f0) * (fm2 - 2.0 * fm1 + f0) +
+              0.25 * (fm2 - 4.0 * fm1 + 3.0 * f0) * (fm2 - 4.0 * fm1 + 3.0 * f0);
+  double b1 = 13.0 / 12.0 * (fm1 - 2.0 * f0 + fp1) * (fm1 - 2.0 * f0 + fp1) +
+              0.25 * (fm1 - fp1) * (fm1 - fp1);
+  double b2 = 13.0 / 12.0 * (f0 - 2.0 * fp1 + fp2) * (f0 - 2.0 * fp1 + fp2) +
+              0.25 * (3.0 * f0 - 4.0 * fp1 + fp2) * (3.0 * f0 - 4.0 * fp1 + fp2);
+  double a0 = 0.1 / ((eps + b0) * (eps + b0));
+  double a1 = 0.6 / ((eps + b1) * (eps + b1));
+  double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  double s = a0 + a1 + a2;
+  double q0 = (2.0 * fm2 - 7.0 * fm1 + 11.0 * f0) / 6.0;
+  double q1 = (-fm1 + 5.0 * f0 + 2.0 * fp1) / 6.0;
+  double q2 = (2.0 * f0 + 5.0 * fp1 - fp2) / 6.0;
+  return (a0 / s) * q0 + (a1 / s) * q1 + (a2 / s) * q2;
+}
+
+/* Characteristic Lax-Friedrichs flux-vector splitting with WENO5 reconstruction at the
+ * interface between node n and n+st (Section 2.1): Roe-averaged eigenvectors, projection of
+ * w and of the physical flux at nodes n-2..n+3, local LF speeds (largest |eigenvalue| over the
+ * stencil), WENO5 of the positive part from the left and of the negative part from the right,
+ * and projection back. */
+static void weno_flux(const grid_t* g, const prims_t* P, double* const wg[5], ptrdiff_t n,
+                      ptrdiff_t st, int dir, double* f) {
+  const orc_cfg* c = g->c;
+  const double* ud = dir == 0 ? P->u : (dir == 1 ? P->v : P->w);
+  ptrdiff_t nl = n, nr = n + st;
+  double sl = sqrt(P->rho[nl]), sr = sqrt(P->rho[nr]);
+  double ur = (sl * P->u[nl] + sr * P->u[nr]) / (sl + sr);
+  double vr = (sl * P->v[nl] + sr * P->v[nr]) / (sl + sr);
+  double wr = (sl * P->w[nl] + sr * P->w[nr]) / (sl + sr);
+  double Hr = (sl * P->H[nl] + sr * P->H[nr]) / (sl + sr);
+  double Lm[25], Rm[25];
+  orc_eigvecs(dir, c->gamma, ur, vr, wr, Hr, Lm, Rm);
+
+  double cw[5][6], cf[5][6], lam[5] = {0, 0, 0, 0, 0};
+  for (int q = 0; q < 6; ++q) {
+    ptrdiff_t nn = n + (q - 2) * st;
+    double wv[5], F[5];
+    for (int m = 0; m < 5; ++m) wv[m] = wg[m][nn];
+    double rho = P->rho[nn], un = ud[nn];
+    F[0] = rho * un;
+    F[1] = rho * un * P->u[nn];
+    F[2] = rho * un * P->v[nn];
+    F[3] = rho * un * P->w[nn];
+    F[4] = rho * un * P->H[nn];
+    F[1 + dir] += P->p[nn];
+    for (int k = 0; k < 5; ++k) {
+      double sw = 0.0, sf = 0.0;
+      for (int m = 0; m < 5; ++m) {
+        sw += Lm[k * 5 + m] * wv[m];
+        sf += Lm[k * 5 + m] * F[m];
+      }
+      cw[k][q] = sw;
+      cf[k][q] = sf;
+    }
+    double ev[5] = {un - P->c[nn], un, un, un, un + P->c[nn]};
+    for (int k = 0; k < 5; ++k)
+      if (fabs(ev[k]) > lam[k]) lam[k] = fabs(ev[k]);
+  }
+  double gh[5];
+  for (int k = 0; k < 5; ++k) {
+    double gp[6], gm[6];
+    for (int q = 0; q < 6; ++q) {
+      gp[q] = 0.5 * (cf[k][q] + lam[k] * cw[k][q]);
+      gm[q] = 0.5 * (cf[k][q] - lam[k] * cw[k][q]);
+    }
+    double sp[5] = {gp[0], gp[1], gp[2], gp[3], gp[4]};         /* nodes n-2 .. n+2 */
+    double sm[5] = {gm[5], gm[4], gm[3], gm[2], gm[1]};         /* nodes n+3 .. n-1 */
+    gh[k] = orc_weno5(sp, c->weno_eps) + orc_weno5(sm, c->weno_eps);
+  }
+  for (int m = 0; m < 5; ++m) {
+    double s = 0.0;
+    for (int k = 0; k < 5; ++k) s += Rm[m * 5 + k] * gh[k];
+    f[m] = s;
+  }
+}
+
+/* Convective part of R along one direction: interface fluxes along every interior line,
+ * the wall rule, and the conservative difference (Eq. num_flux) with the metric. */
+static void convective_dir(const grid_t* g, const prims_t* P, double* const wg[5],
+                           const double* theta, int dir, double* R, unsigned char* flags) {
+  int nd = dir == 0 ? g->nx : (dir == 1 ? g->ny : g->nz);
+  int na = dir == 0 ? g->ny : g->nx; /* first transverse */
+  int nb = dir == 2 ? g->ny : g->nz; /* second transverse */
+  ptrdiff_t st = dir_stride(g, dir);
+  ptrdiff_t Nint = (ptrdiff_t)g->nx * g->ny * g->nz;
+  int wall = dir == 1 && g->c->bc_y == ORC_BC_WALL;
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < nb; ++b) {
+    double* fl = malloc(sizeof(double) * 5 * (size_t)(nd + 1));
+    for (int a = 0; a < na; ++a) {
+      for (int s = 0; s <= nd; ++s) {
+        /* interface s lies between nodes s-1 and s along dir */
+        int i, j, k;
+        if (dir == 0) { i = s - 1; j = a; k = b; }
+        else if (dir == 1) { i = a; j = s - 1; k = b; }
+        else { i = a; j = b; k = s - 1; }
+        ptrdiff_t n = gidx(g, i, j, k);
+        int fw = interface_flag(g, theta, n, st);
+        if (flags) {
+          ptrdiff_t fi;
+          if (dir == 0) fi = ((ptrdiff_t)k * g->ny + j) * (g->nx + 1) + s;
+          else if (dir == 1) fi = ((ptrdiff_t)k * (g->ny + 1) + s) * g->nx + i;
+          else fi = ((ptrdiff_t)s * g->ny + j) * g->nx + i;
+          flags[fi] = (unsigned char)fw;
+        }
+        if (fw) weno_flux(g, P, wg, n, st, dir, fl + 5 * s);
+        else central_flux(g, P, n, st, dir, fl + 5 * s);
+        if (wall && (s == 0 || s == nd)) {
+          /* staggered wall interface: no mass, x/z momentum or energy crosses the wall */
+          fl[5 * s + 0] = 0.0;
+          fl[5 * s + 1] = 0.0;
+          fl[5 * s + 3] = 0.0;
+          fl[5 * s + 4] = 0.0;
+        }
+      }
+      for (int s = 0; s < nd; ++s) {
+        int i, j, k;
+        if (dir == 0) { i = s; j = a; k = b; }
+        else if (dir == 1) { i = a; j = s; k = b; }
+        else { i = a; j = b; k = s; }
+        double h = dir == 0 ? g->dx : (dir == 1 ? g->deta * g->yeta[j] : g->dz);
+        ptrdiff_t q = iidx(g, i, j, k);
+        for (int m = 0; m < 5; ++m)
+          R[m * Nint + q] -= (fl[5 * (s + 1) + m] - fl[5 * s + m]) / h;
+      }
+    }
+    free(fl);
+  }
+}
+
+/* ---------------------------------------------------------------- viscous terms */
+
+/* Viscous terms in Laplacian form at an interior node (Section 2.1 and Eqs. sigma, heat_vec):
+ *   V_i = mu lap(u_i) + mu/3 d_i(div) + d_j mu (d_j u_i + d_i u_j) - 2/3 div d_i mu,
+ *   V_E = u_i V_i + sigma_ij d_j u_i + k lap(T) + d_j k d_j T,  k = cp mu / Pr,
+ * with first derivatives D1 and second derivatives D2 of order 2L; d_i(div) is D1 of the
+ * ghost-filled node divergence. */
+static void viscous_node(const grid_t* g, const prims_t* P, const double* divg, int i, int j,
+                         int k, double* out) {
+  const orc_cfg* c = g->c;
+  const double* vel[3] = {P->u, P->v, P->w};
+  double du[3][3], dT[3], dmu[3], ddiv[3], lap[3], lapT = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) du[a][b] = d1(g, vel[a], i, j, k, b);
+  for (int b = 0; b < 3; ++b) {
+    dT[b] = d1(g, P->T, i, j, k, b);
+    dmu[b] = d1(g, P->mu, i, j, k, b);
+    ddiv[b] = d1(g, divg, i, j, k, b);
+  }
+  for (int a = 0; a < 3; ++a) {
+    lap[a] = 0.0;
+    for (int b = 0; b < 3; ++b) lap[a] += d2(g, vel[a], i, j, k, b);
+  }
+  for (int b = 0; b < 3; ++b) lapT += d2(g, P->T, i, j, k, b);
+  ptrdiff_t n = gidx(g, i, j, k);
+  double mu = P->mu[n];
+  double div = du[0][0] + du[1][1] + du[2][2];
+  double V[3];
+  for (int a = 0; a < 3; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < 3; ++b) s += dmu[b] * (du[a][b] + du[b][a]);
+    V[a] = mu * lap[a] + mu * ddiv[a] / 3.0 + s - 2.0 / 3.0 * div * dmu[a];
+  }
+  double uvec[3] = {P->u[n], P->v[n], P->w[n]};
+  double work = 0.0, diss = 0.0;
+  for (int a = 0; a < 3; ++a) work += uvec[a] * V[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double sig = mu * (du[a][b] + du[b][a] - (a == b ? 2.0 / 3.0 * div : 0.0));
+      diss += sig * du[a][b];
+    }
+  double kc = g->cp * mu / c->prandtl;
+  double heat = kc * lapT;
+  for (int b = 0; b < 3; ++b) heat += g->cp / c->prandtl * dmu[b] * dT[b];
+  out[0] = 0.0;
+  out[1] = V[0];
+  out[2] = V[1];
+  out[3] = V[2];
+  out[4] = work + diss + heat;
+}
+
+/* ---------------------------------------------------------------- right-hand side */
+
+static int rhs_impl(const orc_cfg* c, const double* w, double* rhs, double* theta_out,
+                    double* div_out, unsigned char* fx, unsigned char* fy, unsigned char* fz) {
+  grid_t g;
+  if (grid_init(&g, c)) return -1;
+  ptrdiff_t N = (ptrdiff_t)g.nx * g.ny * g.nz;
+  double* wg[5];
+  for (int m = 0; m < 5; ++m) wg[m] = alloc_nan(g.ng);
+  load_interior(&g, w, wg);
+  fill_ghosts_w(&g, wg);
+  prims_t P;
+  prims_alloc(&g, &P);
+  primitives(&g, wg, &P);
+  double* theta = alloc_nan(g.ng);
+  double* divg = alloc_nan(g.ng);
+  sensor(&g, &P, theta, divg);
+
+  double* R = rhs ? rhs : malloc(sizeof(double) * 5 * (size_t)N);
+  memset(R, 0, sizeof(double) * 5 * (size_t)N);
+  if (c->convective || fx || fy || fz) {
+    double* Rc = c->convective ? R : calloc(5 * (size_t)N, sizeof(double));
+    convective_dir(&g, &P, wg, theta, 0, Rc, fx);
+    convective_dir(&g, &P, wg, theta, 1, Rc, fy);
+    convective_dir(&g, &P, wg, theta, 2, Rc, fz);
+    if (!c->convective) free(Rc);
+  }
+  if (c->viscous) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          double v[5];
+          viscous_node(&g, &P, divg, i, j, k, v);
+          ptrdiff_t q = iidx(&g, i, j, k);
+          for (int m = 0; m < 5; ++m) R[m * N + q] += v[m];
+        }
+  }
+  if (c->forcing) {
+    /* constant mass flow: f makes the volume integral of the x-momentum residual vanish;
+     * the power f u is added to the energy residual (Eqs. 1b, 1c). */
+    double vol = 0.0, sru = 0.0;
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          double dv = g.dx * (g.yeta[j] * g.deta) * g.dz;
+          vol += dv;
+          sru += R[1 * N + iidx(&g, i, j, k)] * dv;
+        }
+    double f = -sru / vol;
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          ptrdiff_t q = iidx(&g, i, j, k);
+          R[1 * N + q] += f;
+          R[4 * N + q] += f * P.u[gidx(&g, i, j, k)];
+        }
+  }
+  if (theta_out || div_out)
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          if (theta_out) theta_out[iidx(&g, i, j, k)] = theta[gidx(&g, i, j, k)];
+          if (div_out) div_out[iidx(&g, i, j, k)] = divg[gidx(&g, i, j, k)];
+        }
+  if (!rhs) free(R);
+  free(theta); free(divg);
+  prims_free(&P);
+  for (int m = 0; m < 5; ++m) free(wg[m]);
+  grid_free(&g);
+  return 0;
+}
+
+int orc_rhs(const orc_cfg* c, const double* w, double* rhs) {
+  return rhs_impl(c, w, rhs, NULL, NULL, NULL, NULL, NULL);
+}
+
+int orc_sensor(const orc_cfg* c, const double* w, double* theta, double* div, unsigned char* fx,
+               unsigned char* fy, unsigned char* fz) {
+  orc_cfg cc = *c;
+  cc.convective = 0; /* flags are still produced by walking the interfaces */
+  cc.viscous = 0;
+  cc.forcing = 0;
+  return rhs_impl(&cc, w, NULL, theta, div, fx, fy, fz);
+}
+
+int orc_fill_ghosts(const orc_cfg* c, const double* w, double* out) {
+  grid_t g;
+  if (grid_init(&g, c)) return -1;
+  double* wg[5];
+  for (int m = 0; m < 5; ++m) {
+    wg[m] = out + (ptrdiff_t)m * g.ng;
+    for (ptrdiff_t q = 0; q < g.ng; ++q) wg[m][q] = NAN;
+  }
+  load_interior(&g, w, wg);
+  fill_ghosts_w(&g, wg);
+  grid_free(&g);
+  return 0;
+}
+
+/* ---------------------------------------------------------------- time integration */
+
+/* Eq. RK: w^(l+1) = w^(l) + alpha_l dt R^(l-1) + beta_l dt R^(l). The printed alpha_1 = +17/60
+ * is read as -17/60 (Wray's scheme; first-order consistency requires sum alpha + sum beta = 1). */
+void orc_rk_stage_update(int stage, double dt, double* w, const double* r_old, const double* r,
+                         long n) {
+  static const double alpha[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+  static const double beta[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+  for (long q = 0; q < n; ++q)
+    w[q] = w[q] + alpha[stage] * dt * r_old[q] + beta[stage] * dt * r[q];
+}
+
+/* Convective CFL step: dt = cfl / max over nodes of sum_d (|u_d| + c) / h_d. */
+double orc_cfl_dt(const orc_cfg* c, const double* w, double cfl) {
+  grid_t g;
+  if (grid_init(&g, c)) return -1.0;
+  ptrdiff_t N = (ptrdiff_t)g.nx * g.ny * g.nz;
+  double smax = 0.0;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        ptrdiff_t q = iidx(&g, i, j, k);
+        double rho = w[q];
+        double u = w[N + q] / rho, v = w[2 * N + q] / rho, ww = w[3 * N + q] / rho;
+        double E = w[4 * N + q] / rho;
+        double T = (E - 0.5 * (u * u + v * v + ww * ww)) / g.cv;
+        double p = rho * c->r_gas * T;
+        double cs = sqrt(c->gamma * p / rho);
+        double s = (fabs(u) + cs) / g.dx + (fabs(v) + cs) / (g.yeta[j] * g.deta) +
+                   (fabs(ww) + cs) / g.dz;
+        if (!(s <= smax)) smax = s; /* a NaN propagates */
+      }
+  grid_free(&g);
+  return cfl / smax;
+}
+
+int orc_rk_step(const orc_cfg* c, double* w, double dt, double cfl, double* dt_used) {
+  long n = 5L * c->nx * c->ny * c->nz;
+  if (dt <= 0.0) dt = orc_cfl_dt(c, w, cfl);
+  if (dt_used) *dt_used = dt;
+  double* r_old = calloc((size_t)n, sizeof(double));
+  double* r = malloc(sizeof(double) * (size_t)n);
+  int rc = 0;
+  for (int stage = 0; stage < 3 && rc == 0; ++stage) {
+    rc = orc_rhs(c, w, r);
+    orc_rk_stage_update(stage, dt, w, r_old, r, n);
+    double* t = r_old;
+    r_old = r;
+    r = t;
+  }
+  free(r_old);
+  free(r);
+  return rc;
+}
+
+/* Metric-weighted totals: sum over interior nodes of w_m dx (y_eta deta) dz. */
+int orc_totals(const orc_cfg* c, const double* w, double out[5]) {
+  grid_t g;
+  if (grid_init(&g, c)) return -1;
+  ptrdiff_t N = (ptrdiff_t)g.nx * g.ny * g.nz;
+  for (int m = 0; m < 5; ++m) {
+    double s = 0.0;
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i)
+          s += w[m * N + iidx(&g, i, j, k)] * (g.dx * (g.yeta[j] * g.deta) * g.dz);
+    out[m] = s;
+  }
+  grid_free(&g);
+  return 0;
+}

@@ -1,0 +1,93 @@
+/*
+ * FP64 CPU oracle for the compressible Navier-Stokes right-hand side and the
+ * Wray low-storage RK3 update of STREAmS (arXiv 2004.02276, Section 2).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code is the plain, slow reference that the
+ * CUDA path is checked against. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it. It shares no code, header,
+ * table or helper with the CUDA library, and the CUDA library never calls it.
+ *
+ * Arrays passed in and out are interior-only, SoA, x fastest:
+ *   w[m][k][j][i], m = 0..4 for (rho, rho u, rho v, rho w, rho E),
+ *   i < nx, j < ny, k < nz.  Size 5*nx*ny*nz doubles.
+ *
+ * Interface flags (which interfaces use WENO) are returned per direction:
+ *   x: [nz][ny][nx+1], y: [nz][ny+1][nx], z: [nz+1][ny][nx];
+ *   entry s along the direction is the interface between nodes s-1 and s.
+ */
+#ifndef STRM_ORACLE_H
+#define STRM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1 };
+enum { ORC_WENO_OFF = 0, ORC_WENO_SENSOR = 1, ORC_WENO_ALL = 2 };
+enum { ORC_VISC_POWER = 0, ORC_VISC_SUTHERLAND = 1 };
+
+typedef struct {
+  /* grid: nx*ny*nz interior nodes; y nodes at eta_j = (j+1/2)/ny */
+  int nx, ny, nz;
+  double lx, ly, lz;
+  int y_map;            /* ORC_MAP_UNIFORM or ORC_MAP_TANH */
+  double beta;          /* tanh stretching parameter */
+  int bc_y;             /* ORC_BC_PERIODIC or ORC_BC_WALL (x and z are periodic) */
+  /* gas: p = rho R T, E = cv T + |u|^2/2, k = cp mu / Pr */
+  double gamma, prandtl, r_gas;
+  int visc_law;         /* mu = mu_ref (T/t_ref)^visc_exp, or Sutherland with constant suth_s */
+  double mu_ref, t_ref, visc_exp, suth_s;
+  double t_wall;        /* isothermal wall temperature */
+  int forcing;          /* constant mass flow rate forcing in x */
+  /* scheme */
+  int L;                /* central stencil half width (order 2L): 2 or 3 */
+  int weno_mode;        /* ORC_WENO_OFF / SENSOR / ALL */
+  double theta_thr;     /* sensor threshold */
+  double weno_eps;      /* WENO epsilon */
+  double u0, l0;        /* sensor velocity and length scales */
+  int convective, viscous; /* term switches (both 1 for the full method) */
+} orc_cfg;
+
+/* Full right-hand side R(w) (convective + viscous + forcing), interior only. */
+int orc_rhs(const orc_cfg* c, const double* w, double* rhs);
+
+/* One Wray RK3 step in place. dt > 0: fixed; dt <= 0: CFL step with number cfl.
+ * The step used is written to *dt_used (nullable). */
+int orc_rk_step(const orc_cfg* c, double* w, double dt, double cfl, double* dt_used);
+
+/* One RK stage update w <- w + dt (alpha_l r_old + beta_l r), n values. */
+void orc_rk_stage_update(int stage, double dt, double* w, const double* r_old,
+                         const double* r, long n);
+
+/* CFL time step for the state w. */
+double orc_cfl_dt(const orc_cfg* c, const double* w, double cfl);
+
+/* Volume-weighted totals of the five conserved fields. */
+int orc_totals(const orc_cfg* c, const double* w, double out[5]);
+
+/* Sensor, node divergence and interface flags (see layout above). Each output nullable. */
+int orc_sensor(const orc_cfg* c, const double* w, double* theta, double* div,
+               unsigned char* fx, unsigned char* fy, unsigned char* fz);
+
+/* Ghost-filled conserved field, [5][nz+2G][ny+2G][nx+2G], G = 3. Corners stay NaN. */
+int orc_fill_ghosts(const orc_cfg* c, const double* w, double* wg);
+
+/* Wall-normal metrics at the nodes: y(eta_j), y_eta, y_etaeta (each ny). */
+void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta);
+
+/* Left/right eigenvectors of the flux Jacobian along direction dir (0,1,2) at the state
+ * (u, v, w, H) with sound speed from H, row-major 5x5; Lm * Rm = I. */
+void orc_eigvecs(int dir, double gamma, double u, double v, double w, double H,
+                 double* Lm, double* Rm);
+
+/* WENO5-JS reconstruction at i+1/2 from f[0..4] = f_{i-2..i+2}. */
+double orc_weno5(const double* f, double eps);
+
+/* Number of ghost layers used by the oracle. */
+int orc_ghosts(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

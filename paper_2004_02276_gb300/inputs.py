@@ -1,0 +1,167 @@
+"""Seeded synthetic inputs and workload definitions.
+
+This module is shared by the CUDA path's tests and benchmark and by the oracle's tests. It holds
+no arithmetic of the method (no fluxes, derivatives, sensor or time stepping): only
+
+* ``Case``: the parameters of a workload (grid, gas, scheme), with the non-dimensionalisation
+  of the plane channel: rho_b = u_b = h = T_w = 1, R = 1/(gamma M_b^2) so that c_w = 1/M_b,
+  mu_w = 2/Re_b (Re_b = 2 rho_b u_b h / mu_w, Section 3.1), mu = mu_w T^0.76;
+* a counter-based SplitMix64 generator (Steele, Lea and Flood, 2014) indexed by
+  (component, k, j, i), and
+* initial states built from it (laminar Poiseuille profile plus uniform velocity noise).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, index: np.ndarray) -> np.ndarray:
+    """SplitMix64 output number ``index`` (0-based) of the stream started at ``seed``."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (index.astype(np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, shape) -> np.ndarray:
+    """Uniform doubles in [0, 1) with 53 random bits, C order over ``shape``."""
+    n = int(np.prod(shape))
+    z = splitmix64(seed, np.arange(n, dtype=np.uint64))
+    return ((z >> np.uint64(11)).astype(np.float64) * 2.0**-53).reshape(shape)
+
+
+@dataclasses.dataclass(frozen=True)
+class Case:
+    """A workload: grid, gas and scheme parameters (channel defaults)."""
+
+    name: str = "channel"
+    nx: int = 64
+    ny: int = 48
+    nz: int = 32
+    lx: float = 2.0 * math.pi
+    ly: float = 2.0
+    lz: float = math.pi
+    beta: float = 1.5            # tanh wall clustering; 0 gives a uniform y grid
+    y_wall: bool = True          # isothermal staggered walls in y (else periodic)
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    mach: float = 1.5            # bulk Mach number u_b / c_w
+    reynolds: float = 3000.0     # bulk Reynolds number 2 rho_b u_b h / mu_w
+    visc_law: str = "power"
+    visc_exp: float = 0.76
+    suth_s: float = 110.4 / 288.15
+    t_wall: float = 1.0
+    forcing: bool = True
+    L: int = 3                   # central scheme of order 2L
+    weno_mode: str = "sensor"    # "off", "sensor" (Ducros switch) or "all"
+    theta_thr: float = 0.05
+    weno_eps: float = 1e-6
+    u0: float = 1.0              # sensor velocity scale (bulk velocity)
+    l0: float = 1.0              # sensor length scale (channel half height)
+    convective: bool = True
+    viscous: bool = True
+    cfl: float = 0.8
+    steps: int = 20
+    noise: float = 0.05          # uniform velocity noise amplitude (fraction of u_b)
+    seed: int = 0
+
+    @property
+    def r_gas(self) -> float:
+        return 1.0 / (self.gamma * self.mach**2)
+
+    @property
+    def mu_ref(self) -> float:
+        return 2.0 / self.reynolds
+
+    @property
+    def t_ref(self) -> float:
+        return self.t_wall
+
+    @property
+    def npts(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def replace(self, **kw) -> "Case":
+        return dataclasses.replace(self, **kw)
+
+
+# The five benchmark workloads' channel members; C1 is the small parity case, C2 the bench case.
+C1 = Case(name="channel-64x48x32", nx=64, ny=48, nz=32, reynolds=3000.0, steps=20)
+C2 = Case(name="channel-256x192x128", nx=256, ny=192, nz=128, reynolds=7000.0, steps=200)
+
+
+def node_y(case: Case) -> np.ndarray:
+    """Wall-normal node positions used to lay out the initial profile (nodes at the cell
+    centres of a tanh-clustered grid between the walls y = -ly/2 and y = ly/2)."""
+    eta = (np.arange(case.ny) + 0.5) / case.ny
+    if case.beta and case.beta > 0:
+        return 0.5 * case.ly * np.tanh(case.beta * (2.0 * eta - 1.0)) / math.tanh(case.beta)
+    return case.ly * (eta - 0.5)
+
+
+def channel_state(case: Case, seed: int | None = None) -> np.ndarray:
+    """Initial channel state w = [rho, rho u, rho v, rho w, rho E], shape [5, nz, ny, nx].
+
+    rho = 1, T = T_w; u = 1.5 u_b (1 - (2y/ly)^2) plus noise, v and w noise only; the noise is
+    uniform in [-a, a] (a = ``case.noise``) from SplitMix64 over index (component, k, j, i).
+    """
+    seed = case.seed if seed is None else seed
+    nz, ny, nx = case.nz, case.ny, case.nx
+    r = uniform(seed, (3, nz, ny, nx))
+    noise = case.noise * (2.0 * r - 1.0)
+    yy = node_y(case)
+    u = 1.5 * (1.0 - (2.0 * yy / case.ly) ** 2)[None, :, None] + noise[0]
+    v = noise[1]
+    w = noise[2]
+    rho = np.ones((nz, ny, nx))
+    T = np.full((nz, ny, nx), case.t_wall)
+    cv = case.r_gas / (case.gamma - 1.0)
+    out = np.empty((5, nz, ny, nx))
+    out[0] = rho
+    out[1] = rho * u
+    out[2] = rho * v
+    out[3] = rho * w
+    out[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    return out
+
+
+def random_state(case: Case, seed: int, amp_u: float = 0.3, amp_rho: float = 0.2,
+                 amp_t: float = 0.2) -> np.ndarray:
+    """A rough random state (no structure) for conservation and parity checks:
+    rho = 1 + amp_rho s, T = 1 + amp_t s, velocities amp_u s, s uniform in [-1, 1]."""
+    nz, ny, nx = case.nz, case.ny, case.nx
+    s = 2.0 * uniform(seed, (5, nz, ny, nx)) - 1.0
+    rho = 1.0 + amp_rho * s[0]
+    u, v, w = amp_u * s[1], amp_u * s[2], amp_u * s[3]
+    T = case.t_wall * (1.0 + amp_t * s[4])
+    cv = case.r_gas / (case.gamma - 1.0)
+    out = np.empty((5, nz, ny, nx))
+    out[0] = rho
+    out[1] = rho * u
+    out[2] = rho * v
+    out[3] = rho * w
+    out[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    return out
+
+
+def primitive_state(case: Case, rho, u, v, w, T) -> np.ndarray:
+    """Conserved state from primitive fields given on the [nz, ny, nx] nodes."""
+    cv = case.r_gas / (case.gamma - 1.0)
+    shape = (case.nz, case.ny, case.nx)
+    rho, u, v, w, T = (np.broadcast_to(np.asarray(a, dtype=np.float64), shape)
+                       for a in (rho, u, v, w, T))
+    out = np.empty((5,) + shape)
+    out[0] = rho
+    out[1] = rho * u
+    out[2] = rho * v
+    out[3] = rho * w
+    out[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    return out
