@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point RK-stage updates per second of the FP64 compressible-channel step.
+
+Workload: the 256 x 192 x 128 plane channel (bulk Mach 1.5, bulk Re 7000, tanh-stretched walls,
+6th-order central + WENO5 under the Ducros switch, power-law viscosity, CFL 0.8), seeded perturbed
+laminar initial state. One benchmark step is one Wray RK3 step (three right-hand-side evaluations
+and stage updates) over the whole grid; value = N * 3 * steps * ranks / time.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the method is not
+decomposed across GPUs here): each rank advances its own copy, timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2004_02276_gb300 import inputs  # noqa: E402
+
+METRIC = "grid-pt RK-stage updates/s, FP64 vs mixed, % HBM roofline at stated error"
+UNIT = "grid-pt RK-stage updates/s"
+CASE = inputs.C2
+
+# Algorithmic FP64 flops per unit of work of each kernel (add/sub/mul = 1, FMA = 2, division and
+# square root = 1), counted from the operations each kernel's formulation performs; the counts are
+# derived line by line in the design doc. Units: faces for the face kernels, interior nodes otherwise.
+FLOPS_PER_UNIT = {
+    "weno_x": 1190, "weno_y": 1190, "weno_z": 1190,
+    "faces_x": 151, "faces_y": 151, "faces_z": 151,
+    "assemble": 520, "sensor": 105, "prims": 25,
+}
+# FP64 peak: 1.25 TFLOP/s nominal for GB300 (the profiling recipe's unit table); a probe of
+# dependent-chain-free DFMA on this pool measured 1.20 TFLOP/s at ~1.97 GHz.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_sample(case):
+    """The oracle on one full RK3 step of the workload (host cores): (rate, seconds, state)."""
+    from oracle import oracle as O
+
+    cfg = O.make_cfg(case)
+    w0 = inputs.channel_state(case, seed=0)
+    t0 = time.perf_counter()
+    w1, dt = O.rk_step(cfg, w0, cfl=case.cfl)
+    sec = time.perf_counter() - t0
+    return case.npts * 3 / sec, sec, w1, O.threads()
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2004_02276_gb300 import binding
+
+    torch.cuda.set_device(local)
+    case = CASE
+    solver = binding.Solver(case, device=f"cuda:{local}")
+    w0 = inputs.channel_state(case, seed=0)
+    w = torch.from_numpy(w0).cuda()
+    r_old = torch.zeros_like(w)
+    stream = solver.stream
+
+    # warm-up (also captures the step graph)
+    solver.advance_n(w, r_old, args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K graph-replayed steps, inputs (state 252 MB, workspace 1.7 GB) exceed L2
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = solver.launch_count()
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        start.record(stream)
+        solver.advance_n(w, r_old, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = solver.launch_count() - n0
+    ms = start.elapsed_time(stop)
+    ms_max = max_over_ranks(world, ms)
+    value = case.npts * 3 * args.steps * world / (ms_max / 1e3)
+
+    # per-kernel event timing over the same number of steps (eager launches)
+    solver.timing(True)
+    solver.advance_n(w, r_old, args.steps)
+    ktimes, weno_faces = solver.timing_read()
+    solver.timing(False)
+    busy = {k: v for k, v in ktimes.items() if v[1] > 0}
+    dom = max(busy, key=lambda k: busy[k][0])
+    dom_ms, dom_n = busy[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    if dom.startswith("weno"):
+        units = weno_faces["xyz".index(dom[-1])] / dom_n
+    elif dom.startswith("faces"):
+        d = "xyz".index(dom[-1])
+        units = (case.nx + (d == 0)) * (case.ny + (d == 1)) * (case.nz + (d == 2))
+    else:
+        units = case.npts
+    achieved = FLOPS_PER_UNIT.get(dom, 0) * units / avg_s / 1e12
+    total_ms = sum(v[0] for v in busy.values())
+    roofline = {
+        "bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
+        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+        "traffic": None, "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe); probe measured 1.20",
+        "units_per_launch": units, "flops_per_unit": FLOPS_PER_UNIT.get(dom),
+        "avg_launch_ms": round(dom_ms / dom_n, 4),
+        "kernel_share": {k: round(v[0] / total_ms, 4) for k, v in sorted(busy.items())},
+        "weno_face_fraction": round(sum(weno_faces) / (3 * args.steps * 3 * case.npts), 4),
+    }
+
+    # end to end through the C ABI with host buffers: per step H2D of the state, one RK3 step,
+    # D2H of the new state
+    w_host = torch.from_numpy(inputs.channel_state(case, seed=0)).pin_memory()
+    wd = torch.empty_like(w)
+    rd = torch.zeros_like(w)
+    solver.advance_n_host(w_host, wd, rd, 1)  # warm (graph for these buffers)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.advance_n_host(w_host, wd, rd, 1)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    nbytes = 5 * case.npts * 8
+    e2e = {"value": case.npts * 3 * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz],
+                   "mach_b": case.mach, "re_b": case.reynolds, "scheme": "central6+WENO5 (Ducros 0.05)",
+                   "cfl": case.cfl, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state 252 MB + workspace 1.7 GB vs 129 MB L2)"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        rate, sec, w_ref, cores = cpu_sample(case)
+        # the same first step on the GPU, for the error at which the figure holds
+        wg = torch.from_numpy(w0).cuda()
+        rg = torch.zeros_like(wg)
+        solver.rk_step(wg, rg)
+        wg = wg.cpu().numpy()
+        err = [float(np.linalg.norm(wg[m] - w_ref[m]) / np.linalg.norm(w_ref[m])) for m in range(5)]
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"one RK3 step of the full {case.name} workload "
+                                         f"({sec:.1f} s on the host)"}
+        out["error"] = {"rel_l2_vs_oracle_first_step": err, "max": max(err)}
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args, world, rank):
+    """The FP64 C oracle timed on the host cores, each step a bounded sample of the workload:
+    one RK3 step on a 256 x 192 x 16 slab of the channel (same x/y grid and scheme)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    case = CASE.replace(nz=16)
+    cfg = O.make_cfg(case)
+    w = inputs.channel_state(case, seed=0)
+    for _ in range(args.warmup):
+        w, _ = O.rk_step(cfg, w, cfl=case.cfl)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w, _ = O.rk_step(cfg, w, cfl=case.cfl)
+    sec = time.perf_counter() - t0
+    value = case.npts * 3 * args.steps / sec
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": CASE.name, "grid": [CASE.nx, CASE.ny, CASE.nz], "precision": "fp64",
+                   "sample": "each step: one RK3 step on a 256x192x16 slab of the workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": "one RK3 step on a 256x192x16 slab per benchmark step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

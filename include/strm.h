@@ -1,0 +1,170 @@
+/*
+ * strm.h: C ABI of the GB300 (sm_103a) library that evaluates the right-hand side of the 3D
+ * compressible Navier-Stokes equations and advances them with Wray's low-storage RK3, the
+ * method of STREAmS (Bernardini, Modesti, Salvadore and Pirozzoli, arXiv 2004.02276, Section 2).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: STRM_OK (0) or a negative status below. strm_last_error() gives a
+ *     thread-local message for the last failure. No C++ exception or abort crosses the ABI.
+ *   - Device pointers: every `double*` state or residual argument is a device address
+ *     (cudaMalloc'd or from a framework allocator) unless its name ends in `_host`.
+ *   - State layout: the conserved variables w = [rho, rho u, rho v, rho w, rho E] (Section 2.2)
+ *     as five SoA fields over the interior nodes only, x fastest:
+ *         w[m*N + (k*ny + j)*nx + i],  N = nx*ny*nz,  0 <= m < 5.
+ *     Residuals R and the RK register use the same layout. Ghost layers live in the workspace.
+ *   - Ownership: the caller owns w, r_old, rhs and the workspace. The library owns only the
+ *     opaque context (host memory) and, after the first strm_advance_n call, a CUDA graph and
+ *     a private capture stream. It never allocates device memory.
+ *   - Streams: all work is enqueued on the stream given to strm_init_grid, in stream order.
+ *     Entry points that return host data (strm_conserved_totals, strm_get_time, the _host
+ *     variants) synchronise that stream; the others return without waiting.
+ *   - Concurrency: a context is not thread safe; use one context per host thread/stream.
+ *
+ * Grid (Section 3.1): nx*ny*nz nodes; x and z uniform and periodic; y nodes at
+ * eta_j = (j + 1/2)/ny mapped by y = (ly/2) tanh(beta (2 eta - 1))/tanh(beta) (beta = 0 gives
+ * a uniform grid), so that walls at eta = 0 and 1 fall on interfaces (staggered wall).
+ * Non-dimensional gas: p = rho R T, E = cv T + |u|^2/2, H = E + p/rho, k = cp mu/Pr.
+ */
+#ifndef STRM_H
+#define STRM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STRM_OK = 0,
+  STRM_EINVAL = -1,     /* bad argument or configuration */
+  STRM_ECUDA = -2,      /* a CUDA runtime call failed */
+  STRM_ENONFINITE = -3, /* a reduction met NaN or Inf (the state blew up) */
+  STRM_ENOMEM = -4,     /* workspace smaller than strm_workspace_bytes() */
+  STRM_ETIMEOUT = -5    /* reserved for bounded device-side waits */
+};
+
+enum { STRM_MAP_UNIFORM = 0, STRM_MAP_TANH = 1 };
+enum { STRM_BC_PERIODIC = 0, STRM_BC_WALL_ISOTHERMAL = 1 };
+enum { STRM_FACE_YMIN_YMAX = 0 };
+enum { STRM_WENO_OFF = 0, STRM_WENO_SENSOR = 1, STRM_WENO_ALL = 2 };
+enum { STRM_VISC_POWER = 0, STRM_VISC_SUTHERLAND = 1 };
+enum { STRM_PREC_FP64 = 0 };
+
+typedef struct {
+  int nx, ny, nz;        /* interior nodes, each >= 1 (ny >= 3 with walls) */
+  double lx, ly, lz;     /* box lengths */
+  int y_map;             /* STRM_MAP_UNIFORM or STRM_MAP_TANH */
+  double beta;           /* tanh clustering parameter (> 0 for STRM_MAP_TANH) */
+} strm_grid;
+
+typedef struct {
+  double gamma;          /* ratio of specific heats */
+  double prandtl;        /* Pr (Section 2: 0.72) */
+  double r_gas;          /* gas constant R in the chosen units */
+  int visc_law;          /* STRM_VISC_POWER: mu_ref (T/t_ref)^visc_exp; SUTHERLAND: suth_s = S/t_ref */
+  double mu_ref, t_ref, visc_exp, suth_s;
+  double t_wall;         /* isothermal wall temperature */
+  int forcing;           /* 1: constant mass flow rate in x (Eqs. 1b, 1c) */
+} strm_phys;
+
+typedef struct {
+  int L;                 /* central scheme half width, order 2L: 2 or 3 (Eq. encflux) */
+  int weno_mode;         /* STRM_WENO_OFF / SENSOR (Ducros switch, Eq. sensor) / ALL */
+  double theta_thr;      /* sensor threshold for the WENO switch */
+  double weno_eps;       /* WENO5 epsilon */
+  double u0, l0;         /* sensor scales: the floor in the sensor denominator is (u0/l0)^2 */
+  int convective;        /* 1: include convective terms (0 only for tests) */
+  int viscous;           /* 1: include viscous terms (0 for inviscid runs) */
+  int precision;         /* STRM_PREC_FP64 */
+} strm_scheme;
+
+typedef struct strm_ctx strm_ctx;
+
+/* Thread-local message describing the last non-OK status. */
+const char* strm_last_error(void);
+
+/* Device workspace (bytes) a context with this grid and scheme needs; 0 if invalid. */
+size_t strm_workspace_bytes(const strm_grid* g, const strm_scheme* s);
+
+/* Create a context (Section 2; grid of Section 3.1). `workspace` is a device buffer of at least
+ * strm_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept alive until
+ * strm_destroy. `stream` is a cudaStream_t (NULL: the legacy default stream). The y boundary
+ * starts periodic; strm_set_bc selects walls. Uploads the wall-normal metrics (stream order). */
+int strm_init_grid(strm_ctx** ctx, const strm_grid* g, const strm_phys* p, const strm_scheme* s,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* Boundary condition of the y faces (x and z are always periodic). kind =
+ * STRM_BC_PERIODIC or STRM_BC_WALL_ISOTHERMAL (no-slip, T = t_wall, staggered: Section 3.1).
+ * params/nparams are reserved and must be NULL/0. */
+int strm_set_bc(strm_ctx* ctx, int face, int kind, const double* params, int nparams);
+
+/* rhs <- R(w): convective (central or WENO per the sensor), viscous and forcing terms
+ * (Section 2.1, Eqs. 1a-c). w and rhs are device arrays of 5*N doubles; they must not alias. */
+int strm_compute_rhs(strm_ctx* ctx, const double* w, double* rhs);
+
+/* One RK3 step in place (Eq. RK, alpha = (0, -17/60, -5/12), beta = (8/15, 5/12, 3/4)).
+ * dt > 0: fixed step; dt <= 0: CFL step dt = cfl / max(sum_d (|u_d| + c)/h_d), computed on the
+ * device. r_old is a caller-owned device register of 5*N doubles (its contents on entry are
+ * not used; on exit it holds the last stage's residual). */
+int strm_rk_step(strm_ctx* ctx, double* w, double* r_old, double dt, double cfl);
+
+/* nsteps RK3 steps (as strm_rk_step) replayed from a CUDA graph captured on first use. */
+int strm_advance_n(strm_ctx* ctx, double* w, double* r_old, int nsteps, double dt, double cfl);
+
+/* Host-buffer variant: copies w_host (5*N doubles, ideally pinned) to the device buffer w,
+ * advances nsteps, copies the state back to w_host and waits for the stream. */
+int strm_advance_n_host(strm_ctx* ctx, double* w_host, double* w, double* r_old, int nsteps,
+                        double dt, double cfl);
+
+/* Metric-weighted totals out_host[m] = sum_interior w_m dx (y_eta deta) dz. Synchronises.
+ * Returns STRM_ENONFINITE if any total is NaN or Inf. */
+int strm_conserved_totals(strm_ctx* ctx, const double* w, double out_host[5]);
+
+/* Simulated time accumulated by strm_rk_step/strm_advance_n and the last dt. Synchronises. */
+int strm_get_time(strm_ctx* ctx, double* t_host, double* dt_host);
+
+/* Set the simulated time (and reset the last dt to 0). Stream-ordered. */
+int strm_set_time(strm_ctx* ctx, double t);
+
+/* Sensor diagnostics for parity checks: theta and node divergence at the interior nodes
+ * (device, N doubles each, nullable), and the WENO face flags (device bytes, nullable) in the
+ * layout x: [nz][ny][nx+1], y: [nz][ny+1][nx], z: [nz+1][ny][nx]; entry s along a direction
+ * is the interface between nodes s-1 and s. */
+int strm_sensor(strm_ctx* ctx, const double* w, double* theta, double* div,
+                unsigned char* flags_x, unsigned char* flags_y, unsigned char* flags_z);
+
+/* Number of WENO faces per direction in the last right-hand-side evaluation. Synchronises. */
+int strm_weno_counts(strm_ctx* ctx, long long counts_host[3]);
+
+/* Kernel classes of the per-kernel timing diagnostics. */
+enum {
+  STRM_K_PRIMS = 0, STRM_K_DT, STRM_K_GHOST_PRIMS, STRM_K_SENSOR, STRM_K_GHOST_SENSOR,
+  STRM_K_FACES_X, STRM_K_FACES_Y, STRM_K_FACES_Z, STRM_K_WENO_X, STRM_K_WENO_Y, STRM_K_WENO_Z,
+  STRM_K_ASSEMBLE, STRM_K_FORCE, STRM_K_RK_UPDATE, STRM_K_COUNT
+};
+
+/* Short name of kernel class k ("" if out of range). */
+const char* strm_kernel_name(int k);
+
+/* Turn per-kernel timing on or off and reset its accumulators. While on, every kernel the
+ * context launches is bracketed by a CUDA event pair on the context's stream and
+ * strm_advance_n launches eagerly instead of replaying its graph; the WENO face counts of
+ * each evaluation are read back (which synchronises). Diagnostics only. */
+int strm_timing(strm_ctx* ctx, int enable);
+
+/* Accumulated milliseconds and launches per kernel class (arrays of STRM_K_COUNT, nullable)
+ * and WENO faces processed per direction (array of 3, nullable) since strm_timing.
+ * Synchronises the stream. */
+int strm_timing_read(strm_ctx* ctx, double* ms_host, long long* launches_host,
+                     long long* weno_faces_host);
+
+/* Total kernels this context has launched (graph replays count every kernel in the graph). */
+int strm_launch_count(strm_ctx* ctx, long long* launches_host);
+
+/* Release the context (not the caller's buffers). Safe on NULL. */
+void strm_destroy(strm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,240 @@
+"""Thin Python binding of libstrm.so (include/strm.h): argument marshalling only.
+
+Every step of the right-hand side and of the RK update runs in the library's CUDA kernels; this
+module converts a workload description into the ABI structs, allocates the caller-owned
+workspace and state buffers with torch on the current CUDA device, and passes raw pointers and
+the current torch stream. It raises if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstrm.so")
+
+STRM_OK = 0
+_STATUS = {-1: "EINVAL", -2: "ECUDA", -3: "ENONFINITE", -4: "ENOMEM", -5: "ETIMEOUT"}
+WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
+VISC_LAWS = {"power": 0, "sutherland": 1}
+
+
+class StrmError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} -> {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("y_map", ctypes.c_int), ("beta", ctypes.c_double)]
+
+
+class Phys(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("r_gas", ctypes.c_double), ("visc_law", ctypes.c_int),
+                ("mu_ref", ctypes.c_double), ("t_ref", ctypes.c_double),
+                ("visc_exp", ctypes.c_double), ("suth_s", ctypes.c_double),
+                ("t_wall", ctypes.c_double), ("forcing", ctypes.c_int)]
+
+
+class Scheme(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("weno_mode", ctypes.c_int),
+                ("theta_thr", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("u0", ctypes.c_double), ("l0", ctypes.c_double),
+                ("convective", ctypes.c_int), ("viscous", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+# every symbol include/strm.h declares, with its ctypes signature
+_P = ctypes.POINTER
+_vp, _d, _i, _sz = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "strm_last_error": ([], ctypes.c_char_p),
+    "strm_workspace_bytes": ([_P(Grid), _P(Scheme)], _sz),
+    "strm_init_grid": ([_P(_vp), _P(Grid), _P(Phys), _P(Scheme), _vp, _sz, _vp], _i),
+    "strm_set_bc": ([_vp, _i, _i, _vp, _i], _i),
+    "strm_compute_rhs": ([_vp, _vp, _vp], _i),
+    "strm_rk_step": ([_vp, _vp, _vp, _d, _d], _i),
+    "strm_advance_n": ([_vp, _vp, _vp, _i, _d, _d], _i),
+    "strm_advance_n_host": ([_vp, _vp, _vp, _vp, _i, _d, _d], _i),
+    "strm_conserved_totals": ([_vp, _vp, _P(_d)], _i),
+    "strm_get_time": ([_vp, _P(_d), _P(_d)], _i),
+    "strm_set_time": ([_vp, _d], _i),
+    "strm_sensor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "strm_weno_counts": ([_vp, _P(ctypes.c_longlong)], _i),
+    "strm_kernel_name": ([_i], ctypes.c_char_p),
+    "strm_timing": ([_vp, _i], _i),
+    "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
+    "strm_launch_count": ([_vp, _P(ctypes.c_longlong)], _i),
+    "strm_destroy": ([_vp], None),
+}
+K_COUNT = 14
+
+
+def lib():
+    """Load libstrm.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(fn, rc):
+    if rc != STRM_OK:
+        raise StrmError(fn, rc, lib().strm_last_error().decode())
+
+
+def structs(case):
+    """ABI structs for a workload (``inputs.Case`` or an object with the same attributes)."""
+    beta = getattr(case, "beta", 0.0) or 0.0
+    g = Grid(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, 1 if beta > 0 else 0, beta)
+    p = Phys(case.gamma, case.prandtl, case.r_gas, VISC_LAWS[getattr(case, "visc_law", "power")],
+             case.mu_ref, getattr(case, "t_ref", 1.0), getattr(case, "visc_exp", 0.76),
+             getattr(case, "suth_s", 0.0), getattr(case, "t_wall", 1.0),
+             int(bool(getattr(case, "forcing", False))))
+    wm = getattr(case, "weno_mode", "sensor")
+    s = Scheme(getattr(case, "L", 3), WENO_MODES[wm] if isinstance(wm, str) else int(wm),
+               getattr(case, "theta_thr", 0.05), getattr(case, "weno_eps", 1e-6),
+               getattr(case, "u0", 1.0), getattr(case, "l0", 1.0),
+               int(bool(getattr(case, "convective", True))),
+               int(bool(getattr(case, "viscous", True))), 0)
+    return g, p, s
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A context of the CUDA library on the current device and torch stream.
+
+    State tensors are float64 CUDA tensors of shape [5, nz, ny, nx] (contiguous).
+    """
+
+    def __init__(self, case, device=None, stream=None):
+        self.case = case
+        self.device = torch.device(device if device is not None else "cuda")
+        self.g, self.p, self.s = structs(case)
+        L = lib()
+        nbytes = L.strm_workspace_bytes(ctypes.byref(self.g), ctypes.byref(self.s))
+        if nbytes == 0:
+            raise StrmError("strm_workspace_bytes", -1, "invalid grid or scheme")
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = ctypes.c_void_p()
+        _check("strm_init_grid", L.strm_init_grid(
+            ctypes.byref(ctx), ctypes.byref(self.g), ctypes.byref(self.p), ctypes.byref(self.s),
+            _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.ctx = ctx
+        if getattr(case, "y_wall", False):
+            _check("strm_set_bc", L.strm_set_bc(self.ctx, 0, 1, None, 0))
+
+    @property
+    def shape(self):
+        return (5, self.case.nz, self.case.ny, self.case.nx)
+
+    def _state(self, w):
+        if not (w.is_cuda and w.dtype == torch.float64 and w.is_contiguous()
+                and tuple(w.shape) == self.shape):
+            raise ValueError(f"state must be a contiguous float64 CUDA tensor of shape {self.shape}")
+        return w
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=torch.float64, device=self.device)
+
+    def compute_rhs(self, w, out=None):
+        out = self.empty() if out is None else out
+        _check("strm_compute_rhs", lib().strm_compute_rhs(self.ctx, _ptr(self._state(w)),
+                                                          _ptr(self._state(out))))
+        return out
+
+    def rk_step(self, w, r_old, dt=0.0, cfl=None):
+        cfl = self.case.cfl if cfl is None else cfl
+        _check("strm_rk_step", lib().strm_rk_step(self.ctx, _ptr(self._state(w)),
+                                                  _ptr(self._state(r_old)), dt, cfl))
+
+    def advance_n(self, w, r_old, nsteps, dt=0.0, cfl=None):
+        cfl = self.case.cfl if cfl is None else cfl
+        _check("strm_advance_n", lib().strm_advance_n(self.ctx, _ptr(self._state(w)),
+                                                      _ptr(self._state(r_old)), nsteps, dt, cfl))
+
+    def advance_n_host(self, w_host, w, r_old, nsteps, dt=0.0, cfl=None):
+        """Host-buffer path: w_host (CPU float64, ideally pinned) -> device -> n steps -> w_host."""
+        cfl = self.case.cfl if cfl is None else cfl
+        if w_host.device.type != "cpu" or w_host.dtype != torch.float64 or not w_host.is_contiguous():
+            raise ValueError("w_host must be a contiguous CPU float64 tensor")
+        _check("strm_advance_n_host", lib().strm_advance_n_host(
+            self.ctx, _ptr(w_host), _ptr(self._state(w)), _ptr(self._state(r_old)), nsteps, dt, cfl))
+
+    def totals(self, w):
+        out = (ctypes.c_double * 5)()
+        _check("strm_conserved_totals", lib().strm_conserved_totals(self.ctx, _ptr(self._state(w)), out))
+        return list(out)
+
+    def time(self):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        _check("strm_get_time", lib().strm_get_time(self.ctx, ctypes.byref(t), ctypes.byref(dt)))
+        return t.value, dt.value
+
+    def set_time(self, t):
+        _check("strm_set_time", lib().strm_set_time(self.ctx, float(t)))
+
+    def sensor(self, w):
+        """(theta, div, flags_x, flags_y, flags_z) as CUDA tensors (flag layout of strm.h)."""
+        c = self.case
+        th = torch.empty((c.nz, c.ny, c.nx), dtype=torch.float64, device=self.device)
+        dv = torch.empty_like(th)
+        fx = torch.empty((c.nz, c.ny, c.nx + 1), dtype=torch.uint8, device=self.device)
+        fy = torch.empty((c.nz, c.ny + 1, c.nx), dtype=torch.uint8, device=self.device)
+        fz = torch.empty((c.nz + 1, c.ny, c.nx), dtype=torch.uint8, device=self.device)
+        _check("strm_sensor", lib().strm_sensor(self.ctx, _ptr(self._state(w)), _ptr(th), _ptr(dv),
+                                                _ptr(fx), _ptr(fy), _ptr(fz)))
+        return th, dv, fx, fy, fz
+
+    def weno_counts(self):
+        out = (ctypes.c_longlong * 3)()
+        _check("strm_weno_counts", lib().strm_weno_counts(self.ctx, out))
+        return list(out)
+
+    def timing(self, enable=True):
+        _check("strm_timing", lib().strm_timing(self.ctx, int(bool(enable))))
+
+    def timing_read(self):
+        """{kernel name: (total ms, launches)} and WENO faces per direction since timing()."""
+        ms = (ctypes.c_double * K_COUNT)()
+        n = (ctypes.c_longlong * K_COUNT)()
+        wf = (ctypes.c_longlong * 3)()
+        _check("strm_timing_read", lib().strm_timing_read(self.ctx, ms, n, wf))
+        names = [lib().strm_kernel_name(k).decode() for k in range(K_COUNT)]
+        return {names[k]: (ms[k], n[k]) for k in range(K_COUNT)}, list(wf)
+
+    def launch_count(self):
+        v = ctypes.c_longlong()
+        _check("strm_launch_count", lib().strm_launch_count(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().strm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

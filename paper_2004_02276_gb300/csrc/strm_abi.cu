@@ -1,0 +1,583 @@
+// C ABI of the library (declared in include/strm.h): context, workspace layout, stage
+// sequencing on the caller's stream, and the CUDA graph replayed by strm_advance_n.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/strm.h"
+#include "strm_dev.cuh"
+#include "strm_launch.h"
+
+using namespace strm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define STRM_CK(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(STRM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define STRM_CK_LAUNCH()                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                   \
+    if (e_ != cudaSuccess) return fail(STRM_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Wray RK3 (Eq. RK); alpha_1 is printed +17/60 in the paper, read as -17/60 (first-order
+// consistency requires sum alpha + sum beta = 1).
+const double kAlpha[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+const double kBeta[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  Dims d;
+  size_t off_prim[11];
+  size_t off_fh[3];
+  size_t off_R, off_wl[3], off_wcount, off_red, off_scal, off_metric;
+  size_t total;
+};
+
+bool valid_grid(const strm_grid* g) {
+  return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->lx > 0 && g->ly > 0 && g->lz > 0 &&
+         (g->y_map == STRM_MAP_UNIFORM || (g->y_map == STRM_MAP_TANH && g->beta > 0));
+}
+
+bool valid_scheme(const strm_scheme* s) {
+  return s && (s->L == 2 || s->L == 3) && s->weno_mode >= 0 && s->weno_mode <= 2 &&
+         s->precision == STRM_PREC_FP64 && s->weno_eps > 0 && s->l0 > 0;
+}
+
+Layout make_layout(const strm_grid* g) {
+  Layout L{};
+  Dims& d = L.d;
+  d.nx = g->nx;
+  d.ny = g->ny;
+  d.nz = g->nz;
+  d.px = ((g->nx + GX + G) + 3) / 4 * 4;
+  d.py = g->ny + 2 * G;
+  d.pz = g->nz + 2 * G;
+  d.plane = (long long)d.px * d.py;
+  d.ng = d.plane * d.pz;
+  d.N = (long long)d.nx * d.ny * d.nz;
+  d.nf[0] = (long long)(d.nx + 1) * d.ny * d.nz;
+  d.nf[1] = (long long)d.nx * (d.ny + 1) * d.nz;
+  d.nf[2] = (long long)d.nx * d.ny * (d.nz + 1);
+  size_t off = 0;
+  for (int f = 0; f < 11; ++f) {
+    L.off_prim[f] = off;
+    off = align_up(off + sizeof(double) * (size_t)d.ng);
+  }
+  for (int dir = 0; dir < 3; ++dir) {
+    L.off_fh[dir] = off;
+    off = align_up(off + sizeof(double) * 5 * (size_t)d.nf[dir]);
+  }
+  L.off_R = off;
+  off = align_up(off + sizeof(double) * 5 * (size_t)d.N);
+  for (int dir = 0; dir < 3; ++dir) {
+    L.off_wl[dir] = off;
+    off = align_up(off + sizeof(int) * (size_t)d.nf[dir]);
+  }
+  L.off_wcount = off;
+  off = align_up(off + 4 * sizeof(unsigned));
+  L.off_red = off;
+  off = align_up(off + sizeof(double) * (5 * (size_t)reduce_blocks(d) + 64));
+  L.off_scal = off;
+  off = align_up(off + sizeof(double) * kScalCount);
+  L.off_metric = off;
+  off = align_up(off + sizeof(double) * 4 * (size_t)d.ny);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct strm_ctx {
+  strm_grid g;
+  strm_phys p;
+  strm_scheme s;
+  Dims d;
+  Consts C;
+  Bufs B;
+  cudaStream_t stream = nullptr;
+  int weno_grid = 0;
+  std::vector<double> metric_host;  // kept alive for the asynchronous upload
+  double time_host[2] = {0.0, 0.0};
+  // graph of one RK step, replayed by strm_advance_n
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double* g_w = nullptr;
+  double* g_r = nullptr;
+  double g_dt = 0.0, g_cfl = 0.0;
+  long long graph_kernels = 0;
+  // launch accounting and the optional per-kernel event timing
+  long long launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> events;
+  struct Rec {
+    int cls, e0, e1;
+  };
+  std::vector<Rec> recs;
+  double kms[STRM_K_COUNT] = {};
+  long long klaunch[STRM_K_COUNT] = {};
+  long long weno_faces[3] = {};
+};
+
+namespace {
+
+void set_consts(strm_ctx* x) {
+  Consts& C = x->C;
+  const strm_phys& p = x->p;
+  const strm_scheme& s = x->s;
+  const strm_grid& g = x->g;
+  C.gamma = p.gamma;
+  C.gm1 = p.gamma - 1.0;
+  C.r_gas = p.r_gas;
+  C.inv_r = 1.0 / p.r_gas;
+  C.cv = p.r_gas / (p.gamma - 1.0);
+  C.inv_cv = 1.0 / C.cv;
+  C.cp = p.gamma * C.cv;
+  C.cp_pr = C.cp / p.prandtl;
+  C.mu_ref = p.mu_ref;
+  C.inv_tref = 1.0 / p.t_ref;
+  C.visc_exp = p.visc_exp;
+  C.suth_s = p.suth_s;
+  C.t_wall = p.t_wall;
+  C.visc_law = p.visc_law;
+  C.forcing = p.forcing ? 1 : 0;
+  C.L = s.L;
+  C.weno_mode = s.weno_mode;
+  C.convective = s.convective ? 1 : 0;
+  C.viscous = s.viscous ? 1 : 0;
+  for (int l = 0; l < 4; ++l) C.a[l] = C.b[l] = 0.0;
+  // central coefficients of order 2L: first derivative a_l, second derivative b_l with
+  // f'' ~ sum_l b_l (f_{+l} + f_{-l} - 2 f_0)/h^2 (Section 2.1)
+  if (s.L == 3) {
+    C.a[1] = 3.0 / 4.0; C.a[2] = -3.0 / 20.0; C.a[3] = 1.0 / 60.0;
+    C.b[1] = 3.0 / 2.0; C.b[2] = -3.0 / 20.0; C.b[3] = 1.0 / 90.0;
+  } else {
+    C.a[1] = 2.0 / 3.0; C.a[2] = -1.0 / 12.0;
+    C.b[1] = 4.0 / 3.0; C.b[2] = -1.0 / 12.0;
+  }
+  C.theta_thr = s.theta_thr;
+  C.weno_eps = s.weno_eps;
+  C.sens_eps = (s.u0 / s.l0) * (s.u0 / s.l0);
+  double dx = g.lx / g.nx, dz = g.lz / g.nz;
+  C.inv_dx = 1.0 / dx;
+  C.inv_dz = 1.0 / dz;
+  C.inv_dx2 = C.inv_dx * C.inv_dx;
+  C.inv_dz2 = C.inv_dz * C.inv_dz;
+}
+
+// Wall-normal metrics at the nodes eta_j = (j + 1/2)/ny of y = (ly/2) tanh(beta(2 eta - 1))/tanh(beta)
+// (uniform: y = ly (eta - 1/2)): 1/(y_eta deta), its square, y_etaeta/(y_eta^3 deta) and the node
+// volume dx (y_eta deta) dz.
+void build_metrics(strm_ctx* x) {
+  const strm_grid& g = x->g;
+  int ny = g.ny;
+  double deta = 1.0 / ny, dx = g.lx / g.nx, dz = g.lz / g.nz;
+  x->metric_host.assign(4 * (size_t)ny, 0.0);
+  double vt = 0.0;
+  for (int j = 0; j < ny; ++j) {
+    double eta = (j + 0.5) * deta, ye, yee;
+    if (g.y_map == STRM_MAP_TANH) {
+      double A = 0.5 * g.ly / std::tanh(g.beta);
+      double th = std::tanh(g.beta * (2.0 * eta - 1.0));
+      double sech2 = 1.0 - th * th;
+      ye = 2.0 * g.beta * A * sech2;
+      yee = -8.0 * g.beta * g.beta * A * sech2 * th;
+    } else {
+      ye = g.ly;
+      yee = 0.0;
+    }
+    double ih = 1.0 / (ye * deta);
+    x->metric_host[j] = ih;
+    x->metric_host[ny + j] = ih * ih;
+    x->metric_host[2 * ny + j] = yee / (ye * ye * ye * deta);
+    x->metric_host[3 * ny + j] = dx * (ye * deta) * dz;
+    vt += x->metric_host[3 * ny + j];
+  }
+  x->C.vtot = vt * g.nx * g.nz;
+}
+
+const char* const kKernelNames[STRM_K_COUNT] = {
+    "prims", "dt_finalize", "ghost_prims", "sensor", "ghost_sensor", "faces_x", "faces_y",
+    "faces_z", "weno_x", "weno_y", "weno_z", "assemble", "force_finalize", "rk_update"};
+
+int take_event(strm_ctx* x, size_t idx) {
+  while (x->events.size() <= idx) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    x->events.push_back(e);
+  }
+  return (int)idx;
+}
+
+// Fold recorded event pairs into the per-kernel totals (synchronises the stream).
+int fold_timing(strm_ctx* x) {
+  if (x->recs.empty()) return STRM_OK;
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  for (const auto& r : x->recs) {
+    float ms = 0.f;
+    STRM_CK(cudaEventElapsedTime(&ms, x->events[r.e0], x->events[r.e1]));
+    x->kms[r.cls] += ms;
+    x->klaunch[r.cls] += 1;
+  }
+  x->recs.clear();
+  return STRM_OK;
+}
+
+// Launch accounting around one kernel launch; with timing on, an event pair brackets it.
+struct LaunchScope {
+  strm_ctx* x;
+  cudaStream_t st;
+  int cls, e0 = -1;
+  LaunchScope(strm_ctx* x_, cudaStream_t st_, int cls_) : x(x_), st(st_), cls(cls_) {
+    if (x->timing) {
+      if (x->recs.size() >= 2048) fold_timing(x);
+      e0 = take_event(x, 2 * x->recs.size());
+      if (e0 >= 0) cudaEventRecord(x->events[e0], st);
+    }
+  }
+  ~LaunchScope() {
+    x->launches += 1;
+    if (e0 >= 0) {
+      int e1 = take_event(x, e0 + 1);
+      if (e1 >= 0) {
+        cudaEventRecord(x->events[e1], st);
+        x->recs.push_back({cls, e0, e1});
+      }
+    }
+  }
+};
+
+#define STRM_LAUNCH(cls, expr) \
+  do {                         \
+    LaunchScope ls_(x, st, cls); \
+    expr;                      \
+  } while (0)
+
+// One right-hand-side evaluation into R (stream order). With dt_mode, stage-0 work also sets the
+// step: dt_fixed > 0 is taken as is, otherwise the CFL step from the primitive pass.
+int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cfl, double dt_fixed,
+                cudaStream_t st) {
+  const Dims& d = x->d;
+  const Consts& C = x->C;
+  const Bufs& B = x->B;
+  STRM_CK(cudaMemsetAsync(B.wcount, 0, 4 * sizeof(unsigned), st));
+  STRM_LAUNCH(STRM_K_PRIMS, launch_prims(d, C, B, w, dt_mode && dt_fixed <= 0.0, st));
+  if (dt_mode) STRM_LAUNCH(STRM_K_DT, launch_dt_finalize(d, B, cfl, dt_fixed, st));
+  STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
+  STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, st));
+  STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
+  if (C.convective) {
+    for (int dir = 0; dir < 3; ++dir)
+      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, st));
+    if (C.weno_mode != STRM_WENO_OFF) {
+      for (int dir = 0; dir < 3; ++dir)
+        STRM_LAUNCH(STRM_K_WENO_X + dir, launch_weno_dir(d, C, B, dir, x->weno_grid, st));
+      if (x->timing) {  // pageable destination: the copy completes before the call returns
+        unsigned c[4];
+        STRM_CK(cudaMemcpyAsync(c, B.wcount, sizeof(c), cudaMemcpyDeviceToHost, st));
+        STRM_CK(cudaStreamSynchronize(st));
+        for (int dir = 0; dir < 3; ++dir) x->weno_faces[dir] += c[dir];
+      }
+    }
+  }
+  STRM_LAUNCH(STRM_K_ASSEMBLE, launch_assemble(d, C, B, R, st));
+  if (C.forcing) STRM_LAUNCH(STRM_K_FORCE, launch_force_finalize(d, C, B, st));
+  STRM_CK_LAUNCH();
+  return STRM_OK;
+}
+
+int enqueue_step(strm_ctx* x, double* w, double* r_old, double dt, double cfl, cudaStream_t st) {
+  for (int stage = 0; stage < 3; ++stage) {
+    int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st);
+    if (rc) return rc;
+    STRM_LAUNCH(STRM_K_RK_UPDATE,
+                launch_rk_update(x->d, x->C, x->B, w, r_old, kAlpha[stage], kBeta[stage], st));
+  }
+  STRM_CK_LAUNCH();
+  return STRM_OK;
+}
+
+int check_step_args(const strm_ctx* x, const double* w, const double* r_old, double dt, double cfl) {
+  if (!x || !w || !r_old) return fail(STRM_EINVAL, "null context or buffer");
+  if (w == r_old) return fail(STRM_EINVAL, "w and r_old must not alias");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(STRM_EINVAL, "need dt > 0 or cfl > 0");
+  return STRM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* strm_last_error(void) { return g_last_error.c_str(); }
+
+size_t strm_workspace_bytes(const strm_grid* g, const strm_scheme* s) {
+  if (!valid_grid(g) || !valid_scheme(s)) return 0;
+  return make_layout(g).total;
+}
+
+int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const strm_scheme* s,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return fail(STRM_EINVAL, "ctx out-pointer is null");
+  *out = nullptr;
+  if (!valid_grid(g)) return fail(STRM_EINVAL, "invalid grid (sizes >= 1, lengths > 0, tanh needs beta > 0)");
+  if (!valid_scheme(s)) return fail(STRM_EINVAL, "invalid scheme (L in {2,3}, weno_mode in 0..2, fp64)");
+  if (!p || !(p->gamma > 1.0) || !(p->r_gas > 0) || !(p->prandtl > 0) || !(p->mu_ref >= 0) ||
+      !(p->t_ref > 0) || !(p->t_wall > 0) || p->visc_law < 0 || p->visc_law > 1)
+    return fail(STRM_EINVAL, "invalid physical parameters");
+  Layout L = make_layout(g);
+  if (!workspace) return fail(STRM_EINVAL, "workspace is null");
+  if (((uintptr_t)workspace & 255) != 0) return fail(STRM_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total)
+    return fail(STRM_ENOMEM, "workspace too small: need " + std::to_string(L.total) + " bytes");
+  strm_ctx* x = new (std::nothrow) strm_ctx();
+  if (!x) return fail(STRM_ENOMEM, "host allocation failed");
+  x->g = *g;
+  x->p = *p;
+  x->s = *s;
+  x->d = L.d;
+  x->stream = (cudaStream_t)stream;
+  set_consts(x);
+  x->C.wall_y = 0;
+  char* ws = (char*)workspace;
+  double** prim[11] = {&x->B.rho, &x->B.u, &x->B.v, &x->B.w, &x->B.p, &x->B.T,
+                       &x->B.H,   &x->B.c, &x->B.mu, &x->B.theta, &x->B.div};
+  for (int f = 0; f < 11; ++f) *prim[f] = (double*)(ws + L.off_prim[f]);
+  for (int dir = 0; dir < 3; ++dir) {
+    x->B.fh[dir] = (double*)(ws + L.off_fh[dir]);
+    x->B.wl[dir] = (int*)(ws + L.off_wl[dir]);
+  }
+  x->B.R = (double*)(ws + L.off_R);
+  x->B.wcount = (unsigned*)(ws + L.off_wcount);
+  x->B.red = (double*)(ws + L.off_red);
+  x->B.scal = (double*)(ws + L.off_scal);
+  double* met = (double*)(ws + L.off_metric);
+  x->B.inv_hy = met;
+  x->B.c2y = met + g->ny;
+  x->B.c1y = met + 2 * g->ny;
+  x->B.vol = met + 3 * g->ny;
+  build_metrics(x);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 4 * g->ny,
+                        cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->B.scal, 0, sizeof(double) * kScalCount, x->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->B.wcount, 0, 4 * sizeof(unsigned), x->stream);
+  if (e != cudaSuccess) {
+    delete x;
+    return fail(STRM_ECUDA, std::string("init: ") + cudaGetErrorString(e));
+  }
+  x->weno_grid = sms * 8;
+  *out = x;
+  return STRM_OK;
+}
+
+int strm_set_bc(strm_ctx* x, int face, int kind, const double* params, int nparams) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  if (face != STRM_FACE_YMIN_YMAX) return fail(STRM_EINVAL, "only the y faces take a boundary kind");
+  if (params || nparams) return fail(STRM_EINVAL, "params are reserved (NULL, 0)");
+  if (kind == STRM_BC_PERIODIC) {
+    x->C.wall_y = 0;
+  } else if (kind == STRM_BC_WALL_ISOTHERMAL) {
+    if (x->g.ny < G) return fail(STRM_EINVAL, "walls need ny >= 3");
+    x->C.wall_y = 1;
+  } else {
+    return fail(STRM_EINVAL, "unknown boundary kind");
+  }
+  if (x->gexec) {  // the captured graph holds the old constants
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
+  return STRM_OK;
+}
+
+int strm_compute_rhs(strm_ctx* x, const double* w, double* rhs) {
+  if (!x || !w || !rhs) return fail(STRM_EINVAL, "null context or buffer");
+  if (w == rhs) return fail(STRM_EINVAL, "w and rhs must not alias");
+  int rc = enqueue_rhs(x, w, rhs, false, 0.0, 0.0, x->stream);
+  if (rc) return rc;
+  cudaStream_t st = x->stream;
+  if (x->C.forcing) STRM_LAUNCH(STRM_K_FORCE, launch_apply_forcing(x->d, x->B, rhs, st));
+  STRM_CK_LAUNCH();
+  return STRM_OK;
+}
+
+int strm_rk_step(strm_ctx* x, double* w, double* r_old, double dt, double cfl) {
+  int rc = check_step_args(x, w, r_old, dt, cfl);
+  if (rc) return rc;
+  return enqueue_step(x, w, r_old, dt, cfl, x->stream);
+}
+
+int strm_advance_n(strm_ctx* x, double* w, double* r_old, int nsteps, double dt, double cfl) {
+  int rc = check_step_args(x, w, r_old, dt, cfl);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(STRM_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return STRM_OK;
+  if (x->timing) {  // event timing needs eager launches
+    for (int n = 0; n < nsteps; ++n) {
+      int erc = enqueue_step(x, w, r_old, dt, cfl, x->stream);
+      if (erc) return erc;
+    }
+    return STRM_OK;
+  }
+  if (!x->gexec || x->g_w != w || x->g_r != r_old || x->g_dt != dt || x->g_cfl != cfl) {
+    if (x->gexec) {
+      STRM_CK(cudaGraphExecDestroy(x->gexec));
+      x->gexec = nullptr;
+    }
+    if (!x->cap) STRM_CK(cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking));
+    // capture on a private stream; the graph itself is launched on the caller's stream
+    STRM_CK(cudaStreamBeginCapture(x->cap, cudaStreamCaptureModeThreadLocal));
+    long long before = x->launches;
+    int erc = enqueue_step(x, w, r_old, dt, cfl, x->cap);
+    x->graph_kernels = x->launches - before;
+    x->launches = before;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(x->cap, &graph);
+    if (erc) {
+      if (graph) cudaGraphDestroy(graph);
+      return erc;
+    }
+    if (e != cudaSuccess) return fail(STRM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&x->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(STRM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    x->g_w = w;
+    x->g_r = r_old;
+    x->g_dt = dt;
+    x->g_cfl = cfl;
+  }
+  for (int n = 0; n < nsteps; ++n) STRM_CK(cudaGraphLaunch(x->gexec, x->stream));
+  x->launches += x->graph_kernels * nsteps;
+  return STRM_OK;
+}
+
+int strm_advance_n_host(strm_ctx* x, double* w_host, double* w, double* r_old, int nsteps, double dt,
+                        double cfl) {
+  if (!x || !w_host) return fail(STRM_EINVAL, "null context or host buffer");
+  size_t bytes = sizeof(double) * 5 * (size_t)x->d.N;
+  STRM_CK(cudaMemcpyAsync(w, w_host, bytes, cudaMemcpyHostToDevice, x->stream));
+  int rc = strm_advance_n(x, w, r_old, nsteps, dt, cfl);
+  if (rc) return rc;
+  STRM_CK(cudaMemcpyAsync(w_host, w, bytes, cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  return STRM_OK;
+}
+
+int strm_conserved_totals(strm_ctx* x, const double* w, double out_host[5]) {
+  if (!x || !w || !out_host) return fail(STRM_EINVAL, "null argument");
+  launch_totals(x->d, x->B, w, x->stream);
+  STRM_CK_LAUNCH();
+  STRM_CK(cudaMemcpyAsync(out_host, x->B.scal + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  for (int m = 0; m < 5; ++m)
+    if (!std::isfinite(out_host[m])) return fail(STRM_ENONFINITE, "non-finite conserved total");
+  return STRM_OK;
+}
+
+int strm_get_time(strm_ctx* x, double* t_host, double* dt_host) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  double v[2];
+  STRM_CK(cudaMemcpyAsync(&v[0], x->B.scal + kScalTime, sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaMemcpyAsync(&v[1], x->B.scal + kScalDt, sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  if (t_host) *t_host = v[0];
+  if (dt_host) *dt_host = v[1];
+  return STRM_OK;
+}
+
+int strm_set_time(strm_ctx* x, double t) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  x->time_host[0] = t;
+  x->time_host[1] = 0.0;
+  STRM_CK(cudaMemcpyAsync(x->B.scal + kScalTime, &x->time_host[0], sizeof(double), cudaMemcpyHostToDevice, x->stream));
+  STRM_CK(cudaMemcpyAsync(x->B.scal + kScalDt, &x->time_host[1], sizeof(double), cudaMemcpyHostToDevice, x->stream));
+  return STRM_OK;
+}
+
+int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsigned char* fx,
+                unsigned char* fy, unsigned char* fz) {
+  if (!x || !w) return fail(STRM_EINVAL, "null context or state");
+  launch_prims(x->d, x->C, x->B, w, false, x->stream);
+  launch_ghost_prims(x->d, x->C, x->B, x->stream);
+  launch_sensor(x->d, x->C, x->B, x->stream);
+  if (theta) launch_export_interior(x->d, x->B.theta, theta, x->stream);
+  if (div) launch_export_interior(x->d, x->B.div, div, x->stream);
+  unsigned char* fl[3] = {fx, fy, fz};
+  for (int dir = 0; dir < 3; ++dir)
+    if (fl[dir]) launch_flags(x->d, x->C, x->B, dir, fl[dir], x->stream);
+  STRM_CK_LAUNCH();
+  return STRM_OK;
+}
+
+int strm_weno_counts(strm_ctx* x, long long counts_host[3]) {
+  if (!x || !counts_host) return fail(STRM_EINVAL, "null argument");
+  unsigned c[4];
+  STRM_CK(cudaMemcpyAsync(c, x->B.wcount, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  for (int d = 0; d < 3; ++d) counts_host[d] = c[d];
+  return STRM_OK;
+}
+
+const char* strm_kernel_name(int k) {
+  return (k >= 0 && k < STRM_K_COUNT) ? kKernelNames[k] : "";
+}
+
+int strm_timing(strm_ctx* x, int enable) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  int rc = fold_timing(x);
+  if (rc) return rc;
+  for (int k = 0; k < STRM_K_COUNT; ++k) {
+    x->kms[k] = 0.0;
+    x->klaunch[k] = 0;
+  }
+  for (int d = 0; d < 3; ++d) x->weno_faces[d] = 0;
+  x->timing = enable != 0;
+  return STRM_OK;
+}
+
+int strm_timing_read(strm_ctx* x, double* ms_host, long long* launches_host, long long* weno_faces_host) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  int rc = fold_timing(x);
+  if (rc) return rc;
+  for (int k = 0; k < STRM_K_COUNT; ++k) {
+    if (ms_host) ms_host[k] = x->kms[k];
+    if (launches_host) launches_host[k] = x->klaunch[k];
+  }
+  if (weno_faces_host)
+    for (int d = 0; d < 3; ++d) weno_faces_host[d] = x->weno_faces[d];
+  return STRM_OK;
+}
+
+int strm_launch_count(strm_ctx* x, long long* launches_host) {
+  if (!x || !launches_host) return fail(STRM_EINVAL, "null argument");
+  *launches_host = x->launches;
+  return STRM_OK;
+}
+
+void strm_destroy(strm_ctx* x) {
+  if (!x) return;
+  for (cudaEvent_t e : x->events) cudaEventDestroy(e);
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  if (x->cap) cudaStreamDestroy(x->cap);
+  delete x;
+}
+
+}  // extern "C"

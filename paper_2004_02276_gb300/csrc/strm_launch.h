@@ -1,0 +1,29 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "strm_dev.cuh"
+
+namespace strm {
+
+int reduce_blocks(const Dims& d);
+void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w, bool want_cfl,
+                  cudaStream_t s);
+void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixed, cudaStream_t s);
+void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, cudaStream_t s);
+void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
+void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, cudaStream_t s);
+void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+void launch_rk_update(const Dims& d, const Consts& C, const Bufs& B, double* w, double* r_old,
+                      double alpha, double beta, cudaStream_t s);
+void launch_apply_forcing(const Dims& d, const Bufs& B, double* rhs, cudaStream_t s);
+void launch_totals(const Dims& d, const Bufs& B, const double* w, cudaStream_t s);
+void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsigned char* out,
+                  cudaStream_t s);
+void launch_export_interior(const Dims& d, const double* src, double* dst, cudaStream_t s);
+
+}  // namespace strm

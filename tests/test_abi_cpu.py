@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every function that
+include/strm.h declares, and the binding's ctypes structs match the header's layout."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2004_02276_gb300 import binding, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "strm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(strm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return binding.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.SIGNATURES)
+
+
+def test_struct_field_counts_match_header():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for cname, py in (("strm_grid", binding.Grid), ("strm_phys", binding.Phys),
+                      ("strm_scheme", binding.Scheme)):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + cname + ";", text).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, names = decl.split(None, 1)
+            fields += [(typ, n.strip()) for n in names.split(",")]
+        assert [n for _, n in fields] == [f for f, _ in py._fields_], cname
+        for (typ, _), (_, ct) in zip(fields, py._fields_):
+            assert {"int": ctypes.c_int, "double": ctypes.c_double}[typ] == ct
+
+
+def test_workspace_bytes_rejects_invalid(lib):
+    g, p, s = binding.structs(inputs.C1)
+    ok = lib.strm_workspace_bytes(ctypes.byref(g), ctypes.byref(s))
+    assert ok > 0
+    for bad in (inputs.C1.replace(nx=0), inputs.C1.replace(L=4), inputs.C1.replace(lx=-1.0)):
+        gb, _, sb = binding.structs(bad)
+        assert lib.strm_workspace_bytes(ctypes.byref(gb), ctypes.byref(sb)) == 0
+    # the workspace grows with the grid
+    g2, _, s2 = binding.structs(inputs.C2)
+    assert lib.strm_workspace_bytes(ctypes.byref(g2), ctypes.byref(s2)) > 10 * ok
+
+
+def test_init_rejects_bad_arguments_before_any_cuda_call(lib):
+    g, p, s = binding.structs(inputs.C1)
+    ctx = ctypes.c_void_p()
+    # null workspace
+    rc = lib.strm_init_grid(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), ctypes.byref(s),
+                            None, 0, None)
+    assert rc == -1 and b"workspace" in lib.strm_last_error()
+    # misaligned workspace pointer (never dereferenced: rejected on the host)
+    rc = lib.strm_init_grid(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), ctypes.byref(s),
+                            ctypes.c_void_p(0x1008), 1 << 40, None)
+    assert rc == -1 and b"aligned" in lib.strm_last_error()
+    # too small
+    rc = lib.strm_init_grid(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), ctypes.byref(s),
+                            ctypes.c_void_p(0x1000), 16, None)
+    assert rc == -4
+    # bad physics
+    p.gamma = 1.0
+    rc = lib.strm_init_grid(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), ctypes.byref(s),
+                            ctypes.c_void_p(0x1000), 1 << 40, None)
+    assert rc == -1
+    assert lib.strm_set_bc(None, 0, 1, None, 0) == -1
+    lib.strm_destroy(None)

@@ -1,0 +1,207 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerance: relative L2 error <= 1e-12 per conserved field (the FP64 target); right-hand sides
+are compared element-wise against the field's largest magnitude (1e-12). WENO face flags are
+integer decisions taken in FP64 on both sides and must agree exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2004_02276_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def rel_l2(a, b):
+    return np.array([np.linalg.norm(a[m] - b[m]) / max(np.linalg.norm(b[m]), 1e-300)
+                     for m in range(5)])
+
+
+def rel_max(a, b):
+    return np.array([np.abs(a[m] - b[m]).max() / max(np.abs(b[m]).max(), 1e-300)
+                     for m in range(5)])
+
+
+def gpu(w):
+    return torch.from_numpy(np.ascontiguousarray(w)).cuda()
+
+
+CASES = {
+    "channel-c1-sensor": (inputs.C1, "channel"),
+    "channel-odd-sizes": (inputs.Case(nx=37, ny=29, nz=11), "channel"),
+    "channel-min-ny": (inputs.Case(nx=16, ny=3, nz=5), "channel"),
+    "periodic-central-L3": (inputs.Case(nx=20, ny=18, nz=14, y_wall=False, forcing=False,
+                                        weno_mode="off"), "random"),
+    "periodic-weno-all-L2": (inputs.Case(nx=20, ny=18, nz=14, y_wall=False, forcing=False,
+                                         weno_mode="all", L=2), "random"),
+    "periodic-sensor-inviscid": (inputs.Case(nx=24, ny=10, nz=9, y_wall=False, forcing=False,
+                                             viscous=False, theta_thr=0.6), "random"),
+    "uniform-2d-sutherland": (inputs.Case(nx=33, ny=1, nz=40, beta=0.0, y_wall=False,
+                                          forcing=False, visc_law="sutherland"), "random"),
+    "line-x-only": (inputs.Case(nx=50, ny=1, nz=1, beta=0.0, y_wall=False, forcing=False,
+                                weno_mode="all"), "random"),
+}
+
+
+def make_state(case, kind, seed=0):
+    return inputs.channel_state(case, seed) if kind == "channel" else inputs.random_state(case, seed)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_and_flags_match_oracle(name):
+    case, kind = CASES[name]
+    w0 = make_state(case, kind)
+    cfg = O.make_cfg(case)
+    ref = O.rhs(cfg, w0)
+    th_o, dv_o, fx_o, fy_o, fz_o = O.sensor(cfg, w0)
+    s = binding.Solver(case)
+    w = gpu(w0)
+    r = s.compute_rhs(w).cpu().numpy()
+    th, dv, fx, fy, fz = (t.cpu().numpy() for t in s.sensor(w))
+    s.close()
+    assert np.array_equal(fx, fx_o) and np.array_equal(fy, fy_o) and np.array_equal(fz, fz_o)
+    np.testing.assert_allclose(th, th_o, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(dv, dv_o, rtol=0, atol=1e-12 * max(1.0, np.abs(dv_o).max()))
+    err = rel_max(r, ref)
+    assert err.max() <= TOL, err
+
+
+def test_c1_twenty_steps_match_oracle():
+    """The FP64 target: relative L2 <= 1e-12 per conserved field after 20 CFL-0.8 steps."""
+    case = inputs.C1
+    w0 = inputs.channel_state(case, seed=0)
+    cfg = O.make_cfg(case)
+    wo, to, dts = O.advance(cfg, w0, case.steps, cfl=case.cfl)
+    s = binding.Solver(case)
+    w = gpu(w0)
+    r_old = torch.zeros_like(w)
+    for _ in range(case.steps):
+        s.rk_step(w, r_old, dt=0.0, cfl=case.cfl)
+    t, dt = s.time()
+    wg = w.cpu().numpy()
+    s.close()
+    err = rel_l2(wg, wo)
+    assert err.max() <= TOL, err
+    assert abs(t - to) <= 1e-13 * to and abs(dt - dts[-1]) <= 1e-13 * dts[-1]
+
+
+def test_graph_replay_equals_single_steps_bitwise():
+    case = inputs.Case(nx=32, ny=24, nz=16)
+    w0 = inputs.channel_state(case, seed=3)
+    s = binding.Solver(case)
+    a = gpu(w0)
+    ra = torch.zeros_like(a)
+    for _ in range(5):
+        s.rk_step(a, ra, cfl=0.8)
+    s.set_time(0.0)
+    b = gpu(w0)
+    rb = torch.zeros_like(b)
+    s.advance_n(b, rb, 5, cfl=0.8)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    # host-buffer variant gives the same state
+    h = torch.from_numpy(w0.copy()).pin_memory()
+    c = torch.empty_like(a)
+    rc = torch.zeros_like(a)
+    s.advance_n_host(h, c, rc, 5, cfl=0.8)
+    assert torch.equal(h.cuda(), a)
+    s.close()
+
+
+def test_fixed_dt_step_matches_oracle():
+    case = inputs.Case(nx=24, ny=20, nz=10, y_wall=False, forcing=False)
+    w0 = inputs.random_state(case, seed=5, amp_u=0.2)
+    cfg = O.make_cfg(case)
+    wo, _ = O.rk_step(cfg, w0, dt=1e-3)
+    s = binding.Solver(case)
+    w = gpu(w0)
+    r_old = torch.zeros_like(w)
+    s.rk_step(w, r_old, dt=1e-3)
+    err = rel_l2(w.cpu().numpy(), wo)
+    s.close()
+    assert err.max() <= TOL, err
+
+
+def test_totals_and_channel_invariants():
+    """Totals match the oracle; mass and bulk x-momentum stay constant on the GPU (staggered wall,
+    forcing each stage)."""
+    case = inputs.Case(nx=48, ny=32, nz=24)
+    w0 = inputs.channel_state(case, seed=2)
+    cfg = O.make_cfg(case)
+    s = binding.Solver(case)
+    w = gpu(w0)
+    t0 = np.array(s.totals(w))
+    # different summation orders over ~4e4 terms: agreement to the FP64 parity bar
+    np.testing.assert_allclose(t0, O.totals(cfg, w0), rtol=TOL)
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 10, cfl=0.8)
+    t1 = np.array(s.totals(w))
+    s.close()
+    assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
+    assert abs(t1[1] - t0[1]) <= 1e-13 * t0[1]
+
+
+def test_nonfinite_state_is_reported():
+    case = inputs.Case(nx=8, ny=6, nz=4)
+    w0 = inputs.channel_state(case, seed=1)
+    w0[4, 1, 2, 3] = np.nan
+    s = binding.Solver(case)
+    with pytest.raises(binding.StrmError) as e:
+        s.totals(gpu(w0))
+    assert e.value.code == -3
+    s.close()
+
+
+def test_invalid_calls_rejected():
+    case = inputs.Case(nx=8, ny=6, nz=4)
+    s = binding.Solver(case)
+    w = gpu(inputs.channel_state(case))
+    with pytest.raises(binding.StrmError):
+        binding._check("strm_compute_rhs",
+                       binding.lib().strm_compute_rhs(s.ctx, binding._ptr(w), binding._ptr(w)))
+    with pytest.raises(binding.StrmError):
+        s.rk_step(w, w)
+    with pytest.raises(ValueError):
+        s.compute_rhs(w.float())
+    s.close()
+
+
+@pytest.mark.slow
+def test_c2_full_size_rhs_and_step_match_oracle():
+    """The benchmark workload (256x192x128 channel), in the launch configuration the benchmark
+    times: the full right-hand side and one full RK3 step, every element against the oracle."""
+    case = inputs.C2
+    w0 = inputs.channel_state(case, seed=0)
+    cfg = O.make_cfg(case)
+    s = binding.Solver(case)
+    w = gpu(w0)
+    r = s.compute_rhs(w).cpu().numpy()
+    ref = O.rhs(cfg, w0)
+    err = rel_max(r, ref)
+    assert err.max() <= TOL, err
+    del ref, r
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 1, cfl=case.cfl)
+    wo, _ = O.rk_step(cfg, w0, cfl=case.cfl)
+    err = rel_l2(w.cpu().numpy(), wo)
+    assert err.max() <= TOL, err
+    # 20 more steps on the GPU alone: invariants that hold at any size
+    t0 = np.array(s.totals(w))
+    s.advance_n(w, r_old, 20, cfl=case.cfl)
+    t1 = np.array(s.totals(w))
+    s.close()
+    assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
+    assert abs(t1[1] - t0[1]) <= 1e-13 * t0[1]
