@@ -36,10 +36,13 @@ CASE = inputs.C2
 # square root = 1), counted from the operations each kernel's formulation performs; the counts are
 # derived line by line in the design doc. Units: faces for the face kernels, interior nodes otherwise.
 FLOPS_PER_UNIT = {
-    "weno_x": 1190, "weno_y": 1190, "weno_z": 1190,
+    "weno_x": 900, "weno_y": 900, "weno_z": 900,
     "faces_x": 151, "faces_y": 151, "faces_z": 151,
     "assemble": 520, "sensor": 105, "prims": 25,
 }
+# DRAM bytes (read + write) per unit from one ncu capture of each kernel on the 192x144x96 channel
+# (profiles/k_weno_channel-192x144x96_fp64.md), scaled to a launch by the units it processes.
+DRAM_BYTES_PER_UNIT = {"weno_x": 107.2, "weno_y": 212.8, "weno_z": 299.4}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 (the profiling recipe's unit table); a probe of
 # dependent-chain-free DFMA on this pool measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 1.25
@@ -153,13 +156,21 @@ def cpu_sample(case):
     return case.npts * 3 / sec, sec, w1, O.threads()
 
 
+def bench_case(args):
+    """The benchmark workload, or (for profiling captures only) the same channel on another grid."""
+    if not args.grid:
+        return CASE
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    return CASE.replace(name=f"channel-{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
     from paper_2004_02276_gb300 import binding
 
     torch.cuda.set_device(local)
-    case = CASE
+    case = bench_case(args)
     solver = binding.Solver(case, device=f"cuda:{local}")
     w0 = inputs.channel_state(case, seed=0)
     w = torch.from_numpy(w0).cuda()
@@ -207,7 +218,9 @@ def run_ours(args, world, rank, local):
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-        "traffic": None, "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe); probe measured 1.20",
+        "traffic": (DRAM_BYTES_PER_UNIT[dom] * units if dom in DRAM_BYTES_PER_UNIT else None),
+        "traffic_source": "ncu dram__bytes_read+write per unit on the 192x144x96 channel, x units",
+        "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe); probe measured 1.20",
         "units_per_launch": units, "flops_per_unit": FLOPS_PER_UNIT.get(dom),
         "avg_launch_ms": round(dom_ms / dom_n, 4),
         "kernel_share": {k: round(v[0] / total_ms, 4) for k, v in sorted(busy.items())},
@@ -236,7 +249,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz],
                    "mach_b": case.mach, "re_b": case.reynolds, "scheme": "central6+WENO5 (Ducros 0.05)",
                    "cfl": case.cfl, "precision": "fp64", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (state 252 MB + workspace 1.7 GB vs 129 MB L2)"},
+                   "l2": "inputs larger than L2 (state %d MB + workspace %.1f GB vs 129 MB L2)"
+                         % (5 * case.npts * 8 // 2**20, solver.workspace.numel() / 1e9)},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu:
@@ -294,6 +308,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--grid", default="", help="NXxNYxNZ override, for profiling captures only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

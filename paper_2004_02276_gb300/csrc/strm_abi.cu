@@ -44,9 +44,9 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   Dims d;
-  size_t off_prim[11];
+  size_t off_prim[12];
   size_t off_fh[3];
-  size_t off_R, off_wl[3], off_wcount, off_red, off_scal, off_metric;
+  size_t off_R, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric;
   size_t total;
 };
 
@@ -76,7 +76,7 @@ Layout make_layout(const strm_grid* g) {
   d.nf[1] = (long long)d.nx * (d.ny + 1) * d.nz;
   d.nf[2] = (long long)d.nx * d.ny * (d.nz + 1);
   size_t off = 0;
-  for (int f = 0; f < 11; ++f) {
+  for (int f = 0; f < 12; ++f) {
     L.off_prim[f] = off;
     off = align_up(off + sizeof(double) * (size_t)d.ng);
   }
@@ -89,9 +89,11 @@ Layout make_layout(const strm_grid* g) {
   for (int dir = 0; dir < 3; ++dir) {
     L.off_wl[dir] = off;
     off = align_up(off + sizeof(int) * (size_t)d.nf[dir]);
+    L.off_cl[dir] = off;
+    off = align_up(off + sizeof(int) * (size_t)d.nf[dir]);
   }
   L.off_wcount = off;
-  off = align_up(off + 4 * sizeof(unsigned));
+  off = align_up(off + 8 * sizeof(unsigned));
   L.off_red = off;
   off = align_up(off + sizeof(double) * (5 * (size_t)reduce_blocks(d) + 64));
   L.off_scal = off;
@@ -276,7 +278,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   const Dims& d = x->d;
   const Consts& C = x->C;
   const Bufs& B = x->B;
-  STRM_CK(cudaMemsetAsync(B.wcount, 0, 4 * sizeof(unsigned), st));
+  STRM_CK(cudaMemsetAsync(B.wcount, 0, 8 * sizeof(unsigned), st));
   STRM_LAUNCH(STRM_K_PRIMS, launch_prims(d, C, B, w, dt_mode && dt_fixed <= 0.0, st));
   if (dt_mode) STRM_LAUNCH(STRM_K_DT, launch_dt_finalize(d, B, cfl, dt_fixed, st));
   STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
@@ -284,7 +286,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
   if (C.convective) {
     for (int dir = 0; dir < 3; ++dir)
-      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, st));
+      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, st));
     if (C.weno_mode != STRM_WENO_OFF) {
       for (int dir = 0; dir < 3; ++dir)
         STRM_LAUNCH(STRM_K_WENO_X + dir, launch_weno_dir(d, C, B, dir, x->weno_grid, st));
@@ -355,12 +357,13 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   set_consts(x);
   x->C.wall_y = 0;
   char* ws = (char*)workspace;
-  double** prim[11] = {&x->B.rho, &x->B.u, &x->B.v, &x->B.w, &x->B.p, &x->B.T,
-                       &x->B.H,   &x->B.c, &x->B.mu, &x->B.theta, &x->B.div};
-  for (int f = 0; f < 11; ++f) *prim[f] = (double*)(ws + L.off_prim[f]);
+  double** prim[12] = {&x->B.rho, &x->B.u, &x->B.v,  &x->B.w,     &x->B.p,   &x->B.T,
+                       &x->B.H,   &x->B.c, &x->B.mu, &x->B.theta, &x->B.div, &x->B.srho};
+  for (int f = 0; f < 12; ++f) *prim[f] = (double*)(ws + L.off_prim[f]);
   for (int dir = 0; dir < 3; ++dir) {
     x->B.fh[dir] = (double*)(ws + L.off_fh[dir]);
     x->B.wl[dir] = (int*)(ws + L.off_wl[dir]);
+    x->B.cl[dir] = (int*)(ws + L.off_cl[dir]);
   }
   x->B.R = (double*)(ws + L.off_R);
   x->B.wcount = (unsigned*)(ws + L.off_wcount);
@@ -379,7 +382,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
     e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 4 * g->ny,
                         cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->B.scal, 0, sizeof(double) * kScalCount, x->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(x->B.wcount, 0, 4 * sizeof(unsigned), x->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->B.wcount, 0, 8 * sizeof(unsigned), x->stream);
   if (e != cudaSuccess) {
     delete x;
     return fail(STRM_ECUDA, std::string("init: ") + cudaGetErrorString(e));

@@ -43,11 +43,13 @@ struct Consts {
 
 struct Bufs {
   double *rho, *u, *v, *w, *p, *T, *H, *c, *mu;  // ghosted primitives
+  double *srho;                                 // ghosted sqrt(rho) (Roe weights)
   double *theta, *div;                          // ghosted sensor and node divergence
   double *fh[3];                                // interface fluxes
   double *R;                                    // residual, 5*N
   int *wl[3];                                   // compacted WENO face lists
-  unsigned int *wcount;                         // [3] list lengths
+  int *cl[3];                                   // compacted central face lists
+  unsigned int *wcount;                         // [0..2] WENO list lengths, [4..6] central
   double *red;                                  // reduction partials
   double *scal;                                 // device scalars, see kScal*
   const double *inv_hy, *c2y, *c1y, *vol;       // per-j metrics: 1/(y_eta deta),

@@ -1,9 +1,9 @@
 // Convective interface fluxes (central energy-consistent, or characteristic LF-WENO5 at the
 // faces the Ducros sensor flags) and the assembly of the residual with the viscous terms.
 //
-// Per direction: k_faces computes the central flux at every unflagged face and appends each
-// flagged face to a compacted list (warp-aggregated atomics), so that k_weno runs the
-// expensive characteristic reconstruction without warp divergence. k_assemble then forms
+// Per direction: k_classify splits the faces into a WENO list and a central list (warp-aggregated
+// atomics), k_central and k_weno then run over their lists without warp divergence whatever the
+// flagged fraction (a per-face branch would run both paths in most warps). k_assemble then forms
 // R = -sum_d (f_{s+1} - f_s)/h_d + viscous terms per node and the forcing partial sums.
 #include "strm_dev.cuh"
 #include "strm_launch.h"
@@ -77,42 +77,49 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
 
 // ------------------------------------------------------------------------------ WENO5
 
-// Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2}, returned as numerator/denominator so that the
-// caller divides once: value = num / den.
-__device__ __forceinline__ void weno5_nd(double fm2, double fm1, double f0, double fp1, double fp2,
-                                         double eps, double& num, double& den) {
-  double t0 = fm2 - 2.0 * fm1 + f0, t1 = fm2 - 4.0 * fm1 + 3.0 * f0;
-  double t2 = fm1 - 2.0 * f0 + fp1, t3 = fm1 - fp1;
-  double t4 = f0 - 2.0 * fp1 + fp2, t5 = 3.0 * f0 - 4.0 * fp1 + fp2;
-  double b0 = (13.0 / 12.0) * t0 * t0 + 0.25 * t1 * t1;
-  double b1 = (13.0 / 12.0) * t2 * t2 + 0.25 * t3 * t3;
-  double b2 = (13.0 / 12.0) * t4 * t4 + 0.25 * t5 * t5;
-  double q0 = eps + b0, q1 = eps + b1, q2 = eps + b2;
+// Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2} = (f0..f4), written in first differences
+// a..d of the stencil: value = f2 + num/den with
+//   6 q_0 = 6 f2 + 5b - 2a,  6 q_1 = 6 f2 + b + 2c,  6 q_2 = 6 f2 + 4c - d,
+// smoothness indicators scaled by 4 (4 beta = 13/3 t^2 + t'^2, so eps4 = 4 eps keeps the
+// weights), and weights d_k/(eps+beta_k)^2 multiplied through by 10 (eps+beta_0..2)^2 products.
+__device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
+                                         double eps4, double& num, double& den) {
+  double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
+  double t0 = b - a, t1 = fma(3.0, b, -a);
+  double t2 = c - b, t3 = b + c;
+  double t4 = d - c, t5 = fma(-3.0, c, d);
+  double q0 = eps4 + fma((13.0 / 3.0) * t0, t0, t1 * t1);
+  double q1 = eps4 + fma((13.0 / 3.0) * t2, t2, t3 * t3);
+  double q2 = eps4 + fma((13.0 / 3.0) * t4, t4, t5 * t5);
   q0 *= q0;
   q1 *= q1;
   q2 *= q2;
-  // alpha_k = d_k / q_k, scaled by q0 q1 q2 (the normalised weights are unchanged)
-  double w0 = 0.1 * (q1 * q2), w1 = 0.6 * (q0 * q2), w2 = 0.3 * (q0 * q1);
-  double c0 = 2.0 * fm2 - 7.0 * fm1 + 11.0 * f0;
-  double c1 = -fm1 + 5.0 * f0 + 2.0 * fp1;
-  double c2 = 2.0 * f0 + 5.0 * fp1 - fp2;
-  num = w0 * c0 + w1 * c1 + w2 * c2;
+  double w0 = q1 * q2, w1 = 6.0 * (q0 * q2), w2 = 3.0 * (q0 * q1);
+  double e0 = fma(-2.0, a, 5.0 * b), e1 = fma(2.0, c, b), e2 = fma(4.0, c, -d);
+  num = fma(w2, e2, fma(w1, e1, w0 * e0));
   den = 6.0 * (w0 + w1 + w2);
 }
 
 // Characteristic Lax-Friedrichs flux-vector splitting with WENO5 (Section 2.1) at the face
-// between nodes n and n+st: Roe average, projection of w and of the Euler flux at the six
-// stencil nodes onto the left eigenvectors (written out through the two scalars A and B of
-// the acoustic rows), local LF speeds (max |eigenvalue| over the stencil), WENO5 of the
-// positive part from the left and of the negative part from the right, projection back.
+// between nodes n and n+st: Roe average, local LF speeds (largest |eigenvalue| of each field over
+// the six stencil nodes), projection of w and of the Euler flux at the stencil nodes onto the
+// left eigenvectors (written out through the acoustic-row scalars A, B and the shear rows),
+// WENO5 of the positive part from the left and of the negative part from the right, and
+// projection back with the right eigenvectors.
+//
+// The split values of field k are carried scaled by s_k (4 for the acoustic fields, 2 for the
+// others) to drop the 1/2 and 1/4 factors of the projection and of the splitting; WENO5 is then
+// run with eps scaled by s_k^2, which leaves its weights unchanged, and the result is divided
+// by s_k. All scalings are powers of two.
 template <int DIR>
 __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long long n, long long st,
                                           double* f) {
   constexpr int T1 = DIR == 0 ? 1 : 0;
   constexpr int T2 = DIR == 2 ? 1 : 2;
   const double* __restrict__ vel[3] = {B.u, B.v, B.w};
+  const double* __restrict__ un_p = vel[DIR];
   // Roe average of nodes n and n + st
-  double sl = sqrt(__ldg(B.rho + n)), sr = sqrt(__ldg(B.rho + n + st));
+  double sl = __ldg(B.srho + n), sr = __ldg(B.srho + n + st);
   double inv = 1.0 / (sl + sr);
   double wl = sl * inv, wr = sr * inv;
   double ua[3];
@@ -120,59 +127,66 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
   for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
   double Ha = wl * __ldg(B.H + n) + wr * __ldg(B.H + n + st);
   double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
-  double ca = sqrt(C.gm1 * (Ha - 0.5 * q2));
-  double ic = 1.0 / ca;
+  double c2a = C.gm1 * (Ha - 0.5 * q2);
+  double ic = rsqrt(c2a);
+  double ca = c2a * ic;
   double b1 = C.gm1 * ic * ic;
   double b2 = 0.5 * q2 * b1;
   double un_a = ua[DIR];
 
-  // characteristic variables at the six stencil nodes
-  double cw[5][6], cf[5][6];
+  // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
   double lam0 = 0.0, lam1 = 0.0, lam4 = 0.0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    long long nn = n + (q - 2) * st;
+    double un = __ldg(un_p + nn), cs = __ldg(B.c + nn);
+    lam0 = fmax(lam0, fabs(un - cs));
+    lam1 = fmax(lam1, fabs(un));
+    lam4 = fmax(lam4, fabs(un + cs));
+  }
+
+  // scaled split characteristic values s_k (L F +- lam_k L w)/2 at the stencil nodes
+  double gp[5][6], gm[5][6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
     double rho = __ldg(B.rho + nn);
     double uu[3] = {__ldg(B.u + nn), __ldg(B.v + nn), __ldg(B.w + nn)};
-    double H = __ldg(B.H + nn), p = __ldg(B.p + nn), cs = __ldg(B.c + nn);
+    double H = __ldg(B.H + nn), p = __ldg(B.p + nn);
     double un = uu[DIR];
     double run = rho * un;
     double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
     double K = b2 + b1 * (H - udot);
     double b1p = b1 * p;
-    double Aw = rho * K - b1p;
+    double Aw = rho * K - b1p;          // acoustic rows: (l0 + l4) w = A_w, (l0 - l4) w = B_w
     double Af = run * K - b1p * un_a;
-    double Bw = rho * (un_a - un) * ic;
-    double Bf = (run * (un_a - un) - p) * ic;
+    double du = un_a - un;
+    double Bw = (rho * ic) * du;
+    double Bf = (run * du - p) * ic;
+    double Sw = Aw + Bw, Sf = Af + Bf, Dw = Aw - Bw, Df = Af - Bf;
+    gp[0][q] = fma(lam0, Sw, Sf);
+    gm[0][q] = fma(-lam0, Sw, Sf);
+    gp[4][q] = fma(lam4, Dw, Df);
+    gm[4][q] = fma(-lam4, Dw, Df);
+    double r1 = fma(lam1, rho, run), r2 = fma(-lam1, rho, run);
+    gp[1][q] = r1 - fma(lam1, Aw, Af);
+    gm[1][q] = r2 - fma(-lam1, Aw, Af);
     double d1 = uu[T1] - ua[T1], d2 = uu[T2] - ua[T2];
-    cw[0][q] = 0.5 * (Aw + Bw);
-    cf[0][q] = 0.5 * (Af + Bf);
-    cw[1][q] = rho - Aw;
-    cf[1][q] = run - Af;
-    cw[2][q] = rho * d1;
-    cf[2][q] = run * d1;
-    cw[3][q] = rho * d2;
-    cf[3][q] = run * d2;
-    cw[4][q] = 0.5 * (Aw - Bw);
-    cf[4][q] = 0.5 * (Af - Bf);
-    lam0 = fmax(lam0, fabs(un - cs));
-    lam1 = fmax(lam1, fabs(un));
-    lam4 = fmax(lam4, fabs(un + cs));
+    gp[2][q] = d1 * r1;
+    gm[2][q] = d1 * r2;
+    gp[3][q] = d2 * r1;
+    gm[3][q] = d2 * r2;
   }
   double g[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double lam = k == 0 ? lam0 : (k == 4 ? lam4 : lam1);
-    double gp[6], gm[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      gp[q] = 0.5 * (cf[k][q] + lam * cw[k][q]);
-      gm[q] = 0.5 * (cf[k][q] - lam * cw[k][q]);
-    }
+    const bool acoustic = (k == 0 || k == 4);
+    const double eps4 = (acoustic ? 64.0 : 16.0) * C.weno_eps;  // 4 s_k^2 eps
     double np_, dp_, nm_, dm_;
-    weno5_nd(gp[0], gp[1], gp[2], gp[3], gp[4], C.weno_eps, np_, dp_);
-    weno5_nd(gm[5], gm[4], gm[3], gm[2], gm[1], C.weno_eps, nm_, dm_);
-    g[k] = (np_ * dm_ + nm_ * dp_) / (dp_ * dm_);
+    weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
+    weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
+    double v = (gp[k][2] + gm[k][3]) + fma(np_, dm_, nm_ * dp_) / (dp_ * dm_);
+    g[k] = (acoustic ? 0.25 : 0.5) * v;
   }
   // back to conserved variables with the right eigenvectors
   double gs = g[0] + g[1] + g[4];
@@ -188,43 +202,63 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 
 // ------------------------------------------------------------------------------ face kernels
 
+// Warp-aggregated append of face q to a compacted list: one atomic per warp and list.
+__device__ __forceinline__ void warp_append(bool mine, unsigned act, int* list, unsigned* count, int q) {
+  unsigned m = __ballot_sync(act, mine);
+  if (!m) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(act, base, leader);
+  if (mine) list[base + __popc(m & ((1u << lane) - 1u))] = q;
+}
+
+// Hybrid switch, sensor mode: split the faces of one direction into a WENO list and a central
+// list, so that each flux kernel runs without warp divergence whatever the flagged fraction.
 template <int L, int DIR>
-__global__ void __launch_bounds__(256) k_faces(Dims d, Consts C, Bufs B) {
+__global__ void __launch_bounds__(256) k_classify(Dims d, Consts C, Bufs B) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.nf[DIR]) return;
   int i, j, k;
   face_node<DIR>(d, q, i, j, k);
-  long long n = gidx(d, i, j, k);
-  long long st = dir_stride(d, DIR);
-  bool fl = face_flag<L>(C, B.theta, n, st);
+  bool fl = face_flag<L>(C, B.theta, gidx(d, i, j, k), dir_stride(d, DIR));
   unsigned act = __activemask();
-  unsigned m = __ballot_sync(act, fl);
-  if (m) {
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(B.wcount + DIR, (unsigned)__popc(m));
-    base = __shfl_sync(act, base, leader);
-    if (fl) B.wl[DIR][base + __popc(m & ((1u << lane) - 1u))] = (int)q;
-  }
-  if (fl) return;
-  double f[5];
-  central_flux<L, DIR>(C, B, n, st, f);
-  double* out = B.fh[DIR];
-  long long nf = d.nf[DIR];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) out[c * nf + q] = f[c];
+  warp_append(fl, act, B.wl[DIR], B.wcount + DIR, (int)q);
+  warp_append(!fl, act, B.cl[DIR], B.wcount + 4 + DIR, (int)q);
 }
 
-template <int DIR>
-__global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
-  unsigned cnt = *(volatile unsigned*)(B.wcount + DIR);
+// Central flux at every face of one direction (WENO off) or at the faces of the central list.
+template <int L, int DIR>
+__global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list) {
+  long long cnt = use_list ? (long long)B.wcount[4 + DIR] : d.nf[DIR];
   long long nf = d.nf[DIR];
   long long st = dir_stride(d, DIR);
   double* out = B.fh[DIR];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
        t += (long long)gridDim.x * blockDim.x) {
-    long long q = B.wl[DIR][t];
+    long long q = use_list ? (long long)B.cl[DIR][t] : t;
+    int i, j, k;
+    face_node<DIR>(d, q, i, j, k);
+    double f[5];
+    central_flux<L, DIR>(C, B, gidx(d, i, j, k), st, f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c * nf + q] = f[c];
+  }
+}
+
+// Characteristic WENO flux at the faces of the WENO list (sensor mode) or at every face (WENO
+// everywhere).
+template <int DIR>
+__global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
+  const bool all = C.weno_mode == 2;
+  long long nf = d.nf[DIR];
+  long long cnt = all ? nf : (long long)B.wcount[DIR];
+  long long st = dir_stride(d, DIR);
+  double* out = B.fh[DIR];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long q = all ? t : (long long)B.wl[DIR][t];
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
     double f[5];
@@ -358,17 +392,27 @@ __global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, doub
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, cudaStream_t s) {
+// Face stage of one direction: sensor mode classifies then runs the central list; WENO off runs
+// the central flux over every face; WENO everywhere needs no central flux.
+void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {
+  if (C.weno_mode == 2) return;
+  bool sensor = C.weno_mode == 1;
   unsigned nb = blocks_for(d.nf[dir], 256);
+#define STRM_FACES(LL, DD)                                              \
+  do {                                                                  \
+    if (sensor) k_classify<LL, DD><<<nb, 256, 0, s>>>(d, C, B);         \
+    k_central<LL, DD><<<sensor ? (unsigned)grid : nb, 256, 0, s>>>(d, C, B, sensor ? 1 : 0); \
+  } while (0)
   if (C.L == 3) {
-    if (dir == 0) k_faces<3, 0><<<nb, 256, 0, s>>>(d, C, B);
-    else if (dir == 1) k_faces<3, 1><<<nb, 256, 0, s>>>(d, C, B);
-    else k_faces<3, 2><<<nb, 256, 0, s>>>(d, C, B);
+    if (dir == 0) STRM_FACES(3, 0);
+    else if (dir == 1) STRM_FACES(3, 1);
+    else STRM_FACES(3, 2);
   } else {
-    if (dir == 0) k_faces<2, 0><<<nb, 256, 0, s>>>(d, C, B);
-    else if (dir == 1) k_faces<2, 1><<<nb, 256, 0, s>>>(d, C, B);
-    else k_faces<2, 2><<<nb, 256, 0, s>>>(d, C, B);
+    if (dir == 0) STRM_FACES(2, 0);
+    else if (dir == 1) STRM_FACES(2, 1);
+    else STRM_FACES(2, 2);
   }
+#undef STRM_FACES
 }
 
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {

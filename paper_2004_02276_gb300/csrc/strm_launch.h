@@ -14,7 +14,7 @@ void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixe
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
-void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, cudaStream_t s);
+void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, cudaStream_t s);
 void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);

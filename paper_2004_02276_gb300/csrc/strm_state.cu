@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) k_prims(Dims d, Consts C, Bufs B, const d
     B.H[n] = E + p * ir;
     B.c[n] = c;
     B.mu[n] = viscosity(C, T);
+    B.srho[n] = sqrt(rho);
     if (want_cfl)
       spec = (fabs(u) + c) * C.inv_dx + (fabs(v) + c) * B.inv_hy[j] + (fabs(ww) + c) * C.inv_dz;
   }
@@ -63,10 +64,6 @@ __global__ void k_dt_finalize(Bufs B, int nparts, double cfl, double dt_fixed) {
 
 // ---------------------------------------------------------------------------------- ghost fills
 
-struct GhostPrim {
-  double rho, u, v, w, p, T, H, c, mu;
-};
-
 __device__ __forceinline__ void copy_prims(const Bufs& B, long long dst, long long src) {
   B.rho[dst] = B.rho[src];
   B.u[dst] = B.u[src];
@@ -77,6 +74,7 @@ __device__ __forceinline__ void copy_prims(const Bufs& B, long long dst, long lo
   B.H[dst] = B.H[src];
   B.c[dst] = B.c[src];
   B.mu[dst] = B.mu[src];
+  B.srho[dst] = B.srho[src];
 }
 
 // Isothermal no-slip staggered wall: the ghost mirrors an interior node across the wall
@@ -95,6 +93,7 @@ __device__ __forceinline__ void wall_prims(const Consts& C, const Bufs& B, long 
   B.H[dst] = C.cp * T + 0.5 * (u * u + v * v + w * w);
   B.c[dst] = sqrt(C.gamma * p / rho);
   B.mu[dst] = viscosity(C, T);
+  B.srho[dst] = sqrt(rho);
 }
 
 // Thread layout of a face ghost fill: x faces (2G * ny * nz), then y faces (nx * 2G * nz), then
