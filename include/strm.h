@@ -161,6 +161,28 @@ int strm_timing_read(strm_ctx* ctx, double* ms_host, long long* launches_host,
 /* Total kernels this context has launched (graph replays count every kernel in the graph). */
 int strm_launch_count(strm_ctx* ctx, long long* launches_host);
 
+/* Largest grid (nx*ny*nz) strm_conserved_totals_static accepts. */
+#define STRM_STATIC_MAX_NODES 67108864
+
+/* Conserved totals for callers that cannot allocate device memory. The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ *
+ * Same result as strm_conserved_totals (out_host[m] = sum w_m dx (y_eta deta) dz over the
+ * interior), but it needs no context and no workspace and allocates nothing, so it can be
+ * called by code that must not call cudaMalloc: an in-situ monitor attached to a solver whose
+ * allocator already holds the device memory, or a tool running where allocation is not
+ * allowed. The caller passes the grid, the device state w (layout as above) and a stream
+ * (NULL: the legacy default stream); the call synchronises that stream.
+ *
+ * Its scratch (partial sums and results, about 0.66 MB) is a file-scope __device__ array of
+ * the library: every GPU that loads the library holds it until the process exits, and every
+ * call on a device shares it. Calls that overlap on the GPU (for example on two streams) race
+ * on that array; serialise them. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture. Grids above STRM_STATIC_MAX_NODES nodes are rejected with STRM_EINVAL. */
+int strm_conserved_totals_static(const strm_grid* g, const double* w, double out_host[5],
+                                 void* stream);
+
 /* Release the context (not the caller's buffers). Safe on NULL. */
 void strm_destroy(strm_ctx* ctx);
 

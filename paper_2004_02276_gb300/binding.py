@@ -72,6 +72,7 @@ SIGNATURES = {
     "strm_timing": ([_vp, _i], _i),
     "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
     "strm_launch_count": ([_vp, _P(ctypes.c_longlong)], _i),
+    "strm_conserved_totals_static": ([_P(Grid), _vp, _P(_d), _vp], _i),
     "strm_destroy": ([_vp], None),
 }
 K_COUNT = 14
@@ -117,6 +118,18 @@ def structs(case):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def conserved_totals_static(case, w, stream=None):
+    """Totals of a device state through the entry point that allocates nothing (no context,
+    no workspace); for callers that cannot allocate device memory."""
+    g, _, _ = structs(case)
+    out = (ctypes.c_double * 5)()
+    st = stream if stream is not None else torch.cuda.current_stream(w.device)
+    _check("strm_conserved_totals_static",
+           lib().strm_conserved_totals_static(ctypes.byref(g), _ptr(w), out,
+                                              ctypes.c_void_p(st.cuda_stream)))
+    return list(out)
 
 
 class Solver:

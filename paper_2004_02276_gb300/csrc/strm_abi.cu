@@ -106,6 +106,8 @@ Layout make_layout(const strm_grid* g) {
 
 }  // namespace
 
+int strm::record_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct strm_ctx {
   strm_grid g;
   strm_phys p;

@@ -3,9 +3,14 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "strm_dev.cuh"
 
 namespace strm {
+
+// Set the thread-local message returned by strm_last_error and return code.
+int record_error(int code, const std::string& msg);
 
 int reduce_blocks(const Dims& d);
 void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w, bool want_cfl,
