@@ -48,7 +48,10 @@ enum { STRM_BC_PERIODIC = 0, STRM_BC_WALL_ISOTHERMAL = 1 };
 enum { STRM_FACE_YMIN_YMAX = 0 };
 enum { STRM_WENO_OFF = 0, STRM_WENO_SENSOR = 1, STRM_WENO_ALL = 2 };
 enum { STRM_VISC_POWER = 0, STRM_VISC_SUTHERLAND = 1 };
-enum { STRM_PREC_FP64 = 0 };
+/* STRM_PREC_FP64: every operation in FP64. STRM_PREC_MIXED: flux, sensor, WENO and viscous
+ * arithmetic in FP32; FP64 for the stored state, primitives, the projection of w and of the
+ * flux into characteristic variables, the RK stage accumulation, forcing, CFL and totals. */
+enum { STRM_PREC_FP64 = 0, STRM_PREC_MIXED = 1 };
 
 typedef struct {
   int nx, ny, nz;        /* interior nodes, each >= 1 (ny >= 3 with walls) */
@@ -75,7 +78,7 @@ typedef struct {
   double u0, l0;         /* sensor scales: the floor in the sensor denominator is (u0/l0)^2 */
   int convective;        /* 1: include convective terms (0 only for tests) */
   int viscous;           /* 1: include viscous terms (0 for inviscid runs) */
-  int precision;         /* STRM_PREC_FP64 */
+  int precision;         /* STRM_PREC_FP64 or STRM_PREC_MIXED */
 } strm_scheme;
 
 typedef struct strm_ctx strm_ctx;

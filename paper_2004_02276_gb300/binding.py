@@ -19,6 +19,7 @@ STRM_OK = 0
 _STATUS = {-1: "EINVAL", -2: "ECUDA", -3: "ENONFINITE", -4: "ENOMEM", -5: "ETIMEOUT"}
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
 VISC_LAWS = {"power": 0, "sutherland": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 
 class StrmError(RuntimeError):
@@ -112,7 +113,8 @@ def structs(case):
                getattr(case, "theta_thr", 0.05), getattr(case, "weno_eps", 1e-6),
                getattr(case, "u0", 1.0), getattr(case, "l0", 1.0),
                int(bool(getattr(case, "convective", True))),
-               int(bool(getattr(case, "viscous", True))), 0)
+               int(bool(getattr(case, "viscous", True))),
+               PRECISIONS[getattr(case, "precision", "fp64")])
     return g, p, s
 
 

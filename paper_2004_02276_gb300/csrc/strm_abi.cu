@@ -42,11 +42,16 @@ const double kBeta[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Node fields held in FP64 (all of them in FP64 precision; those the FP64 characteristic
+// projection reads in mixed precision) and in FP32 (mixed precision only).
+const int kN64All = 12, kN64Mixed = 8, kN32Mixed = 11;
+
 struct Layout {
   Dims d;
-  size_t off_prim[12];
+  bool mixed;
+  size_t off_n64[12], off_n32[11];
   size_t off_fh[3];
-  size_t off_R, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric;
+  size_t off_R, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
 };
 
@@ -57,11 +62,13 @@ bool valid_grid(const strm_grid* g) {
 
 bool valid_scheme(const strm_scheme* s) {
   return s && (s->L == 2 || s->L == 3) && s->weno_mode >= 0 && s->weno_mode <= 2 &&
-         s->precision == STRM_PREC_FP64 && s->weno_eps > 0 && s->l0 > 0;
+         (s->precision == STRM_PREC_FP64 || s->precision == STRM_PREC_MIXED) && s->weno_eps > 0 &&
+         s->l0 > 0;
 }
 
-Layout make_layout(const strm_grid* g) {
+Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   Layout L{};
+  L.mixed = s->precision == STRM_PREC_MIXED;
   Dims& d = L.d;
   d.nx = g->nx;
   d.ny = g->ny;
@@ -76,13 +83,20 @@ Layout make_layout(const strm_grid* g) {
   d.nf[1] = (long long)d.nx * (d.ny + 1) * d.nz;
   d.nf[2] = (long long)d.nx * d.ny * (d.nz + 1);
   size_t off = 0;
-  for (int f = 0; f < 12; ++f) {
-    L.off_prim[f] = off;
+  int n64 = L.mixed ? kN64Mixed : kN64All;
+  for (int f = 0; f < n64; ++f) {
+    L.off_n64[f] = off;
     off = align_up(off + sizeof(double) * (size_t)d.ng);
   }
+  if (L.mixed)
+    for (int f = 0; f < kN32Mixed; ++f) {
+      L.off_n32[f] = off;
+      off = align_up(off + sizeof(float) * (size_t)d.ng);
+    }
+  size_t fbytes = L.mixed ? sizeof(float) : sizeof(double);
   for (int dir = 0; dir < 3; ++dir) {
     L.off_fh[dir] = off;
-    off = align_up(off + sizeof(double) * 5 * (size_t)d.nf[dir]);
+    off = align_up(off + fbytes * 5 * (size_t)d.nf[dir]);
   }
   L.off_R = off;
   off = align_up(off + sizeof(double) * 5 * (size_t)d.N);
@@ -100,6 +114,8 @@ Layout make_layout(const strm_grid* g) {
   off = align_up(off + sizeof(double) * kScalCount);
   L.off_metric = off;
   off = align_up(off + sizeof(double) * 4 * (size_t)d.ny);
+  L.off_metric32 = off;
+  off = align_up(off + sizeof(float) * 3 * (size_t)d.ny);
   L.total = off;
   return L;
 }
@@ -117,7 +133,8 @@ struct strm_ctx {
   Bufs B;
   cudaStream_t stream = nullptr;
   int weno_grid = 0;
-  std::vector<double> metric_host;  // kept alive for the asynchronous upload
+  std::vector<double> metric_host;   // kept alive for the asynchronous uploads
+  std::vector<float> metric_host32;
   double time_host[2] = {0.0, 0.0};
   // graph of one RK step, replayed by strm_advance_n
   cudaStream_t cap = nullptr;
@@ -141,11 +158,43 @@ struct strm_ctx {
 
 namespace {
 
+template <typename R>
+void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const strm_grid& g) {
+  for (int l = 0; l < 4; ++l) K.a[l] = K.b[l] = R(0);
+  // central coefficients of order 2L: first derivative a_l, second derivative b_l with
+  // f'' ~ sum_l b_l (f_{+l} + f_{-l} - 2 f_0)/h^2 (Section 2.1)
+  if (s.L == 3) {
+    K.a[1] = R(3.0 / 4.0); K.a[2] = R(-3.0 / 20.0); K.a[3] = R(1.0 / 60.0);
+    K.b[1] = R(3.0 / 2.0); K.b[2] = R(-3.0 / 20.0); K.b[3] = R(1.0 / 90.0);
+  } else {
+    K.a[1] = R(2.0 / 3.0); K.a[2] = R(-1.0 / 12.0);
+    K.b[1] = R(4.0 / 3.0); K.b[2] = R(-1.0 / 12.0);
+  }
+  double dx = g.lx / g.nx, dz = g.lz / g.nz;
+  K.inv_dx = R(1.0 / dx);
+  K.inv_dz = R(1.0 / dz);
+  K.inv_dx2 = R((1.0 / dx) * (1.0 / dx));
+  K.inv_dz2 = R((1.0 / dz) * (1.0 / dz));
+  double cv = p.r_gas / (p.gamma - 1.0), cp = p.gamma * cv;
+  K.cp_pr = R(cp / p.prandtl);
+  K.sens_eps = R((s.u0 / s.l0) * (s.u0 / s.l0));
+  K.theta_thr = R(s.theta_thr);
+  K.weno_eps = R(s.weno_eps);
+  K.gamma = R(p.gamma);
+  K.gm1 = R(p.gamma - 1.0);
+  K.r_gas = R(p.r_gas);
+  K.cp = R(cp);
+  K.t_wall = R(p.t_wall);
+  K.mu_ref = R(p.mu_ref);
+  K.inv_tref = R(1.0 / p.t_ref);
+  K.visc_exp = R(p.visc_exp);
+  K.suth_s = R(p.suth_s);
+}
+
 void set_consts(strm_ctx* x) {
   Consts& C = x->C;
   const strm_phys& p = x->p;
   const strm_scheme& s = x->s;
-  const strm_grid& g = x->g;
   C.gamma = p.gamma;
   C.gm1 = p.gamma - 1.0;
   C.r_gas = p.r_gas;
@@ -165,24 +214,9 @@ void set_consts(strm_ctx* x) {
   C.weno_mode = s.weno_mode;
   C.convective = s.convective ? 1 : 0;
   C.viscous = s.viscous ? 1 : 0;
-  for (int l = 0; l < 4; ++l) C.a[l] = C.b[l] = 0.0;
-  // central coefficients of order 2L: first derivative a_l, second derivative b_l with
-  // f'' ~ sum_l b_l (f_{+l} + f_{-l} - 2 f_0)/h^2 (Section 2.1)
-  if (s.L == 3) {
-    C.a[1] = 3.0 / 4.0; C.a[2] = -3.0 / 20.0; C.a[3] = 1.0 / 60.0;
-    C.b[1] = 3.0 / 2.0; C.b[2] = -3.0 / 20.0; C.b[3] = 1.0 / 90.0;
-  } else {
-    C.a[1] = 2.0 / 3.0; C.a[2] = -1.0 / 12.0;
-    C.b[1] = 4.0 / 3.0; C.b[2] = -1.0 / 12.0;
-  }
-  C.theta_thr = s.theta_thr;
-  C.weno_eps = s.weno_eps;
-  C.sens_eps = (s.u0 / s.l0) * (s.u0 / s.l0);
-  double dx = g.lx / g.nx, dz = g.lz / g.nz;
-  C.inv_dx = 1.0 / dx;
-  C.inv_dz = 1.0 / dz;
-  C.inv_dx2 = C.inv_dx * C.inv_dx;
-  C.inv_dz2 = C.inv_dz * C.inv_dz;
+  C.mixed = s.precision == STRM_PREC_MIXED ? 1 : 0;
+  fill_coefs(C.k64, p, s, x->g);
+  fill_coefs(C.k32, p, s, x->g);
 }
 
 // Wall-normal metrics at the nodes eta_j = (j + 1/2)/ny of y = (ly/2) tanh(beta(2 eta - 1))/tanh(beta)
@@ -213,6 +247,8 @@ void build_metrics(strm_ctx* x) {
     x->metric_host[3 * ny + j] = dx * (ye * deta) * dz;
     vt += x->metric_host[3 * ny + j];
   }
+  x->metric_host32.resize(3 * (size_t)ny);
+  for (int q = 0; q < 3 * ny; ++q) x->metric_host32[q] = (float)x->metric_host[q];
   x->C.vtot = vt * g.nx * g.nz;
 }
 
@@ -332,7 +368,7 @@ const char* strm_last_error(void) { return g_last_error.c_str(); }
 
 size_t strm_workspace_bytes(const strm_grid* g, const strm_scheme* s) {
   if (!valid_grid(g) || !valid_scheme(s)) return 0;
-  return make_layout(g).total;
+  return make_layout(g, s).total;
 }
 
 int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const strm_scheme* s,
@@ -340,11 +376,11 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   if (!out) return fail(STRM_EINVAL, "ctx out-pointer is null");
   *out = nullptr;
   if (!valid_grid(g)) return fail(STRM_EINVAL, "invalid grid (sizes >= 1, lengths > 0, tanh needs beta > 0)");
-  if (!valid_scheme(s)) return fail(STRM_EINVAL, "invalid scheme (L in {2,3}, weno_mode in 0..2, fp64)");
+  if (!valid_scheme(s)) return fail(STRM_EINVAL, "invalid scheme (L in {2,3}, weno_mode in 0..2, precision fp64 or mixed)");
   if (!p || !(p->gamma > 1.0) || !(p->r_gas > 0) || !(p->prandtl > 0) || !(p->mu_ref >= 0) ||
       !(p->t_ref > 0) || !(p->t_wall > 0) || p->visc_law < 0 || p->visc_law > 1)
     return fail(STRM_EINVAL, "invalid physical parameters");
-  Layout L = make_layout(g);
+  Layout L = make_layout(g, s);
   if (!workspace) return fail(STRM_EINVAL, "workspace is null");
   if (((uintptr_t)workspace & 255) != 0) return fail(STRM_EINVAL, "workspace must be 256-byte aligned");
   if (workspace_bytes < L.total)
@@ -359,11 +395,24 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   set_consts(x);
   x->C.wall_y = 0;
   char* ws = (char*)workspace;
-  double** prim[12] = {&x->B.rho, &x->B.u, &x->B.v,  &x->B.w,     &x->B.p,   &x->B.T,
-                       &x->B.H,   &x->B.c, &x->B.mu, &x->B.theta, &x->B.div, &x->B.srho};
-  for (int f = 0; f < 12; ++f) *prim[f] = (double*)(ws + L.off_prim[f]);
+  Nodes<double>& N64 = x->B.n64;
+  Nodes<float>& N32 = x->B.n32;
+  N64 = Nodes<double>{};
+  N32 = Nodes<float>{};
+  if (L.mixed) {
+    double** f64[kN64Mixed] = {&N64.rho, &N64.u, &N64.v, &N64.w, &N64.p, &N64.T, &N64.H, &N64.srho};
+    for (int f = 0; f < kN64Mixed; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
+    float** f32[kN32Mixed] = {&N32.rho, &N32.u, &N32.v, &N32.w, &N32.p, &N32.T,
+                              &N32.H,   &N32.c, &N32.mu, &N32.theta, &N32.div};
+    for (int f = 0; f < kN32Mixed; ++f) *f32[f] = (float*)(ws + L.off_n32[f]);
+  } else {
+    double** f64[kN64All] = {&N64.rho, &N64.u, &N64.v,  &N64.w,     &N64.p,   &N64.T,
+                             &N64.H,   &N64.c, &N64.mu, &N64.theta, &N64.div, &N64.srho};
+    for (int f = 0; f < kN64All; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
+  }
   for (int dir = 0; dir < 3; ++dir) {
-    x->B.fh[dir] = (double*)(ws + L.off_fh[dir]);
+    x->B.fh64[dir] = L.mixed ? nullptr : (double*)(ws + L.off_fh[dir]);
+    x->B.fh32[dir] = L.mixed ? (float*)(ws + L.off_fh[dir]) : nullptr;
     x->B.wl[dir] = (int*)(ws + L.off_wl[dir]);
     x->B.cl[dir] = (int*)(ws + L.off_cl[dir]);
   }
@@ -372,16 +421,23 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->B.red = (double*)(ws + L.off_red);
   x->B.scal = (double*)(ws + L.off_scal);
   double* met = (double*)(ws + L.off_metric);
-  x->B.inv_hy = met;
-  x->B.c2y = met + g->ny;
-  x->B.c1y = met + 2 * g->ny;
+  float* met32 = (float*)(ws + L.off_metric32);
+  x->B.m64.inv_hy = met;
+  x->B.m64.c2y = met + g->ny;
+  x->B.m64.c1y = met + 2 * g->ny;
   x->B.vol = met + 3 * g->ny;
+  x->B.m32.inv_hy = met32;
+  x->B.m32.c2y = met32 + g->ny;
+  x->B.m32.c1y = met32 + 2 * g->ny;
   build_metrics(x);
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 4 * g->ny,
+                        cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(met32, x->metric_host32.data(), sizeof(float) * 3 * g->ny,
                         cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->B.scal, 0, sizeof(double) * kScalCount, x->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->B.wcount, 0, 8 * sizeof(unsigned), x->stream);
@@ -523,8 +579,7 @@ int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsign
   launch_prims(x->d, x->C, x->B, w, false, x->stream);
   launch_ghost_prims(x->d, x->C, x->B, x->stream);
   launch_sensor(x->d, x->C, x->B, x->stream);
-  if (theta) launch_export_interior(x->d, x->B.theta, theta, x->stream);
-  if (div) launch_export_interior(x->d, x->B.div, div, x->stream);
+  launch_export_sensor(x->d, x->C, x->B, theta, div, x->stream);
   unsigned char* fl[3] = {fx, fy, fz};
   for (int dir = 0; dir < 3; ++dir)
     if (fl[dir]) launch_flags(x->d, x->C, x->B, dir, fl[dir], x->stream);

@@ -2,11 +2,14 @@
 //
 // Layout in HBM
 //   state w, residual R, RK register: SoA [5][nz][ny][nx] FP64 (interior only, caller-owned)
-//   primitives and sensor fields: ghosted [nz+2G][ny+2G][px] FP64 (workspace); the interior
-//     node (i,j,k) sits at ((k+G)*py + j+G)*px + i+GX; GX = 4 keeps interior rows 32-byte
-//     aligned, px is a multiple of 4.
+//   node fields (workspace): ghosted [nz+2G][ny+2G][px]; the interior node (i,j,k) sits at
+//     ((k+G)*py + j+G)*px + i+GX; GX = 4 keeps interior rows 32-byte aligned, px is a multiple
+//     of 4. FP64 precision keeps every node field in FP64. Mixed precision keeps the fields the
+//     characteristic projection reads (rho, u, v, w, p, T, H, sqrt rho) in FP64 and FP32 copies
+//     of all fields for the FP32 kernels.
 //   interface fluxes (workspace): x faces [5][nz][ny][nx+1], y faces [5][nz][ny+1][nx],
-//     z faces [5][nz+1][ny][nx]; face s along a direction lies between nodes s-1 and s.
+//     z faces [5][nz+1][ny][nx] (FP64, or FP32 in mixed precision); face s along a direction
+//     lies between nodes s-1 and s.
 #pragma once
 
 #include <cstdint>
@@ -27,34 +30,67 @@ struct Dims {
   long long nf[3];    // faces per direction
 };
 
+// Ghosted node fields of one precision.
+template <typename R>
+struct Nodes {
+  R *rho, *u, *v, *w, *p, *T, *H, *c, *mu, *srho, *theta, *div;
+};
+
+// Per-j wall-normal metrics: 1/(y_eta deta), 1/(y_eta deta)^2, y_etaeta/(y_eta^3 deta).
+template <typename R>
+struct Metric {
+  const R *inv_hy, *c2y, *c1y;
+};
+
+// Scheme and gas coefficients in the arithmetic precision of a kernel.
+template <typename R>
+struct Coefs {
+  R a[4], b[4];                      // central first/second-derivative coefficients, 1..L
+  R inv_dx, inv_dz, inv_dx2, inv_dz2;
+  R cp_pr, sens_eps, theta_thr, weno_eps;
+  R gamma, gm1, r_gas, cp, t_wall, mu_ref, inv_tref, visc_exp, suth_s;
+};
+
 struct Consts {
-  // gas
+  // gas (FP64)
   double gamma, gm1, r_gas, inv_r, cv, inv_cv, cp, cp_pr;
   double mu_ref, inv_tref, visc_exp, suth_s, t_wall;
   int visc_law, wall_y, forcing;
   // scheme
-  int L, weno_mode, convective, viscous;
-  double a[4], b[4];
-  double theta_thr, weno_eps, sens_eps;
-  // uniform directions
-  double inv_dx, inv_dz, inv_dx2, inv_dz2;
+  int L, weno_mode, convective, viscous, mixed;
   double vtot;  // total metric volume
+  Coefs<double> k64;
+  Coefs<float> k32;
 };
 
 struct Bufs {
-  double *rho, *u, *v, *w, *p, *T, *H, *c, *mu;  // ghosted primitives
-  double *srho;                                 // ghosted sqrt(rho) (Roe weights)
-  double *theta, *div;                          // ghosted sensor and node divergence
-  double *fh[3];                                // interface fluxes
-  double *R;                                    // residual, 5*N
-  int *wl[3];                                   // compacted WENO face lists
-  int *cl[3];                                   // compacted central face lists
-  unsigned int *wcount;                         // [0..2] WENO list lengths, [4..6] central
-  double *red;                                  // reduction partials
-  double *scal;                                 // device scalars, see kScal*
-  const double *inv_hy, *c2y, *c1y, *vol;       // per-j metrics: 1/(y_eta deta),
-                                                // 1/(y_eta deta)^2, y_etaeta/(y_eta^3 deta), volume
+  Nodes<double> n64;
+  Nodes<float> n32;
+  double* fh64[3];                              // interface fluxes (FP64 precision)
+  float* fh32[3];                               // interface fluxes (mixed precision)
+  double* R;                                    // residual, 5*N
+  int* wl[3];                                   // compacted WENO face lists
+  int* cl[3];                                   // compacted central face lists
+  unsigned int* wcount;                         // [0..2] WENO list lengths, [4..6] central
+  double* red;                                  // reduction partials
+  double* scal;                                 // device scalars, see kScal*
+  Metric<double> m64;
+  Metric<float> m32;
+  const double* vol;                            // node volume dx (y_eta deta) dz per j
 };
+
+template <typename R> __device__ __forceinline__ const Nodes<R>& nodes(const Bufs& B);
+template <> __device__ __forceinline__ const Nodes<double>& nodes<double>(const Bufs& B) { return B.n64; }
+template <> __device__ __forceinline__ const Nodes<float>& nodes<float>(const Bufs& B) { return B.n32; }
+template <typename R> __device__ __forceinline__ const Metric<R>& metric(const Bufs& B);
+template <> __device__ __forceinline__ const Metric<double>& metric<double>(const Bufs& B) { return B.m64; }
+template <> __device__ __forceinline__ const Metric<float>& metric<float>(const Bufs& B) { return B.m32; }
+template <typename R> __device__ __forceinline__ R* face_flux(const Bufs& B, int dir);
+template <> __device__ __forceinline__ double* face_flux<double>(const Bufs& B, int dir) { return B.fh64[dir]; }
+template <> __device__ __forceinline__ float* face_flux<float>(const Bufs& B, int dir) { return B.fh32[dir]; }
+template <typename R> __device__ __forceinline__ const Coefs<R>& coefs(const Consts& C);
+template <> __device__ __forceinline__ const Coefs<double>& coefs<double>(const Consts& C) { return C.k64; }
+template <> __device__ __forceinline__ const Coefs<float>& coefs<float>(const Consts& C) { return C.k32; }
 
 // device scalars
 enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalCount = 16 };
@@ -72,18 +108,21 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
+__device__ __forceinline__ double rpow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float rpow(float x, float e) { return powf(x, e); }
+
 // Viscosity law (Section 2): power law mu_ref (T/t_ref)^exp, or Sutherland.
-__device__ __forceinline__ double viscosity(const Consts& C, double T) {
-  double tr = T * C.inv_tref;
-  if (C.visc_law == 1) return C.mu_ref * pow(tr, 1.5) * (1.0 + C.suth_s) / (tr + C.suth_s);
-  return C.mu_ref * pow(tr, C.visc_exp);
+template <typename R>
+__device__ __forceinline__ R viscosity(const Coefs<R>& K, int law, R T) {
+  R tr = T * K.inv_tref;
+  if (law == 1) return K.mu_ref * rpow(tr, R(1.5)) * (R(1) + K.suth_s) / (tr + K.suth_s);
+  return K.mu_ref * rpow(tr, K.visc_exp);
 }
 
 // sum_l a_l (f_{+l} - f_{-l}) along a line (first-derivative numerator of order 2L)
-template <int L>
-__device__ __forceinline__ double dsum(const double* __restrict__ f, long long n, long long st,
-                                       const double* a) {
-  double s = 0.0;
+template <int L, typename R>
+__device__ __forceinline__ R dsum(const R* __restrict__ f, long long n, long long st, const R* a) {
+  R s = R(0);
 #pragma unroll
   for (int l = 1; l <= L; ++l) s += a[l] * (__ldg(f + n + l * st) - __ldg(f + n - l * st));
   return s;
@@ -91,30 +130,87 @@ __device__ __forceinline__ double dsum(const double* __restrict__ f, long long n
 
 // First- and second-derivative numerators along one line, sharing the loads:
 // s1 = sum_l a_l (f_{+l} - f_{-l}), s2 = sum_l b_l (f_{+l} + f_{-l} - 2 f_0).
-template <int L>
-__device__ __forceinline__ void dsum12(const double* __restrict__ f, long long n, long long st,
-                                       const double* a, const double* b, double& s1, double& s2) {
-  double f0 = __ldg(f + n);
-  s1 = 0.0;
-  s2 = 0.0;
+template <int L, typename R>
+__device__ __forceinline__ void dsum12(const R* __restrict__ f, long long n, long long st, const R* a,
+                                       const R* b, R& s1, R& s2) {
+  R f0 = __ldg(f + n);
+  s1 = R(0);
+  s2 = R(0);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    double fp = __ldg(f + n + l * st), fm = __ldg(f + n - l * st);
+    R fp = __ldg(f + n + l * st), fm = __ldg(f + n - l * st);
     s1 += a[l] * (fp - fm);
-    s2 += b[l] * ((fp + fm) - 2.0 * f0);
+    s2 += b[l] * ((fp + fm) - R(2) * f0);
   }
 }
 
+// Ducros sensor at interior node (i,j,k) (Eq. sensor): theta = max(-div / sqrt(div^2 +
+// |curl u|^2 + (u0/L0)^2), 0), first derivatives of order 2L in precision R; div is returned too.
+template <int L, typename R>
+__device__ __forceinline__ R theta_node(const Dims& d, const Consts& C, const Bufs& B, int i, int j,
+                                        int k, R& div) {
+  const Nodes<R>& P = nodes<R>(B);
+  const Coefs<R>& K = coefs<R>(C);
+  long long n = gidx(d, i, j, k);
+  long long sy = d.px, sz = d.plane;
+  R hy = metric<R>(B).inv_hy[j];
+  R ux = dsum<L>(P.u, n, 1, K.a) * K.inv_dx;
+  R uy = dsum<L>(P.u, n, sy, K.a) * hy;
+  R uz = dsum<L>(P.u, n, sz, K.a) * K.inv_dz;
+  R vx = dsum<L>(P.v, n, 1, K.a) * K.inv_dx;
+  R vy = dsum<L>(P.v, n, sy, K.a) * hy;
+  R vz = dsum<L>(P.v, n, sz, K.a) * K.inv_dz;
+  R wx = dsum<L>(P.w, n, 1, K.a) * K.inv_dx;
+  R wy = dsum<L>(P.w, n, sy, K.a) * hy;
+  R wz = dsum<L>(P.w, n, sz, K.a) * K.inv_dz;
+  div = ux + vy + wz;
+  R o1 = wy - vz, o2 = uz - wx, o3 = vx - uy;
+  R den = sqrt(div * div + (o1 * o1 + o2 * o2 + o3 * o3) + K.sens_eps);
+  R th = -div / den;
+  return th > R(0) ? th : R(0);
+}
+
 // WENO switch at the face between nodes n and n+st: max theta over nodes n-L+1 .. n+L.
-template <int L>
-__device__ __forceinline__ bool face_flag(const Consts& C, const double* __restrict__ theta,
-                                          long long n, long long st) {
-  if (C.weno_mode == 2) return true;
-  if (C.weno_mode == 0) return false;
-  double tmax = 0.0;
+template <int L, typename R>
+__device__ __forceinline__ R face_theta_max(const R* __restrict__ theta, long long n, long long st) {
+  R tmax = R(0);
 #pragma unroll
   for (int q = -L + 1; q <= L; ++q) tmax = fmax(tmax, __ldg(theta + n + q * st));
-  return tmax > C.theta_thr;
+  return tmax;
+}
+
+// Interior node whose theta a ghost node along y carries (periodic copy or even wall mirror);
+// along x and z the ghosts are periodic copies.
+__device__ __forceinline__ int theta_source(int idx, int n, bool wall) {
+  if (!wall) return wrapi(idx, n);
+  if (idx < 0) return -1 - idx;
+  if (idx >= n) return 2 * n - 1 - idx;
+  return idx;
+}
+
+// Hybrid switch decision for the face whose left node is (i,j,k) along dir. FP64 precision
+// compares the FP64 window maximum. Mixed precision compares the FP32 maximum, except when it
+// falls within 0.2% of the threshold (far wider than the FP32 error of theta): then theta is
+// recomputed in FP64 over the window (from the FP64 velocities), so that the decision is the
+// one the FP64 path takes for the same state.
+template <int L, typename R>
+__device__ __forceinline__ bool face_decision(const Dims& d, const Consts& C, const Bufs& B, int i, int j,
+                                              int k, int dir) {
+  if (C.weno_mode == 2) return true;
+  if (C.weno_mode == 0) return false;
+  R tmax = face_theta_max<L>(nodes<R>(B).theta, gidx(d, i, j, k), dir_stride(d, dir));
+  const R thr = coefs<R>(C).theta_thr;
+  if (sizeof(R) == sizeof(double) || fabs(tmax - thr) > R(0.002) * thr) return tmax > thr;
+  double t64 = 0.0;
+  for (int q = -L + 1; q <= L; ++q) {
+    int ii = i + (dir == 0 ? q : 0), jj = j + (dir == 1 ? q : 0), kk = k + (dir == 2 ? q : 0);
+    ii = theta_source(ii, d.nx, false);
+    jj = theta_source(jj, d.ny, C.wall_y != 0);
+    kk = theta_source(kk, d.nz, false);
+    double dv;
+    t64 = fmax(t64, theta_node<L, double>(d, C, B, ii, jj, kk, dv));
+  }
+  return t64 > C.k64.theta_thr;
 }
 
 // Block-wide sum (deterministic order) of a per-thread value; result valid in thread 0.

@@ -39,27 +39,29 @@ __device__ __forceinline__ void face_node(const Dims& d, long long q, int& i, in
 // Energy-consistent split flux at the face between nodes n and n+st (Eqs. avg_operator,
 // encflux): f_phi = 2 sum_l a_l sum_{m<l} (rho, u_n, phi)~_{n-m,l}. With
 // qq = (rho_a + rho_b)(u_a + u_b)/4 this is sum_l a_l sum_m qq (phi_a + phi_b); the pressure
-// enters the normal momentum as sum_l a_l sum_m (p_a + p_b).
-template <int L, int DIR>
+// enters the normal momentum as sum_l a_l sum_m (p_a + p_b). R is the arithmetic precision.
+template <int L, int DIR, typename R>
 __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, long long n, long long st,
-                                             double* f) {
-  const double* __restrict__ ud = DIR == 0 ? B.u : (DIR == 1 ? B.v : B.w);
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, ap = 0.0;
+                                             R* f) {
+  const Nodes<R>& P = nodes<R>(B);
+  const R* a = coefs<R>(C).a;
+  const R* __restrict__ ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
+  R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0), ap = R(0);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, sp = 0.0;
+    R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0), sp = R(0);
 #pragma unroll
     for (int m = 0; m < l; ++m) {
       long long ia = n - m * st, ib = n + (l - m) * st;
-      double qq = 0.25 * (__ldg(B.rho + ia) + __ldg(B.rho + ib)) * (__ldg(ud + ia) + __ldg(ud + ib));
+      R qq = R(0.25) * (__ldg(P.rho + ia) + __ldg(P.rho + ib)) * (__ldg(ud + ia) + __ldg(ud + ib));
       s0 += qq;
-      s1 += qq * (__ldg(B.u + ia) + __ldg(B.u + ib));
-      s2 += qq * (__ldg(B.v + ia) + __ldg(B.v + ib));
-      s3 += qq * (__ldg(B.w + ia) + __ldg(B.w + ib));
-      s4 += qq * (__ldg(B.H + ia) + __ldg(B.H + ib));
-      sp += __ldg(B.p + ia) + __ldg(B.p + ib);
+      s1 += qq * (__ldg(P.u + ia) + __ldg(P.u + ib));
+      s2 += qq * (__ldg(P.v + ia) + __ldg(P.v + ib));
+      s3 += qq * (__ldg(P.w + ia) + __ldg(P.w + ib));
+      s4 += qq * (__ldg(P.H + ia) + __ldg(P.H + ib));
+      sp += __ldg(P.p + ia) + __ldg(P.p + ib);
     }
-    double al = C.a[l];
+    R al = a[l];
     a0 += al * s0;
     a1 += al * s1;
     a2 += al * s2;
@@ -67,7 +69,7 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
     a4 += al * s4;
     ap += al * sp;
   }
-  f[0] = 2.0 * a0;
+  f[0] = R(2) * a0;
   f[1] = a1;
   f[2] = a2;
   f[3] = a3;
@@ -116,16 +118,17 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
                                           double* f) {
   constexpr int T1 = DIR == 0 ? 1 : 0;
   constexpr int T2 = DIR == 2 ? 1 : 2;
-  const double* __restrict__ vel[3] = {B.u, B.v, B.w};
+  const Nodes<double>& P = B.n64;
+  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
   const double* __restrict__ un_p = vel[DIR];
   // Roe average of nodes n and n + st
-  double sl = __ldg(B.srho + n), sr = __ldg(B.srho + n + st);
+  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
   double inv = 1.0 / (sl + sr);
   double wl = sl * inv, wr = sr * inv;
   double ua[3];
 #pragma unroll
   for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
-  double Ha = wl * __ldg(B.H + n) + wr * __ldg(B.H + n + st);
+  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
   double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
   double c2a = C.gm1 * (Ha - 0.5 * q2);
   double ic = rsqrt(c2a);
@@ -139,7 +142,7 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    double un = __ldg(un_p + nn), cs = __ldg(B.c + nn);
+    double un = __ldg(un_p + nn), cs = __ldg(P.c + nn);
     lam0 = fmax(lam0, fabs(un - cs));
     lam1 = fmax(lam1, fabs(un));
     lam4 = fmax(lam4, fabs(un + cs));
@@ -150,9 +153,9 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    double rho = __ldg(B.rho + nn);
-    double uu[3] = {__ldg(B.u + nn), __ldg(B.v + nn), __ldg(B.w + nn)};
-    double H = __ldg(B.H + nn), p = __ldg(B.p + nn);
+    double rho = __ldg(P.rho + nn);
+    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
+    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
     double un = uu[DIR];
     double run = rho * un;
     double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
@@ -181,7 +184,7 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const bool acoustic = (k == 0 || k == 4);
-    const double eps4 = (acoustic ? 64.0 : 16.0) * C.weno_eps;  // 4 s_k^2 eps
+    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;  // 4 s_k^2 eps
     double np_, dp_, nm_, dm_;
     weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
     weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
@@ -200,6 +203,117 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
          ua[T2] * g[3];
 }
 
+// FP32 WENO5 (mixed precision), same first-difference form; the nonlinear weights are formed
+// as 10 d_k/(eps+beta_k)^2 directly (products of (eps+beta)^2 could overflow FP32).
+__device__ __forceinline__ float weno5_f(float f0, float f1, float f2, float f3, float f4, float eps4) {
+  float a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
+  float t0 = b - a, t1 = fmaf(3.f, b, -a);
+  float t2 = c - b, t3 = b + c;
+  float t4 = d - c, t5 = fmaf(-3.f, c, d);
+  float q0 = eps4 + fmaf((13.f / 3.f) * t0, t0, t1 * t1);
+  float q1 = eps4 + fmaf((13.f / 3.f) * t2, t2, t3 * t3);
+  float q2 = eps4 + fmaf((13.f / 3.f) * t4, t4, t5 * t5);
+  float w0 = 1.f / (q0 * q0), w1 = 6.f / (q1 * q1), w2 = 3.f / (q2 * q2);
+  float e0 = fmaf(-2.f, a, 5.f * b), e1 = fmaf(2.f, c, b), e2 = fmaf(4.f, c, -d);
+  return f2 + fmaf(w2, e2, fmaf(w1, e1, w0 * e0)) / (6.f * (w0 + w1 + w2));
+}
+
+// Mixed-precision characteristic WENO flux. The projection into characteristic variables is
+// done in FP64: Roe state, eigen-scalars and, per stencil node, the acoustic-row scalars
+// A and B of w and of the Euler flux (where cancellation happens). The LF split, WENO5 and the
+// projection back to conserved variables run in FP32; the result is an FP32 face flux.
+template <int DIR>
+__device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, long long n, long long st,
+                                                float* f) {
+  constexpr int T1 = DIR == 0 ? 1 : 0;
+  constexpr int T2 = DIR == 2 ? 1 : 2;
+  const Nodes<double>& P = B.n64;
+  const Nodes<float>& F = B.n32;
+  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
+  const float* __restrict__ velf[3] = {F.u, F.v, F.w};
+  // FP64 Roe average of nodes n and n + st and the eigen-scalars
+  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
+  double inv = 1.0 / (sl + sr);
+  double wl = sl * inv, wr = sr * inv;
+  double ua[3];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
+  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
+  double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
+  double c2a = C.gm1 * (Ha - 0.5 * q2);
+  double ic = rsqrt(c2a);
+  double ca = c2a * ic;
+  double b1 = C.gm1 * ic * ic;
+  double b2 = 0.5 * q2 * b1;
+  double un_a = ua[DIR];
+  // FP32 local LF speeds
+  float lam0 = 0.f, lam1 = 0.f, lam4 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    long long nn = n + (q - 2) * st;
+    float un = __ldg(velf[DIR] + nn), cs = __ldg(F.c + nn);
+    lam0 = fmaxf(lam0, fabsf(un - cs));
+    lam1 = fmaxf(lam1, fabsf(un));
+    lam4 = fmaxf(lam4, fabsf(un + cs));
+  }
+  const float uat1 = (float)ua[T1], uat2 = (float)ua[T2];
+  float gp[5][6], gm[5][6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    long long nn = n + (q - 2) * st;
+    double rho = __ldg(P.rho + nn);
+    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
+    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
+    double un = uu[DIR];
+    double run = rho * un;
+    double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
+    double K = b2 + b1 * (H - udot);
+    double b1p = b1 * p;
+    double Aw = rho * K - b1p;
+    double Af = run * K - b1p * un_a;
+    double du = un_a - un;
+    double Bw = (rho * ic) * du;
+    double Bf = (run * du - p) * ic;
+    float Sw = (float)(Aw + Bw), Sf = (float)(Af + Bf), Dw = (float)(Aw - Bw), Df = (float)(Af - Bf);
+    float Awf = (float)Aw, Aff = (float)Af;
+    float rhof = __ldg(F.rho + nn), unf = __ldg(velf[DIR] + nn);
+    float runf = rhof * unf;
+    gp[0][q] = fmaf(lam0, Sw, Sf);
+    gm[0][q] = fmaf(-lam0, Sw, Sf);
+    gp[4][q] = fmaf(lam4, Dw, Df);
+    gm[4][q] = fmaf(-lam4, Dw, Df);
+    float r1 = fmaf(lam1, rhof, runf), r2 = fmaf(-lam1, rhof, runf);
+    gp[1][q] = r1 - fmaf(lam1, Awf, Aff);
+    gm[1][q] = r2 - fmaf(-lam1, Awf, Aff);
+    float d1 = __ldg(velf[T1] + nn) - uat1, d2 = __ldg(velf[T2] + nn) - uat2;
+    gp[2][q] = d1 * r1;
+    gm[2][q] = d1 * r2;
+    gp[3][q] = d2 * r1;
+    gm[3][q] = d2 * r2;
+  }
+  const float eps = C.k32.weno_eps;
+  float g[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const bool acoustic = (k == 0 || k == 4);
+    const float eps4 = (acoustic ? 64.f : 16.f) * eps;  // 4 s_k^2 eps
+    float v = weno5_f(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4) +
+              weno5_f(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4);
+    g[k] = (acoustic ? 0.25f : 0.5f) * v;
+  }
+  const float uaf[3] = {(float)ua[0], (float)ua[1], (float)ua[2]};
+  const float caf = (float)ca, Haf = (float)Ha, q2f = (float)q2, unaf = (float)un_a;
+  float gs = g[0] + g[1] + g[4];
+  f[0] = gs;
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) f[1 + dd] = gs * uaf[dd];
+  f[1 + DIR] += caf * (g[4] - g[0]);
+  f[1 + T1] += g[2];
+  f[1 + T2] += g[3];
+  f[4] = Haf * (g[0] + g[4]) + unaf * caf * (g[4] - g[0]) + 0.5f * q2f * g[1] + uaf[T1] * g[2] +
+         uaf[T2] * g[3];
+}
+
 // ------------------------------------------------------------------------------ face kernels
 
 // Warp-aggregated append of face q to a compacted list: one atomic per warp and list.
@@ -216,55 +330,61 @@ __device__ __forceinline__ void warp_append(bool mine, unsigned act, int* list, 
 
 // Hybrid switch, sensor mode: split the faces of one direction into a WENO list and a central
 // list, so that each flux kernel runs without warp divergence whatever the flagged fraction.
-template <int L, int DIR>
+template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_classify(Dims d, Consts C, Bufs B) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.nf[DIR]) return;
   int i, j, k;
   face_node<DIR>(d, q, i, j, k);
-  bool fl = face_flag<L>(C, B.theta, gidx(d, i, j, k), dir_stride(d, DIR));
+  bool fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
   unsigned act = __activemask();
   warp_append(fl, act, B.wl[DIR], B.wcount + DIR, (int)q);
   warp_append(!fl, act, B.cl[DIR], B.wcount + 4 + DIR, (int)q);
 }
 
 // Central flux at every face of one direction (WENO off) or at the faces of the central list.
-template <int L, int DIR>
+template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list) {
   long long cnt = use_list ? (long long)B.wcount[4 + DIR] : d.nf[DIR];
   long long nf = d.nf[DIR];
   long long st = dir_stride(d, DIR);
-  double* out = B.fh[DIR];
+  R* out = face_flux<R>(B, DIR);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
        t += (long long)gridDim.x * blockDim.x) {
     long long q = use_list ? (long long)B.cl[DIR][t] : t;
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
-    double f[5];
-    central_flux<L, DIR>(C, B, gidx(d, i, j, k), st, f);
+    R f[5];
+    central_flux<L, DIR, R>(C, B, gidx(d, i, j, k), st, f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c * nf + q] = f[c];
   }
 }
 
 // Characteristic WENO flux at the faces of the WENO list (sensor mode) or at every face (WENO
-// everywhere).
-template <int DIR>
+// everywhere); FP64, or the mixed-precision variant writing FP32 face fluxes.
+template <int DIR, bool MIXED>
 __global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
   const bool all = C.weno_mode == 2;
   long long nf = d.nf[DIR];
   long long cnt = all ? nf : (long long)B.wcount[DIR];
   long long st = dir_stride(d, DIR);
-  double* out = B.fh[DIR];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
        t += (long long)gridDim.x * blockDim.x) {
     long long q = all ? t : (long long)B.wl[DIR][t];
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
-    double f[5];
-    weno_flux<DIR>(C, B, gidx(d, i, j, k), st, f);
+    if (MIXED) {
+      float f[5];
+      weno_flux_mixed<DIR>(C, B, gidx(d, i, j, k), st, f);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) out[c * nf + q] = f[c];
+      for (int c = 0; c < 5; ++c) B.fh32[DIR][c * nf + q] = f[c];
+    } else {
+      double f[5];
+      weno_flux<DIR>(C, B, gidx(d, i, j, k), st, f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) B.fh64[DIR][c * nf + q] = f[c];
+    }
   }
 }
 
@@ -275,25 +395,28 @@ __global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
 //   V_E = u_i V_i + sigma_ij d_j u_i + k lap T + d_j k d_j T,  k = cp mu / Pr,
 // first and second derivatives of order 2L; along y, d/dy = (1/y_eta) d/deta and
 // d2/dy2 = (f_etaeta - (y_etaeta/y_eta) f_eta)/y_eta^2; d_i(div) from the ghost-filled div.
-template <int L>
+template <int L, typename R>
 __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, const Dims& d, long long n,
-                                             int j, double* V) {
+                                             int j, R* V) {
+  const Nodes<R>& P = nodes<R>(B);
+  const Coefs<R>& K = coefs<R>(C);
+  const Metric<R>& M = metric<R>(B);
   const long long sy = d.px, sz = d.plane;
-  const double hy = __ldg(B.inv_hy + j), c2 = __ldg(B.c2y + j), c1 = __ldg(B.c1y + j);
-  const double* __restrict__ fld[4] = {B.u, B.v, B.w, B.T};
-  double du[3][3], lap[3], dT[3], lapT = 0.0;
+  const R hy = __ldg(M.inv_hy + j), c2 = __ldg(M.c2y + j), c1 = __ldg(M.c1y + j);
+  const R* __restrict__ fld[4] = {P.u, P.v, P.w, P.T};
+  R du[3][3], lap[3], dT[3], lapT = R(0);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    double s1, s2, d0, d1v, d2v, l0;
-    dsum12<L>(fld[a], n, 1, C.a, C.b, s1, s2);
-    d0 = s1 * C.inv_dx;
-    l0 = s2 * C.inv_dx2;
-    dsum12<L>(fld[a], n, sy, C.a, C.b, s1, s2);
+    R s1, s2, d0, d1v, d2v, l0;
+    dsum12<L>(fld[a], n, 1, K.a, K.b, s1, s2);
+    d0 = s1 * K.inv_dx;
+    l0 = s2 * K.inv_dx2;
+    dsum12<L>(fld[a], n, sy, K.a, K.b, s1, s2);
     d1v = s1 * hy;
     l0 += s2 * c2 - s1 * c1;
-    dsum12<L>(fld[a], n, sz, C.a, C.b, s1, s2);
-    d2v = s1 * C.inv_dz;
-    l0 += s2 * C.inv_dz2;
+    dsum12<L>(fld[a], n, sz, K.a, K.b, s1, s2);
+    d2v = s1 * K.inv_dz;
+    l0 += s2 * K.inv_dz2;
     if (a < 3) {
       du[a][0] = d0;
       du[a][1] = d1v;
@@ -306,41 +429,43 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
       lapT = l0;
     }
   }
-  double dmu[3], ddiv[3];
-  dmu[0] = dsum<L>(B.mu, n, 1, C.a) * C.inv_dx;
-  dmu[1] = dsum<L>(B.mu, n, sy, C.a) * hy;
-  dmu[2] = dsum<L>(B.mu, n, sz, C.a) * C.inv_dz;
-  ddiv[0] = dsum<L>(B.div, n, 1, C.a) * C.inv_dx;
-  ddiv[1] = dsum<L>(B.div, n, sy, C.a) * hy;
-  ddiv[2] = dsum<L>(B.div, n, sz, C.a) * C.inv_dz;
-  const double mu = __ldg(B.mu + n);
-  const double div = du[0][0] + du[1][1] + du[2][2];
-  double Vm[3];
+  R dmu[3], ddiv[3];
+  dmu[0] = dsum<L>(P.mu, n, 1, K.a) * K.inv_dx;
+  dmu[1] = dsum<L>(P.mu, n, sy, K.a) * hy;
+  dmu[2] = dsum<L>(P.mu, n, sz, K.a) * K.inv_dz;
+  ddiv[0] = dsum<L>(P.div, n, 1, K.a) * K.inv_dx;
+  ddiv[1] = dsum<L>(P.div, n, sy, K.a) * hy;
+  ddiv[2] = dsum<L>(P.div, n, sz, K.a) * K.inv_dz;
+  const R mu = __ldg(P.mu + n);
+  const R div = du[0][0] + du[1][1] + du[2][2];
+  R Vm[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double s = dmu[0] * (du[a][0] + du[0][a]) + dmu[1] * (du[a][1] + du[1][a]) +
-               dmu[2] * (du[a][2] + du[2][a]);
-    Vm[a] = mu * lap[a] + mu * ddiv[a] * (1.0 / 3.0) + s - (2.0 / 3.0) * div * dmu[a];
+    R s = dmu[0] * (du[a][0] + du[0][a]) + dmu[1] * (du[a][1] + du[1][a]) +
+          dmu[2] * (du[a][2] + du[2][a]);
+    Vm[a] = mu * lap[a] + mu * ddiv[a] * R(1.0 / 3.0) + s - R(2.0 / 3.0) * div * dmu[a];
   }
-  const double uu[3] = {__ldg(B.u + n), __ldg(B.v + n), __ldg(B.w + n)};
-  double work = uu[0] * Vm[0] + uu[1] * Vm[1] + uu[2] * Vm[2];
+  const R uu[3] = {__ldg(P.u + n), __ldg(P.v + n), __ldg(P.w + n)};
+  R work = uu[0] * Vm[0] + uu[1] * Vm[1] + uu[2] * Vm[2];
   // sigma_ij d_j u_i = mu [ sum_ij (d_j u_i + d_i u_j) d_j u_i - 2/3 div^2 ]
-  double diss = 0.0;
+  R diss = R(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) diss += (du[a][b] + du[b][a]) * du[a][b];
-  diss = mu * (diss - (2.0 / 3.0) * div * div);
-  double heat = C.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
-  V[0] = 0.0;
+  diss = mu * (diss - R(2.0 / 3.0) * div * div);
+  R heat = K.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
+  V[0] = R(0);
   V[1] = Vm[0];
   V[2] = Vm[1];
   V[3] = Vm[2];
   V[4] = work + diss + heat;
 }
 
-template <int L>
-__global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, double* __restrict__ R) {
+// Residual per node: R = -sum_d (f_{s+1} - f_s)/h_d (Eq. num_flux, with the staggered-wall rule)
+// plus the viscous terms, in precision R; stored in FP64 with the forcing partial sums.
+template <int L, typename R>
+__global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, double* __restrict__ Rout) {
   __shared__ double sh[32];
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double fpart = 0.0;
@@ -349,38 +474,49 @@ __global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, doub
     long long r = q / d.nx;
     int j = (int)(r % d.ny);
     int k = (int)(r / d.ny);
-    double res[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const Coefs<R>& K = coefs<R>(C);
+    R res[5] = {R(0), R(0), R(0), R(0), R(0)};
+    double mass64 = 0.0;
     if (C.convective) {
       long long qx = ((long long)k * d.ny + j) * (d.nx + 1) + i;
       long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
       long long qz = ((long long)k * d.ny + j) * d.nx + i;
       long long sxy = (long long)d.nx * d.ny;
-      double hy = __ldg(B.inv_hy + j);
+      R hy = __ldg(metric<R>(B).inv_hy + j);
       bool wlo = C.wall_y && j == 0, whi = C.wall_y && j == d.ny - 1;
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        const double* fx = B.fh[0] + m * d.nf[0];
-        const double* fy = B.fh[1] + m * d.nf[1];
-        const double* fz = B.fh[2] + m * d.nf[2];
-        double ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
+        const R* fx = face_flux<R>(B, 0) + m * d.nf[0];
+        const R* fy = face_flux<R>(B, 1) + m * d.nf[1];
+        const R* fz = face_flux<R>(B, 2) + m * d.nf[2];
+        R ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
         // staggered wall interface: no mass, x/z momentum or energy crosses it
         if (m != 2) {
-          if (wlo) ylo = 0.0;
-          if (whi) yhi = 0.0;
+          if (wlo) ylo = R(0);
+          if (whi) yhi = R(0);
         }
-        res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * C.inv_dx + (yhi - ylo) * hy +
-                   (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * C.inv_dz);
+        res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
+                   (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * K.inv_dz);
+        if (m == 0 && sizeof(R) != sizeof(double)) {
+          // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
+          // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
+          // FP64 round-off as in the FP64 path
+          mass64 = -(((double)__ldg(fx + qx + 1) - (double)__ldg(fx + qx)) * C.k64.inv_dx +
+                     ((double)yhi - (double)ylo) * __ldg(B.m64.inv_hy + j) +
+                     ((double)__ldg(fz + qz + sxy) - (double)__ldg(fz + qz)) * C.k64.inv_dz);
+        }
       }
     }
     if (C.viscous) {
-      double V[5];
-      viscous_node<L>(C, B, d, gidx(d, i, j, k), j, V);
+      R V[5];
+      viscous_node<L, R>(C, B, d, gidx(d, i, j, k), j, V);
 #pragma unroll
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }
 #pragma unroll
-    for (int m = 0; m < 5; ++m) R[m * d.N + q] = res[m];
-    fpart = res[1] * __ldg(B.vol + j);
+    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = (double)res[m];
+    if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
+    fpart = (double)res[1] * __ldg(B.vol + j);
   }
   if (C.forcing) {
     double s = block_sum(fpart, sh);
@@ -392,40 +528,57 @@ __global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, doub
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+template <int L, int DIR, typename R>
+static void faces_one(const Dims& d, const Consts& C, const Bufs& B, bool sensor, unsigned nb, int grid,
+                      cudaStream_t s) {
+  if (sensor) k_classify<L, DIR, R><<<nb, 256, 0, s>>>(d, C, B);
+  k_central<L, DIR, R><<<sensor ? (unsigned)grid : nb, 256, 0, s>>>(d, C, B, sensor ? 1 : 0);
+}
+
+template <int L, typename R>
+static void faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, bool sensor, unsigned nb,
+                      int grid, cudaStream_t s) {
+  if (dir == 0) faces_one<L, 0, R>(d, C, B, sensor, nb, grid, s);
+  else if (dir == 1) faces_one<L, 1, R>(d, C, B, sensor, nb, grid, s);
+  else faces_one<L, 2, R>(d, C, B, sensor, nb, grid, s);
+}
+
 // Face stage of one direction: sensor mode classifies then runs the central list; WENO off runs
 // the central flux over every face; WENO everywhere needs no central flux.
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {
   if (C.weno_mode == 2) return;
   bool sensor = C.weno_mode == 1;
   unsigned nb = blocks_for(d.nf[dir], 256);
-#define STRM_FACES(LL, DD)                                              \
-  do {                                                                  \
-    if (sensor) k_classify<LL, DD><<<nb, 256, 0, s>>>(d, C, B);         \
-    k_central<LL, DD><<<sensor ? (unsigned)grid : nb, 256, 0, s>>>(d, C, B, sensor ? 1 : 0); \
-  } while (0)
-  if (C.L == 3) {
-    if (dir == 0) STRM_FACES(3, 0);
-    else if (dir == 1) STRM_FACES(3, 1);
-    else STRM_FACES(3, 2);
+  if (C.mixed) {
+    if (C.L == 3) faces_dir<3, float>(d, C, B, dir, sensor, nb, grid, s);
+    else faces_dir<2, float>(d, C, B, dir, sensor, nb, grid, s);
   } else {
-    if (dir == 0) STRM_FACES(2, 0);
-    else if (dir == 1) STRM_FACES(2, 1);
-    else STRM_FACES(2, 2);
+    if (C.L == 3) faces_dir<3, double>(d, C, B, dir, sensor, nb, grid, s);
+    else faces_dir<2, double>(d, C, B, dir, sensor, nb, grid, s);
   }
-#undef STRM_FACES
 }
 
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {
-  if (dir == 0) k_weno<0><<<grid, 128, 0, s>>>(d, C, B);
-  else if (dir == 1) k_weno<1><<<grid, 128, 0, s>>>(d, C, B);
-  else k_weno<2><<<grid, 128, 0, s>>>(d, C, B);
+  if (C.mixed) {
+    if (dir == 0) k_weno<0, true><<<grid, 128, 0, s>>>(d, C, B);
+    else if (dir == 1) k_weno<1, true><<<grid, 128, 0, s>>>(d, C, B);
+    else k_weno<2, true><<<grid, 128, 0, s>>>(d, C, B);
+  } else {
+    if (dir == 0) k_weno<0, false><<<grid, 128, 0, s>>>(d, C, B);
+    else if (dir == 1) k_weno<1, false><<<grid, 128, 0, s>>>(d, C, B);
+    else k_weno<2, false><<<grid, 128, 0, s>>>(d, C, B);
+  }
 }
 
 void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, cudaStream_t s) {
-  if (C.L == 3)
-    k_assemble<3><<<blocks_for(d.N, kRedBlock), kRedBlock, 0, s>>>(d, C, B, R);
-  else
-    k_assemble<2><<<blocks_for(d.N, kRedBlock), kRedBlock, 0, s>>>(d, C, B, R);
+  unsigned nb = blocks_for(d.N, kRedBlock);
+  if (C.mixed) {
+    if (C.L == 3) k_assemble<3, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+    else k_assemble<2, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+  } else {
+    if (C.L == 3) k_assemble<3, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+    else k_assemble<2, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+  }
 }
 
 }  // namespace strm

@@ -29,6 +29,7 @@ void launch_apply_forcing(const Dims& d, const Bufs& B, double* rhs, cudaStream_
 void launch_totals(const Dims& d, const Bufs& B, const double* w, cudaStream_t s);
 void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsigned char* out,
                   cudaStream_t s);
-void launch_export_interior(const Dims& d, const double* src, double* dst, cudaStream_t s);
+void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double* theta, double* div,
+                          cudaStream_t s);
 
 }  // namespace strm

@@ -7,19 +7,25 @@ namespace strm {
 
 // ---------------------------------------------------------------------------------- primitives
 
+__device__ __forceinline__ void node_ijk(const Dims& d, long long q, int& i, int& j, int& k) {
+  i = (int)(q % d.nx);
+  long long r = q / d.nx;
+  j = (int)(r % d.ny);
+  k = (int)(r / d.ny);
+}
+
 // Primitive variables at the interior nodes from w = [rho, rho u, rho v, rho w, rho E]
-// (Section 2: E = cv T + |u|^2/2, p = rho R T, H = E + p/rho), plus c and mu(T). With
-// want_cfl, each block also writes the largest sum_d (|u_d| + c)/h_d of its nodes.
+// (Section 2: E = cv T + |u|^2/2, p = rho R T, H = E + p/rho), plus c, mu(T) and sqrt(rho).
+// With want_cfl, each block also writes the largest sum_d (|u_d| + c)/h_d of its nodes.
 __global__ void __launch_bounds__(256) k_prims(Dims d, Consts C, Bufs B, const double* __restrict__ w,
                                                int want_cfl) {
   __shared__ double sh[32];
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double spec = 0.0;
   if (q < d.N) {
-    int i = (int)(q % d.nx);
-    long long r = q / d.nx;
-    int j = (int)(r % d.ny);
-    int k = (int)(r / d.ny);
+    int i, j, k;
+    node_ijk(d, q, i, j, k);
+    const Nodes<double>& P = B.n64;
     double rho = w[q];
     double ir = 1.0 / rho;
     double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
@@ -28,18 +34,69 @@ __global__ void __launch_bounds__(256) k_prims(Dims d, Consts C, Bufs B, const d
     double p = rho * C.r_gas * T;
     double c = sqrt(C.gamma * p * ir);
     long long n = gidx(d, i, j, k);
-    B.rho[n] = rho;
-    B.u[n] = u;
-    B.v[n] = v;
-    B.w[n] = ww;
-    B.T[n] = T;
-    B.p[n] = p;
-    B.H[n] = E + p * ir;
-    B.c[n] = c;
-    B.mu[n] = viscosity(C, T);
-    B.srho[n] = sqrt(rho);
+    P.rho[n] = rho;
+    P.u[n] = u;
+    P.v[n] = v;
+    P.w[n] = ww;
+    P.T[n] = T;
+    P.p[n] = p;
+    P.H[n] = E + p * ir;
+    P.c[n] = c;
+    P.mu[n] = viscosity(C.k64, C.visc_law, T);
+    P.srho[n] = sqrt(rho);
     if (want_cfl)
-      spec = (fabs(u) + c) * C.inv_dx + (fabs(v) + c) * B.inv_hy[j] + (fabs(ww) + c) * C.inv_dz;
+      spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
+  }
+  if (want_cfl) {
+    double m = block_max(spec, sh);
+    if (threadIdx.x == 0) B.red[blockIdx.x] = m;
+  }
+}
+
+// Mixed precision: the fields the characteristic projection reads are formed in FP64 (rho, u,
+// v, w, p, T, H, sqrt rho); FP32 copies of all fields feed the FP32 kernels, with c and mu(T)
+// evaluated in FP32. The CFL partial is formed in FP64 from the FP64 velocities.
+__global__ void __launch_bounds__(256) k_prims_mixed(Dims d, Consts C, Bufs B, const double* __restrict__ w,
+                                                     int want_cfl) {
+  __shared__ double sh[32];
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double spec = 0.0;
+  if (q < d.N) {
+    int i, j, k;
+    node_ijk(d, q, i, j, k);
+    const Nodes<double>& P = B.n64;
+    const Nodes<float>& F = B.n32;
+    double rho = w[q];
+    double ir = 1.0 / rho;
+    double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
+    double E = w[4 * d.N + q] * ir;
+    double T = (E - 0.5 * (u * u + v * v + ww * ww)) * C.inv_cv;
+    double p = rho * C.r_gas * T;
+    double H = E + p * ir;
+    long long n = gidx(d, i, j, k);
+    P.rho[n] = rho;
+    P.u[n] = u;
+    P.v[n] = v;
+    P.w[n] = ww;
+    P.T[n] = T;
+    P.p[n] = p;
+    P.H[n] = H;
+    P.srho[n] = sqrt(rho);
+    float rf = (float)rho, pf = (float)p, Tf = (float)T;
+    float cf = sqrtf(C.k32.gamma * pf / rf);
+    F.rho[n] = rf;
+    F.u[n] = (float)u;
+    F.v[n] = (float)v;
+    F.w[n] = (float)ww;
+    F.p[n] = pf;
+    F.T[n] = Tf;
+    F.H[n] = (float)H;
+    F.c[n] = cf;
+    F.mu[n] = viscosity(C.k32, C.visc_law, Tf);
+    if (want_cfl) {
+      double c = (double)cf;
+      spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
+    }
   }
   if (want_cfl) {
     double m = block_max(spec, sh);
@@ -63,38 +120,6 @@ __global__ void k_dt_finalize(Bufs B, int nparts, double cfl, double dt_fixed) {
 }
 
 // ---------------------------------------------------------------------------------- ghost fills
-
-__device__ __forceinline__ void copy_prims(const Bufs& B, long long dst, long long src) {
-  B.rho[dst] = B.rho[src];
-  B.u[dst] = B.u[src];
-  B.v[dst] = B.v[src];
-  B.w[dst] = B.w[src];
-  B.p[dst] = B.p[src];
-  B.T[dst] = B.T[src];
-  B.H[dst] = B.H[src];
-  B.c[dst] = B.c[src];
-  B.mu[dst] = B.mu[src];
-  B.srho[dst] = B.srho[src];
-}
-
-// Isothermal no-slip staggered wall: the ghost mirrors an interior node across the wall
-// interface with reversed velocity, T_g = 2 T_w - T, p_g = p, rho_g = p_g/(R T_g).
-__device__ __forceinline__ void wall_prims(const Consts& C, const Bufs& B, long long dst, long long src) {
-  double u = -B.u[src], v = -B.v[src], w = -B.w[src];
-  double p = B.p[src];
-  double T = 2.0 * C.t_wall - B.T[src];
-  double rho = p / (C.r_gas * T);
-  B.rho[dst] = rho;
-  B.u[dst] = u;
-  B.v[dst] = v;
-  B.w[dst] = w;
-  B.p[dst] = p;
-  B.T[dst] = T;
-  B.H[dst] = C.cp * T + 0.5 * (u * u + v * v + w * w);
-  B.c[dst] = sqrt(C.gamma * p / rho);
-  B.mu[dst] = viscosity(C, T);
-  B.srho[dst] = sqrt(rho);
-}
 
 // Thread layout of a face ghost fill: x faces (2G * ny * nz), then y faces (nx * 2G * nz), then
 // z faces (nx * ny * 2G). Edges and corners are never read and stay untouched.
@@ -144,60 +169,129 @@ __device__ __forceinline__ bool ghost_target(const Dims& d, long long q, int& fa
   return false;
 }
 
+template <typename R>
+__device__ __forceinline__ void copy_node(const Nodes<R>& P, long long dst, long long src, bool cmu) {
+  P.rho[dst] = P.rho[src];
+  P.u[dst] = P.u[src];
+  P.v[dst] = P.v[src];
+  P.w[dst] = P.w[src];
+  P.p[dst] = P.p[src];
+  P.T[dst] = P.T[src];
+  P.H[dst] = P.H[src];
+  if (cmu) {
+    P.c[dst] = P.c[src];
+    P.mu[dst] = P.mu[src];
+  }
+}
+
+// Isothermal no-slip staggered wall: the ghost mirrors an interior node across the wall
+// interface with reversed velocity, T_g = 2 T_w - T, p_g = p, rho_g = p_g/(R T_g).
+struct WallGhost {
+  double rho, u, v, w, p, T, H;
+};
+
+__device__ __forceinline__ WallGhost wall_state(const Consts& C, const Nodes<double>& P, long long src) {
+  WallGhost g;
+  g.u = -P.u[src];
+  g.v = -P.v[src];
+  g.w = -P.w[src];
+  g.p = P.p[src];
+  g.T = 2.0 * C.t_wall - P.T[src];
+  g.rho = g.p / (C.r_gas * g.T);
+  g.H = C.cp * g.T + 0.5 * (g.u * g.u + g.v * g.v + g.w * g.w);
+  return g;
+}
+
+__device__ __forceinline__ void store_wall64(const Nodes<double>& P, long long dst, const WallGhost& g) {
+  P.rho[dst] = g.rho;
+  P.u[dst] = g.u;
+  P.v[dst] = g.v;
+  P.w[dst] = g.w;
+  P.p[dst] = g.p;
+  P.T[dst] = g.T;
+  P.H[dst] = g.H;
+  P.srho[dst] = sqrt(g.rho);
+}
+
 __global__ void __launch_bounds__(256) k_ghost_prims(Dims d, Consts C, Bufs B, long long nthreads) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nthreads) return;
   int face, i, j, k, si, sj, sk, mirror;
   if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
+  const Nodes<double>& P = B.n64;
   long long dst = gidx(d, i, j, k);
-  if (face == 1 && C.wall_y)
-    wall_prims(C, B, dst, gidx(d, i, mirror, k));
-  else
-    copy_prims(B, dst, gidx(d, si, sj, sk));
+  if (face == 1 && C.wall_y) {
+    WallGhost g = wall_state(C, P, gidx(d, i, mirror, k));
+    store_wall64(P, dst, g);
+    P.c[dst] = sqrt(C.gamma * g.p / g.rho);
+    P.mu[dst] = viscosity(C.k64, C.visc_law, g.T);
+  } else {
+    long long src = gidx(d, si, sj, sk);
+    copy_node(P, dst, src, true);
+    P.srho[dst] = P.srho[src];
+  }
+}
+
+// Mixed precision: FP64 fields by the same rules, FP32 copies from them (c, mu in FP32).
+__global__ void __launch_bounds__(256) k_ghost_prims_mixed(Dims d, Consts C, Bufs B, long long nthreads) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nthreads) return;
+  int face, i, j, k, si, sj, sk, mirror;
+  if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
+  const Nodes<double>& P = B.n64;
+  const Nodes<float>& F = B.n32;
+  long long dst = gidx(d, i, j, k);
+  if (face == 1 && C.wall_y) {
+    WallGhost g = wall_state(C, P, gidx(d, i, mirror, k));
+    store_wall64(P, dst, g);
+    float rf = (float)g.rho, pf = (float)g.p, Tf = (float)g.T;
+    F.rho[dst] = rf;
+    F.u[dst] = (float)g.u;
+    F.v[dst] = (float)g.v;
+    F.w[dst] = (float)g.w;
+    F.p[dst] = pf;
+    F.T[dst] = Tf;
+    F.H[dst] = (float)g.H;
+    F.c[dst] = sqrtf(C.k32.gamma * pf / rf);
+    F.mu[dst] = viscosity(C.k32, C.visc_law, Tf);
+  } else {
+    long long src = gidx(d, si, sj, sk);
+    copy_node(P, dst, src, false);
+    P.srho[dst] = P.srho[src];
+    copy_node(F, dst, src, true);
+  }
 }
 
 // theta and the node divergence: periodic copies, even mirror across a wall.
+template <typename R>
 __global__ void __launch_bounds__(256) k_ghost_scalars(Dims d, Consts C, Bufs B, long long nthreads) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nthreads) return;
   int face, i, j, k, si, sj, sk, mirror;
   if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
+  const Nodes<R>& P = nodes<R>(B);
   long long dst = gidx(d, i, j, k);
   long long src = (face == 1 && C.wall_y) ? gidx(d, i, mirror, k) : gidx(d, si, sj, sk);
-  B.theta[dst] = B.theta[src];
-  B.div[dst] = B.div[src];
+  P.theta[dst] = P.theta[src];
+  P.div[dst] = P.div[src];
 }
 
 // ---------------------------------------------------------------------------------- sensor
 
-// Ducros sensor (Eq. sensor): theta = max(-div / sqrt(div^2 + |curl u|^2 + (u0/L0)^2), 0) with
-// first derivatives of order 2L; the node divergence is kept for the viscous terms.
-template <int L>
+// Ducros sensor (Eq. sensor) at the interior nodes; the node divergence is kept for the
+// viscous terms.
+template <int L, typename R>
 __global__ void __launch_bounds__(256) k_sensor(Dims d, Consts C, Bufs B) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.N) return;
-  int i = (int)(q % d.nx);
-  long long r = q / d.nx;
-  int j = (int)(r % d.ny);
-  int k = (int)(r / d.ny);
+  int i, j, k;
+  node_ijk(d, q, i, j, k);
+  const Nodes<R>& P = nodes<R>(B);
+  R div;
+  R th = theta_node<L, R>(d, C, B, i, j, k, div);
   long long n = gidx(d, i, j, k);
-  long long sy = d.px, sz = d.plane;
-  double hy = B.inv_hy[j];
-  double ux = dsum<L>(B.u, n, 1, C.a) * C.inv_dx;
-  double uy = dsum<L>(B.u, n, sy, C.a) * hy;
-  double uz = dsum<L>(B.u, n, sz, C.a) * C.inv_dz;
-  double vx = dsum<L>(B.v, n, 1, C.a) * C.inv_dx;
-  double vy = dsum<L>(B.v, n, sy, C.a) * hy;
-  double vz = dsum<L>(B.v, n, sz, C.a) * C.inv_dz;
-  double wx = dsum<L>(B.w, n, 1, C.a) * C.inv_dx;
-  double wy = dsum<L>(B.w, n, sy, C.a) * hy;
-  double wz = dsum<L>(B.w, n, sz, C.a) * C.inv_dz;
-  double div = ux + vy + wz;
-  double o1 = wy - vz, o2 = uz - wx, o3 = vx - uy;
-  double den = sqrt(div * div + (o1 * o1 + o2 * o2 + o3 * o3) + C.sens_eps);
-  double th = -div / den;
-  B.theta[n] = th > 0.0 ? th : 0.0;
-  B.div[n] = div;
+  P.theta[n] = th;
+  P.div[n] = div;
 }
 
 // ---------------------------------------------------------------------------------- RK, forcing
@@ -212,7 +306,8 @@ __global__ void k_force_finalize(Bufs B, int nparts, double inv_vtot) {
 }
 
 // Stage update of Eq. RK: w <- w + dt (alpha R_old + beta R), R includes the forcing terms
-// R_rhou += f, R_rhoE += f u (Eqs. 1b, 1c); R_old <- R. One thread per node, five fields.
+// R_rhou += f, R_rhoE += f u (Eqs. 1b, 1c); R_old <- R. One thread per node, five fields. FP64
+// in both precisions.
 __global__ void __launch_bounds__(256) k_rk_update(Dims d, Consts C, Bufs B, double* __restrict__ w,
                                                    double* __restrict__ r_old, double alpha,
                                                    double beta) {
@@ -223,9 +318,9 @@ __global__ void __launch_bounds__(256) k_rk_update(Dims d, Consts C, Bufs B, dou
   double ad = alpha * dt, bd = beta * dt;
   double uq = 0.0;
   if (C.forcing) {
-    int i = (int)(q % d.nx);
-    long long r = q / d.nx;
-    uq = B.u[gidx(d, i, (int)(r % d.ny), (int)(r / d.ny))];
+    int i, j, k;
+    node_ijk(d, q, i, j, k);
+    uq = B.n64.u[gidx(d, i, j, k)];
   }
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
@@ -245,9 +340,9 @@ __global__ void __launch_bounds__(256) k_apply_forcing(Dims d, Bufs B, double* _
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.N) return;
   double f = B.scal[kScalForce];
-  int i = (int)(q % d.nx);
-  long long r = q / d.nx;
-  double uq = B.u[gidx(d, i, (int)(r % d.ny), (int)(r / d.ny))];
+  int i, j, k;
+  node_ijk(d, q, i, j, k);
+  double uq = B.n64.u[gidx(d, i, j, k)];
   rhs[d.N + q] += f;
   rhs[4 * d.N + q] += f * uq;
 }
@@ -279,7 +374,7 @@ __global__ void k_totals_finalize(Bufs B, int nparts) {
 // ---------------------------------------------------------------------------------- flags, copies
 
 // WENO face flags in the export layout (x: [nz][ny][nx+1], y: [nz][ny+1][nx], z: [nz+1][ny][nx]).
-template <int L>
+template <int L, typename R>
 __global__ void __launch_bounds__(256) k_flags(Dims d, Consts C, Bufs B, int dir, unsigned char* out) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.nf[dir]) return;
@@ -297,16 +392,17 @@ __global__ void __launch_bounds__(256) k_flags(Dims d, Consts C, Bufs B, int dir
     long long r = q / d.nx;
     j = (int)(r % d.ny); k = (int)(r / d.ny) - 1;
   }
-  out[q] = face_flag<L>(C, B.theta, gidx(d, i, j, k), dir_stride(d, dir)) ? 1 : 0;
+  out[q] = face_decision<L, R>(d, C, B, i, j, k, dir) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(256) k_export_interior(Dims d, const double* __restrict__ src,
+template <typename R>
+__global__ void __launch_bounds__(256) k_export_interior(Dims d, const R* __restrict__ src,
                                                          double* __restrict__ dst) {
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.N) return;
-  int i = (int)(q % d.nx);
-  long long r = q / d.nx;
-  dst[q] = src[gidx(d, i, (int)(r % d.ny), (int)(r / d.ny))];
+  int i, j, k;
+  node_ijk(d, q, i, j, k);
+  dst[q] = (double)src[gidx(d, i, j, k)];
 }
 
 // ---------------------------------------------------------------------------------- launchers
@@ -317,7 +413,10 @@ int reduce_blocks(const Dims& d) { return (int)blocks_for(d.N, kRedBlock); }
 
 void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w, bool want_cfl,
                   cudaStream_t s) {
-  k_prims<<<blocks_for(d.N, kRedBlock), kRedBlock, 0, s>>>(d, C, B, w, want_cfl ? 1 : 0);
+  if (C.mixed)
+    k_prims_mixed<<<blocks_for(d.N, kRedBlock), kRedBlock, 0, s>>>(d, C, B, w, want_cfl ? 1 : 0);
+  else
+    k_prims<<<blocks_for(d.N, kRedBlock), kRedBlock, 0, s>>>(d, C, B, w, want_cfl ? 1 : 0);
 }
 
 void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixed, cudaStream_t s) {
@@ -330,19 +429,29 @@ static long long ghost_threads(const Dims& d) {
 
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
   long long n = ghost_threads(d);
-  k_ghost_prims<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+  if (C.mixed)
+    k_ghost_prims_mixed<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+  else
+    k_ghost_prims<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
 }
 
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
-  if (C.L == 3)
-    k_sensor<3><<<blocks_for(d.N, 256), 256, 0, s>>>(d, C, B);
-  else
-    k_sensor<2><<<blocks_for(d.N, 256), 256, 0, s>>>(d, C, B);
+  unsigned nb = blocks_for(d.N, 256);
+  if (C.mixed) {
+    if (C.L == 3) k_sensor<3, float><<<nb, 256, 0, s>>>(d, C, B);
+    else k_sensor<2, float><<<nb, 256, 0, s>>>(d, C, B);
+  } else {
+    if (C.L == 3) k_sensor<3, double><<<nb, 256, 0, s>>>(d, C, B);
+    else k_sensor<2, double><<<nb, 256, 0, s>>>(d, C, B);
+  }
 }
 
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
   long long n = ghost_threads(d);
-  k_ghost_scalars<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+  if (C.mixed)
+    k_ghost_scalars<float><<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+  else
+    k_ghost_scalars<double><<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
 }
 
 void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
@@ -366,14 +475,26 @@ void launch_totals(const Dims& d, const Bufs& B, const double* w, cudaStream_t s
 
 void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsigned char* out,
                   cudaStream_t s) {
-  if (C.L == 3)
-    k_flags<3><<<blocks_for(d.nf[dir], 256), 256, 0, s>>>(d, C, B, dir, out);
-  else
-    k_flags<2><<<blocks_for(d.nf[dir], 256), 256, 0, s>>>(d, C, B, dir, out);
+  unsigned nb = blocks_for(d.nf[dir], 256);
+  if (C.mixed) {
+    if (C.L == 3) k_flags<3, float><<<nb, 256, 0, s>>>(d, C, B, dir, out);
+    else k_flags<2, float><<<nb, 256, 0, s>>>(d, C, B, dir, out);
+  } else {
+    if (C.L == 3) k_flags<3, double><<<nb, 256, 0, s>>>(d, C, B, dir, out);
+    else k_flags<2, double><<<nb, 256, 0, s>>>(d, C, B, dir, out);
+  }
 }
 
-void launch_export_interior(const Dims& d, const double* src, double* dst, cudaStream_t s) {
-  k_export_interior<<<blocks_for(d.N, 256), 256, 0, s>>>(d, src, dst);
+void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double* theta, double* div,
+                          cudaStream_t s) {
+  unsigned nb = blocks_for(d.N, 256);
+  if (C.mixed) {
+    if (theta) k_export_interior<float><<<nb, 256, 0, s>>>(d, B.n32.theta, theta);
+    if (div) k_export_interior<float><<<nb, 256, 0, s>>>(d, B.n32.div, div);
+  } else {
+    if (theta) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.theta, theta);
+    if (div) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.div, div);
+  }
 }
 
 }  // namespace strm

@@ -68,6 +68,7 @@ class Case:
     l0: float = 1.0              # sensor length scale (channel half height)
     convective: bool = True
     viscous: bool = True
+    precision: str = "fp64"      # "fp64", or "mixed" (FP32 flux arithmetic, FP64 state)
     cfl: float = 0.8
     steps: int = 20
     noise: float = 0.05          # uniform velocity noise amplitude (fraction of u_b)

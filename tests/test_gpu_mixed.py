@@ -1,0 +1,105 @@
+"""Mixed precision (FP32 flux, sensor, WENO and viscous arithmetic; FP64 state, projection into
+characteristic variables, RK accumulation and reductions) against the FP64 oracle.
+
+The stated error of the variant: with a continuous flux (central everywhere, or WENO everywhere)
+the relative L2 error per conserved field after 100 RK3 steps of the 64x48x32 channel is <= 1e-5.
+With the Ducros switch, FP32 rounding (~1e-7 after one step) eventually flips the central/WENO
+choice at faces whose sensor value sits at the threshold, which the grid-scale noise of this
+initial state makes common; each flip changes that face's flux by O(noise) and the difference
+spreads. Those runs are checked for the error before the first flips, for exact conservation,
+and the error reached after 100 steps is bounded and reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2004_02276_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel_l2(a, b):
+    return np.array([np.linalg.norm(a[m] - b[m]) / np.linalg.norm(b[m]) for m in range(5)])
+
+
+def profiles(w):
+    """Mean streamwise velocity and Reynolds stresses <u'u'>, <v'v'>, <w'w'>, <u'v'> over x, z."""
+    rho = w[0]
+    u, v, ww = w[1] / rho, w[2] / rho, w[3] / rho
+    um, vm, wm = (a.mean(axis=(0, 2), keepdims=True) for a in (u, v, ww))
+    up, vp, wp = u - um, v - vm, ww - wm
+    return np.stack([um[0, :, 0], (up * up).mean(axis=(0, 2)), (vp * vp).mean(axis=(0, 2)),
+                     (wp * wp).mean(axis=(0, 2)), (up * vp).mean(axis=(0, 2))])
+
+
+def test_mixed_rhs_close_to_oracle():
+    case = inputs.C1.replace(precision="mixed")
+    w0 = inputs.channel_state(case, seed=0)
+    ref = O.rhs(O.make_cfg(case), w0)
+    s = binding.Solver(case)
+    r = s.compute_rhs(torch.from_numpy(w0).cuda()).cpu().numpy()
+    s.close()
+    err = rel_l2(r, ref)
+    assert err.max() < 1e-4, err
+
+
+def run_both(case, nsteps):
+    w0 = inputs.channel_state(case, seed=0)
+    wo, to, _ = O.advance(O.make_cfg(case), w0, nsteps, cfl=case.cfl)
+    s = binding.Solver(case)
+    w = torch.from_numpy(w0).cuda()
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, nsteps, cfl=case.cfl)
+    t, _ = s.time()
+    wm = w.cpu().numpy()
+    s.close()
+    return wm, wo, t, to
+
+
+@pytest.mark.parametrize("mode", ["off", "all"])
+def test_mixed_hundred_steps_continuous_flux(mode):
+    case = inputs.C1.replace(precision="mixed", weno_mode=mode)
+    wm, wo, t, to = run_both(case, 100)
+    err = rel_l2(wm, wo)
+    assert err.max() <= 1e-5, err
+    assert abs(t - to) <= 1e-6 * to
+    pm, po = profiles(wm), profiles(wo)
+    perr = np.abs(pm - po).max(axis=1) / np.maximum(np.abs(po).max(axis=1), 1e-12)
+    assert perr.max() <= 1e-4, perr
+
+
+def test_mixed_sensor_switch():
+    case = inputs.C1.replace(precision="mixed")
+    wm, wo, _, _ = run_both(case, 1)
+    assert rel_l2(wm, wo).max() <= 1e-6  # before any switch flip: FP32 rounding only
+    wm, wo, t, to = run_both(case, 100)
+    err = rel_l2(wm, wo)
+    # the dense fields keep a small error; the velocity-noise fields (|rho v|, |rho w| ~ 0.01)
+    # carry the local differences of the flipped faces
+    assert max(err[0], err[1], err[4]) <= 2e-4, err
+    assert max(err[2], err[3]) <= 2e-2, err
+    print("mixed sensor-mode relative L2 error after 100 steps:", err)
+
+
+def test_mixed_conserves_mass_and_bulk_flow():
+    """Conservation does not depend on the arithmetic precision of the fluxes (telescoping and
+    the staggered wall), and the forcing is reduced in FP64."""
+    case = inputs.Case(nx=48, ny=32, nz=24, precision="mixed")
+    s = binding.Solver(case)
+    w = torch.from_numpy(inputs.channel_state(case, seed=2)).cuda()
+    t0 = np.array(s.totals(w))
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 10, cfl=0.8)
+    t1 = np.array(s.totals(w))
+    s.close()
+    assert abs(t1[0] - t0[0]) <= 1e-12 * t0[0]
+    assert abs(t1[1] - t0[1]) <= 1e-12 * t0[1]
