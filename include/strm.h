@@ -164,6 +164,44 @@ int strm_timing_read(strm_ctx* ctx, double* ms_host, long long* launches_host,
 /* Total kernels this context has launched (graph replays count every kernel in the graph). */
 int strm_launch_count(strm_ctx* ctx, long long* launches_host);
 
+/* ---- Batched ensemble: many independent grids advanced together (different sizes, gas and
+ * flow parameters; the same central order L and precision). Each kernel of the right-hand side
+ * and of the RK update runs as one launch over all instances, and one RK3 step of the whole
+ * ensemble is a CUDA graph replayed per step. Every instance computes exactly what a context of
+ * its own would (same kernels, same per-instance reduction order). */
+typedef struct strm_ensemble strm_ensemble;
+
+/* Device workspace for n instances (sum of the per-instance workspaces plus the instance
+ * tables); 0 if any grid or scheme is invalid. */
+size_t strm_ensemble_workspace_bytes(int n, const strm_grid* grids, const strm_scheme* schemes);
+
+/* Create an ensemble of n instances: grids[e], phys[e], schemes[e] and the y boundary kind
+ * bc_y[e] (STRM_BC_PERIODIC or STRM_BC_WALL_ISOTHERMAL). `workspace`: caller-owned device
+ * memory of strm_ensemble_workspace_bytes() bytes, 256-byte aligned. Work goes to `stream`. */
+int strm_ensemble_create(strm_ensemble** ens, int n, const strm_grid* grids, const strm_phys* phys,
+                         const strm_scheme* schemes, const int* bc_y, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* nsteps RK3 steps of every instance (dt > 0 fixed for all, else each instance takes its own CFL
+ * step with number cfl). w and r_old are host arrays of n device pointers (layout as for a
+ * single grid, sized by each instance's grid). */
+int strm_ensemble_advance(strm_ensemble* ens, double* const* w, double* const* r_old, int nsteps,
+                          double dt, double cfl);
+
+/* Autotuner: times one right-hand side of the ensemble (CUDA events, best of two) for the WENO
+ * block size x blocks-per-SM candidates and then the central-list grid, keeps the fastest, and
+ * writes {weno block, WENO blocks per SM, central blocks per SM} to choice_host (nullable). The
+ * state is read, not modified. */
+int strm_ensemble_tune(strm_ensemble* ens, double* const* w, double* const* r_old, int* choice_host);
+
+/* Conserved totals of every instance, out_host[5*e + m]. Synchronises. */
+int strm_ensemble_totals(strm_ensemble* ens, double* const* w, double* out_host);
+
+/* Simulated time of every instance, t_host[e]. Synchronises. */
+int strm_ensemble_times(strm_ensemble* ens, double* t_host);
+
+void strm_ensemble_destroy(strm_ensemble* ens);
+
 /* Largest grid (nx*ny*nz) strm_conserved_totals_static accepts. */
 #define STRM_STATIC_MAX_NODES 67108864
 

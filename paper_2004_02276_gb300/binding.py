@@ -74,6 +74,13 @@ SIGNATURES = {
     "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
     "strm_launch_count": ([_vp, _P(ctypes.c_longlong)], _i),
     "strm_conserved_totals_static": ([_P(Grid), _vp, _P(_d), _vp], _i),
+    "strm_ensemble_workspace_bytes": ([_i, _P(Grid), _P(Scheme)], _sz),
+    "strm_ensemble_create": ([_P(_vp), _i, _P(Grid), _P(Phys), _P(Scheme), _P(_i), _vp, _sz, _vp], _i),
+    "strm_ensemble_advance": ([_vp, _P(_vp), _P(_vp), _i, _d, _d], _i),
+    "strm_ensemble_tune": ([_vp, _P(_vp), _P(_vp), _P(_i)], _i),
+    "strm_ensemble_totals": ([_vp, _P(_vp), _P(_d)], _i),
+    "strm_ensemble_times": ([_vp, _P(_d)], _i),
+    "strm_ensemble_destroy": ([_vp], None),
     "strm_destroy": ([_vp], None),
 }
 K_COUNT = 14
@@ -247,6 +254,79 @@ class Solver:
         if getattr(self, "ctx", None):
             lib().strm_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Many independent grids advanced together by the batched kernels of the library.
+
+    ``cases`` is a list of workload descriptions sharing L and precision. State tensors are
+    lists of float64 CUDA tensors, one [5, nz, ny, nx] tensor per instance.
+    """
+
+    def __init__(self, cases, device=None, stream=None):
+        self.cases = list(cases)
+        n = len(self.cases)
+        self.device = torch.device(device if device is not None else "cuda")
+        parts = [structs(c) for c in self.cases]
+        self.grids = (Grid * n)(*[p[0] for p in parts])
+        self.phys = (Phys * n)(*[p[1] for p in parts])
+        self.schemes = (Scheme * n)(*[p[2] for p in parts])
+        self.bc = (ctypes.c_int * n)(*[1 if getattr(c, "y_wall", False) else 0 for c in self.cases])
+        L = lib()
+        nbytes = L.strm_ensemble_workspace_bytes(n, self.grids, self.schemes)
+        if nbytes == 0:
+            raise StrmError("strm_ensemble_workspace_bytes", -1, "invalid grid or scheme")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ens = ctypes.c_void_p()
+        _check("strm_ensemble_create", L.strm_ensemble_create(
+            ctypes.byref(ens), n, self.grids, self.phys, self.schemes, self.bc,
+            _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.ens = ens
+
+    def empty(self):
+        return [torch.empty((5, c.nz, c.ny, c.nx), dtype=torch.float64, device=self.device)
+                for c in self.cases]
+
+    def _ptrs(self, ts):
+        if len(ts) != len(self.cases):
+            raise ValueError("one state tensor per instance")
+        for t, c in zip(ts, self.cases):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                    and tuple(t.shape) == (5, c.nz, c.ny, c.nx)):
+                raise ValueError("state tensors must be contiguous float64 CUDA [5, nz, ny, nx]")
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def advance(self, ws, rs, nsteps, dt=0.0, cfl=0.8):
+        _check("strm_ensemble_advance", lib().strm_ensemble_advance(
+            self.ens, self._ptrs(ws), self._ptrs(rs), nsteps, dt, cfl))
+
+    def tune(self, ws, rs):
+        """Run the autotuner; returns (WENO block, WENO blocks per SM, central blocks per SM)."""
+        out = (ctypes.c_int * 3)()
+        _check("strm_ensemble_tune", lib().strm_ensemble_tune(self.ens, self._ptrs(ws), self._ptrs(rs), out))
+        return tuple(out)
+
+    def totals(self, ws):
+        out = (ctypes.c_double * (5 * len(self.cases)))()
+        _check("strm_ensemble_totals", lib().strm_ensemble_totals(self.ens, self._ptrs(ws), out))
+        return [list(out[5 * e:5 * e + 5]) for e in range(len(self.cases))]
+
+    def times(self):
+        out = (ctypes.c_double * len(self.cases))()
+        _check("strm_ensemble_times", lib().strm_ensemble_times(self.ens, out))
+        return list(out)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            lib().strm_ensemble_destroy(self.ens)
+            self.ens = None
 
     def __del__(self):
         try:

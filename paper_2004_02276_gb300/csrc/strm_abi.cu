@@ -632,6 +632,18 @@ int strm_launch_count(strm_ctx* x, long long* launches_host) {
   return STRM_OK;
 }
 
+}  // extern "C"
+
+// Internal: the per-grid pieces of a context, for the batched ensemble.
+void strm::ctx_parts(strm_ctx* x, Dims* d, Consts* C, Bufs* B, int* sms) {
+  *d = x->d;
+  *C = x->C;
+  *B = x->B;
+  *sms = x->weno_grid / 8;
+}
+
+extern "C" {
+
 void strm_destroy(strm_ctx* x) {
   if (!x) return;
   for (cudaEvent_t e : x->events) cudaEventDestroy(e);

@@ -1,0 +1,488 @@
+// Batched ensemble: many independent grids (uneven sizes, Mach and Reynolds numbers) advanced
+// together. Every kernel type of a right-hand side runs as one launch over all instances: the
+// node, ghost and face index spaces of the instances are concatenated with each instance padded
+// to whole blocks, and a block finds its instance by binary search over per-kernel-type block
+// offsets; the list kernels (central and WENO faces) walk the instances in a grid-stride loop.
+// One RK3 step of the whole ensemble is captured once as a CUDA graph and replayed. The launch
+// shapes of the list kernels are chosen by a small autotuner that times the candidates on the
+// ensemble itself.
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/strm.h"
+#include "strm_body.cuh"
+#include "strm_launch.h"
+
+namespace strm {
+
+struct Inst {
+  Dims d;
+  Consts C;
+  Bufs B;
+  double* w;
+  double* r_old;
+};
+
+enum { kKindNode = 0, kKindGhost = 1, kKindFace = 2, kKinds = 5 };  // faces: 2, 3, 4
+
+struct BatchIndex {
+  const Inst* inst;  // device table [n]
+  const int* start;  // device block starts [kKinds][n + 1]
+  int n;
+};
+
+__device__ __forceinline__ int find_inst(const int* start, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Instance of this block for kernel kind k, and the block index it plays within the instance.
+__device__ __forceinline__ const Inst& block_inst(const BatchIndex& X, int kind, int& blk) {
+  const int* st = X.start + kind * (X.n + 1);
+  int e = find_inst(st, X.n, blockIdx.x);
+  blk = blockIdx.x - __ldg(st + e);
+  return X.inst[e];
+}
+
+__device__ __forceinline__ int inst_blocks(const BatchIndex& X, int kind, int e) {
+  const int* st = X.start + kind * (X.n + 1);
+  return st[e + 1] - st[e];
+}
+
+__device__ __forceinline__ long long ghost_count(const Dims& d) {
+  return 2LL * G * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+}
+
+__global__ void kb_zero_counts(BatchIndex X) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= X.n) return;
+  for (int c = 0; c < 8; ++c) X.inst[e].B.wcount[c] = 0u;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) kb_prims(BatchIndex X, int want_cfl) {
+  __shared__ double sh[32];
+  int blk;
+  const Inst& I = block_inst(X, kKindNode, blk);
+  if (MIXED) body_prims_mixed(I.d, I.C, I.B, I.w, want_cfl, blk, sh);
+  else body_prims(I.d, I.C, I.B, I.w, want_cfl, blk, sh);
+}
+
+__global__ void kb_dt_finalize(BatchIndex X, double cfl, double dt_fixed) {
+  __shared__ double sh[32];
+  const Inst& I = X.inst[blockIdx.x];
+  body_dt_finalize(I.B, inst_blocks(X, kKindNode, blockIdx.x), cfl, dt_fixed, sh);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) kb_ghost_prims(BatchIndex X) {
+  int blk;
+  const Inst& I = block_inst(X, kKindGhost, blk);
+  if (MIXED) body_ghost_prims_mixed(I.d, I.C, I.B, ghost_count(I.d), blk);
+  else body_ghost_prims(I.d, I.C, I.B, ghost_count(I.d), blk);
+}
+
+template <int L, typename R>
+__global__ void __launch_bounds__(256) kb_sensor(BatchIndex X) {
+  int blk;
+  const Inst& I = block_inst(X, kKindNode, blk);
+  body_sensor<L, R>(I.d, I.C, I.B, blk);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_ghost_scalars(BatchIndex X) {
+  int blk;
+  const Inst& I = block_inst(X, kKindGhost, blk);
+  body_ghost_scalars<R>(I.d, I.C, I.B, ghost_count(I.d), blk);
+}
+
+template <int L, int DIR, typename R>
+__global__ void __launch_bounds__(256) kb_classify(BatchIndex X) {
+  int blk;
+  const Inst& I = block_inst(X, kKindFace + DIR, blk);
+  if (I.C.weno_mode != 1) return;
+  body_classify<L, DIR, R>(I.d, I.C, I.B, blk);
+}
+
+template <int L, int DIR, typename R>
+__global__ void __launch_bounds__(256) kb_central(BatchIndex X) {
+  long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long ts = (long long)gridDim.x * blockDim.x;
+  for (int e = 0; e < X.n; ++e) {
+    const Inst& I = X.inst[e];
+    int mode = I.C.weno_mode;
+    if (mode != 2) body_central<L, DIR, R>(I.d, I.C, I.B, mode == 1 ? 1 : 0, t0, ts);
+  }
+}
+
+template <int DIR, bool MIXED>
+__global__ void __launch_bounds__(256) kb_weno(BatchIndex X) {
+  long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long ts = (long long)gridDim.x * blockDim.x;
+  for (int e = 0; e < X.n; ++e) {
+    const Inst& I = X.inst[e];
+    if (I.C.weno_mode != 0) body_weno<DIR, MIXED>(I.d, I.C, I.B, t0, ts);
+  }
+}
+
+template <int L, typename R>
+__global__ void __launch_bounds__(256) kb_assemble(BatchIndex X) {
+  __shared__ double sh[32];
+  int blk;
+  const Inst& I = block_inst(X, kKindNode, blk);
+  body_assemble<L, R>(I.d, I.C, I.B, I.B.R, blk, sh);
+}
+
+__global__ void kb_force_finalize(BatchIndex X) {
+  __shared__ double sh[32];
+  const Inst& I = X.inst[blockIdx.x];
+  body_force_finalize(I.B, inst_blocks(X, kKindNode, blockIdx.x), 1.0 / I.C.vtot, sh);
+}
+
+__global__ void __launch_bounds__(256) kb_rk_update(BatchIndex X, double alpha, double beta) {
+  int blk;
+  const Inst& I = block_inst(X, kKindNode, blk);
+  body_rk_update(I.d, I.C, I.B, I.w, I.r_old, alpha, beta, blk);
+}
+
+}  // namespace strm
+
+using namespace strm;
+
+namespace {
+
+const double kAlphaE[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};  // Eq. RK, alpha_1 read as -17/60
+const double kBetaE[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+long long ghost_count_host(const Dims& d) {
+  return 2LL * G * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+}
+
+struct Tuning {
+  int weno_block = 128;
+  int weno_per_sm = 8;
+  int central_per_sm = 16;
+};
+
+}  // namespace
+
+struct strm_ensemble {
+  int n = 0;
+  int L = 3;
+  bool mixed = false;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  std::vector<strm_ctx*> ctx;
+  std::vector<Inst> inst_host;
+  std::vector<int> start_host;  // [kKinds][n + 1]
+  int total_blocks[kKinds] = {};
+  Inst* inst_dev = nullptr;
+  int* start_dev = nullptr;
+  Tuning tune;
+  // graph of one RK step of the ensemble
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double*> g_w, g_r;
+  double g_cfl = 0.0, g_dt = 0.0;
+  std::vector<double> time_host;
+};
+
+namespace {
+
+#define STRME_CK(call)                                                                             \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return record_error(STRM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+BatchIndex index_of(const strm_ensemble* E) { return BatchIndex{E->inst_dev, E->start_dev, E->n}; }
+
+// One right-hand side of every instance into its workspace residual (and, with dt_mode, the
+// per-instance step of stage 0).
+template <int L, bool MIXED>
+void enqueue_rhs_t(const strm_ensemble* E, bool dt_mode, double cfl, double dt_fixed, cudaStream_t st) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  BatchIndex X = index_of(E);
+  const Tuning& T = E->tune;
+  kb_zero_counts<<<nblocks(E->n, 32), 32, 0, st>>>(X);
+  kb_prims<MIXED><<<E->total_blocks[kKindNode], 256, 0, st>>>(X, dt_mode && dt_fixed <= 0.0 ? 1 : 0);
+  if (dt_mode) kb_dt_finalize<<<E->n, 1024, 0, st>>>(X, cfl, dt_fixed);
+  kb_ghost_prims<MIXED><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
+  kb_sensor<L, R><<<E->total_blocks[kKindNode], 256, 0, st>>>(X);
+  kb_ghost_scalars<R><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
+  kb_classify<L, 0, R><<<E->total_blocks[kKindFace + 0], 256, 0, st>>>(X);
+  kb_classify<L, 1, R><<<E->total_blocks[kKindFace + 1], 256, 0, st>>>(X);
+  kb_classify<L, 2, R><<<E->total_blocks[kKindFace + 2], 256, 0, st>>>(X);
+  unsigned cg = (unsigned)(E->sms * T.central_per_sm);
+  kb_central<L, 0, R><<<cg, 256, 0, st>>>(X);
+  kb_central<L, 1, R><<<cg, 256, 0, st>>>(X);
+  kb_central<L, 2, R><<<cg, 256, 0, st>>>(X);
+  unsigned wg = (unsigned)(E->sms * T.weno_per_sm);
+  kb_weno<0, MIXED><<<wg, T.weno_block, 0, st>>>(X);
+  kb_weno<1, MIXED><<<wg, T.weno_block, 0, st>>>(X);
+  kb_weno<2, MIXED><<<wg, T.weno_block, 0, st>>>(X);
+  kb_assemble<L, R><<<E->total_blocks[kKindNode], 256, 0, st>>>(X);
+  kb_force_finalize<<<E->n, 1024, 0, st>>>(X);
+}
+
+void enqueue_rhs(const strm_ensemble* E, bool dt_mode, double cfl, double dt_fixed, cudaStream_t st) {
+  if (E->L == 3) {
+    if (E->mixed) enqueue_rhs_t<3, true>(E, dt_mode, cfl, dt_fixed, st);
+    else enqueue_rhs_t<3, false>(E, dt_mode, cfl, dt_fixed, st);
+  } else {
+    if (E->mixed) enqueue_rhs_t<2, true>(E, dt_mode, cfl, dt_fixed, st);
+    else enqueue_rhs_t<2, false>(E, dt_mode, cfl, dt_fixed, st);
+  }
+}
+
+int enqueue_step(const strm_ensemble* E, double dt, double cfl, cudaStream_t st) {
+  BatchIndex X = index_of(E);
+  for (int stage = 0; stage < 3; ++stage) {
+    enqueue_rhs(E, stage == 0, cfl, dt, st);
+    kb_rk_update<<<E->total_blocks[kKindNode], 256, 0, st>>>(X, kAlphaE[stage], kBetaE[stage]);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("ensemble launch: ") + cudaGetErrorString(e));
+  return STRM_OK;
+}
+
+// Point the instance table at the caller's state buffers (re-uploaded only when they change).
+int bind_states(strm_ensemble* E, double* const* w, double* const* r_old) {
+  bool same = E->g_w.size() == (size_t)E->n;
+  for (int e = 0; e < E->n && same; ++e) same = E->g_w[e] == w[e] && E->g_r[e] == r_old[e];
+  if (same) return STRM_OK;
+  for (int e = 0; e < E->n; ++e) {
+    if (!w[e] || !r_old[e] || w[e] == r_old[e]) return record_error(STRM_EINVAL, "null or aliased state buffer");
+    E->inst_host[e].w = w[e];
+    E->inst_host[e].r_old = r_old[e];
+  }
+  STRME_CK(cudaMemcpyAsync(E->inst_dev, E->inst_host.data(), sizeof(Inst) * E->n, cudaMemcpyHostToDevice,
+                           E->stream));
+  // the copy reads inst_host; wait so that a later change cannot race with it
+  STRME_CK(cudaStreamSynchronize(E->stream));
+  E->g_w.assign(w, w + E->n);
+  E->g_r.assign(r_old, r_old + E->n);
+  if (E->gexec) {
+    cudaGraphExecDestroy(E->gexec);
+    E->gexec = nullptr;
+  }
+  return STRM_OK;
+}
+
+size_t table_bytes(int n) { return align256(sizeof(Inst) * (size_t)n) + align256(sizeof(int) * kKinds * (n + 1)); }
+
+}  // namespace
+
+extern "C" {
+
+size_t strm_ensemble_workspace_bytes(int n, const strm_grid* grids, const strm_scheme* schemes) {
+  if (n < 1 || !grids || !schemes) return 0;
+  size_t total = 0;
+  for (int e = 0; e < n; ++e) {
+    size_t b = strm_workspace_bytes(&grids[e], &schemes[e]);
+    if (!b) return 0;
+    total += align256(b);
+  }
+  return total + table_bytes(n);
+}
+
+int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, const strm_phys* phys,
+                         const strm_scheme* schemes, const int* bc_y, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  if (!out) return record_error(STRM_EINVAL, "ensemble out-pointer is null");
+  *out = nullptr;
+  if (n < 1 || !grids || !phys || !schemes || !bc_y) return record_error(STRM_EINVAL, "null or empty ensemble");
+  for (int e = 1; e < n; ++e)
+    if (schemes[e].L != schemes[0].L || schemes[e].precision != schemes[0].precision)
+      return record_error(STRM_EINVAL, "ensemble instances must share L and precision");
+  size_t need = strm_ensemble_workspace_bytes(n, grids, schemes);
+  if (!need) return record_error(STRM_EINVAL, "invalid grid or scheme in the ensemble");
+  if (!workspace || ((uintptr_t)workspace & 255)) return record_error(STRM_EINVAL, "workspace null or not 256-byte aligned");
+  if (workspace_bytes < need) return record_error(STRM_ENOMEM, "workspace too small: need " + std::to_string(need));
+  strm_ensemble* E = new (std::nothrow) strm_ensemble();
+  if (!E) return record_error(STRM_ENOMEM, "host allocation failed");
+  E->n = n;
+  E->L = schemes[0].L;
+  E->mixed = schemes[0].precision == STRM_PREC_MIXED;
+  E->stream = (cudaStream_t)stream;
+  E->inst_host.resize(n);
+  E->time_host.assign(n, 0.0);
+  char* ws = (char*)workspace;
+  size_t off = 0;
+  for (int e = 0; e < n; ++e) {
+    size_t b = align256(strm_workspace_bytes(&grids[e], &schemes[e]));
+    strm_ctx* c = nullptr;
+    int rc = strm_init_grid(&c, &grids[e], &phys[e], &schemes[e], ws + off, b, stream);
+    if (rc == STRM_OK) rc = strm_set_bc(c, STRM_FACE_YMIN_YMAX, bc_y[e], nullptr, 0);
+    if (rc != STRM_OK) {
+      if (c) strm_destroy(c);
+      strm_ensemble_destroy(E);
+      return rc;
+    }
+    E->ctx.push_back(c);
+    Inst& I = E->inst_host[e];
+    ctx_parts(c, &I.d, &I.C, &I.B, &E->sms);
+    I.w = I.r_old = nullptr;
+    off += b;
+  }
+  E->inst_dev = (Inst*)(ws + off);
+  E->start_dev = (int*)(ws + off + align256(sizeof(Inst) * (size_t)n));
+  E->start_host.assign(kKinds * (n + 1), 0);
+  for (int k = 0; k < kKinds; ++k) {
+    int acc = 0;
+    for (int e = 0; e < n; ++e) {
+      const Dims& d = E->inst_host[e].d;
+      long long cnt = k == kKindNode ? d.N : (k == kKindGhost ? ghost_count_host(d) : d.nf[k - kKindFace]);
+      E->start_host[k * (n + 1) + e] = acc;
+      acc += (int)nblocks(cnt, 256);
+    }
+    E->start_host[k * (n + 1) + n] = acc;
+    E->total_blocks[k] = acc;
+  }
+  cudaError_t ce = cudaMemcpyAsync(E->start_dev, E->start_host.data(), sizeof(int) * E->start_host.size(),
+                                   cudaMemcpyHostToDevice, E->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(E->stream);
+  if (ce != cudaSuccess) {
+    strm_ensemble_destroy(E);
+    return record_error(STRM_ECUDA, std::string("ensemble table upload: ") + cudaGetErrorString(ce));
+  }
+  *out = E;
+  return STRM_OK;
+}
+
+int strm_ensemble_advance(strm_ensemble* E, double* const* w, double* const* r_old, int nsteps, double dt,
+                          double cfl) {
+  if (!E || !w || !r_old) return record_error(STRM_EINVAL, "null ensemble or state table");
+  if (nsteps < 0) return record_error(STRM_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return record_error(STRM_EINVAL, "need dt > 0 or cfl > 0");
+  int rc = bind_states(E, w, r_old);
+  if (rc) return rc;
+  if (nsteps == 0) return STRM_OK;
+  if (!E->gexec || E->g_cfl != cfl || E->g_dt != dt) {
+    if (E->gexec) {
+      STRME_CK(cudaGraphExecDestroy(E->gexec));
+      E->gexec = nullptr;
+    }
+    if (!E->cap) STRME_CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
+    STRME_CK(cudaStreamBeginCapture(E->cap, cudaStreamCaptureModeThreadLocal));
+    int erc = enqueue_step(E, dt, cfl, E->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(E->cap, &graph);
+    if (erc) {
+      if (graph) cudaGraphDestroy(graph);
+      return erc;
+    }
+    if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&E->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    E->g_cfl = cfl;
+    E->g_dt = dt;
+  }
+  for (int s = 0; s < nsteps; ++s) STRME_CK(cudaGraphLaunch(E->gexec, E->stream));
+  return STRM_OK;
+}
+
+int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old, int* choice_host) {
+  if (!E || !w || !r_old) return record_error(STRM_EINVAL, "null ensemble or state table");
+  int rc = bind_states(E, w, r_old);
+  if (rc) return rc;
+  cudaEvent_t a, b;
+  STRME_CK(cudaEventCreate(&a));
+  STRME_CK(cudaEventCreate(&b));
+  auto time_rhs = [&](float* best_ms) -> int {
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(a, E->stream);
+      enqueue_rhs(E, false, 0.0, 0.0, E->stream);
+      cudaEventRecord(b, E->stream);
+      cudaError_t e = cudaEventSynchronize(b);
+      if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("tune: ") + cudaGetErrorString(e));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      best = std::min(best, ms);
+    }
+    *best_ms = best;
+    return STRM_OK;
+  };
+  // WENO launch shape first (the dominant kernel), then the central list grid
+  Tuning bestT = E->tune;
+  float best = 1e30f;
+  const int blocks[3] = {64, 128, 256}, per_sm[3] = {4, 8, 16};
+  for (int bi = 0; bi < 3 && rc == STRM_OK; ++bi)
+    for (int gi = 0; gi < 3 && rc == STRM_OK; ++gi) {
+      E->tune.weno_block = blocks[bi];
+      E->tune.weno_per_sm = per_sm[gi];
+      float ms;
+      rc = time_rhs(&ms);
+      if (rc == STRM_OK && ms < best) {
+        best = ms;
+        bestT = E->tune;
+      }
+    }
+  E->tune = bestT;
+  const int cper[3] = {8, 16, 32};
+  for (int ci = 0; ci < 3 && rc == STRM_OK; ++ci) {
+    E->tune.central_per_sm = cper[ci];
+    float ms;
+    rc = time_rhs(&ms);
+    if (rc == STRM_OK && ms < best) {
+      best = ms;
+      bestT = E->tune;
+    }
+  }
+  E->tune = bestT;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (E->gexec) {  // the captured graph holds the old launch shapes
+    cudaGraphExecDestroy(E->gexec);
+    E->gexec = nullptr;
+  }
+  if (choice_host) {
+    choice_host[0] = E->tune.weno_block;
+    choice_host[1] = E->tune.weno_per_sm;
+    choice_host[2] = E->tune.central_per_sm;
+  }
+  return rc;
+}
+
+int strm_ensemble_totals(strm_ensemble* E, double* const* w, double* out_host) {
+  if (!E || !w || !out_host) return record_error(STRM_EINVAL, "null argument");
+  for (int e = 0; e < E->n; ++e) {
+    int rc = strm_conserved_totals(E->ctx[e], w[e], out_host + 5 * e);
+    if (rc) return rc;
+  }
+  return STRM_OK;
+}
+
+int strm_ensemble_times(strm_ensemble* E, double* t_host) {
+  if (!E || !t_host) return record_error(STRM_EINVAL, "null argument");
+  for (int e = 0; e < E->n; ++e) {
+    int rc = strm_get_time(E->ctx[e], &t_host[e], nullptr);
+    if (rc) return rc;
+  }
+  return STRM_OK;
+}
+
+void strm_ensemble_destroy(strm_ensemble* E) {
+  if (!E) return;
+  if (E->gexec) cudaGraphExecDestroy(E->gexec);
+  if (E->cap) cudaStreamDestroy(E->cap);
+  for (strm_ctx* c : E->ctx) strm_destroy(c);
+  delete E;
+}
+
+}  // extern "C"

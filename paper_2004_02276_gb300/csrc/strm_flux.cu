@@ -1,527 +1,37 @@
-// Convective interface fluxes (central energy-consistent, or characteristic LF-WENO5 at the
-// faces the Ducros sensor flags) and the assembly of the residual with the viscous terms.
+// Face kernels of one grid (central energy-consistent flux, characteristic LF-WENO5 at the faces
+// the Ducros sensor flags) and the assembly of the residual with the viscous terms.
 //
 // Per direction: k_classify splits the faces into a WENO list and a central list (warp-aggregated
 // atomics), k_central and k_weno then run over their lists without warp divergence whatever the
 // flagged fraction (a per-face branch would run both paths in most warps). k_assemble then forms
-// R = -sum_d (f_{s+1} - f_s)/h_d + viscous terms per node and the forcing partial sums.
-#include "strm_dev.cuh"
+// R = -sum_d (f_{s+1} - f_s)/h_d + viscous terms per node and the forcing partial sums. The
+// bodies are in strm_body.cuh.
+#include "strm_body.cuh"
 #include "strm_launch.h"
 
 namespace strm {
 
-// ------------------------------------------------------------------------------ face decoding
-
-// Face q of direction DIR -> left node (i, j, k) (= node s-1 along DIR).
-template <int DIR>
-__device__ __forceinline__ void face_node(const Dims& d, long long q, int& i, int& j, int& k) {
-  if (DIR == 0) {
-    int s = (int)(q % (d.nx + 1));
-    long long r = q / (d.nx + 1);
-    i = s - 1;
-    j = (int)(r % d.ny);
-    k = (int)(r / d.ny);
-  } else if (DIR == 1) {
-    i = (int)(q % d.nx);
-    long long r = q / d.nx;
-    j = (int)(r % (d.ny + 1)) - 1;
-    k = (int)(r / (d.ny + 1));
-  } else {
-    i = (int)(q % d.nx);
-    long long r = q / d.nx;
-    j = (int)(r % d.ny);
-    k = (int)(r / d.ny) - 1;
-  }
-}
-
-// ------------------------------------------------------------------------------ central flux
-
-// Energy-consistent split flux at the face between nodes n and n+st (Eqs. avg_operator,
-// encflux): f_phi = 2 sum_l a_l sum_{m<l} (rho, u_n, phi)~_{n-m,l}. With
-// qq = (rho_a + rho_b)(u_a + u_b)/4 this is sum_l a_l sum_m qq (phi_a + phi_b); the pressure
-// enters the normal momentum as sum_l a_l sum_m (p_a + p_b). R is the arithmetic precision.
-template <int L, int DIR, typename R>
-__device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, long long n, long long st,
-                                             R* f) {
-  const Nodes<R>& P = nodes<R>(B);
-  const R* a = coefs<R>(C).a;
-  const R* __restrict__ ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
-  R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0), ap = R(0);
-#pragma unroll
-  for (int l = 1; l <= L; ++l) {
-    R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0), sp = R(0);
-#pragma unroll
-    for (int m = 0; m < l; ++m) {
-      long long ia = n - m * st, ib = n + (l - m) * st;
-      R qq = R(0.25) * (__ldg(P.rho + ia) + __ldg(P.rho + ib)) * (__ldg(ud + ia) + __ldg(ud + ib));
-      s0 += qq;
-      s1 += qq * (__ldg(P.u + ia) + __ldg(P.u + ib));
-      s2 += qq * (__ldg(P.v + ia) + __ldg(P.v + ib));
-      s3 += qq * (__ldg(P.w + ia) + __ldg(P.w + ib));
-      s4 += qq * (__ldg(P.H + ia) + __ldg(P.H + ib));
-      sp += __ldg(P.p + ia) + __ldg(P.p + ib);
-    }
-    R al = a[l];
-    a0 += al * s0;
-    a1 += al * s1;
-    a2 += al * s2;
-    a3 += al * s3;
-    a4 += al * s4;
-    ap += al * sp;
-  }
-  f[0] = R(2) * a0;
-  f[1] = a1;
-  f[2] = a2;
-  f[3] = a3;
-  f[4] = a4;
-  f[1 + DIR] += ap;
-}
-
-// ------------------------------------------------------------------------------ WENO5
-
-// Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2} = (f0..f4), written in first differences
-// a..d of the stencil: value = f2 + num/den with
-//   6 q_0 = 6 f2 + 5b - 2a,  6 q_1 = 6 f2 + b + 2c,  6 q_2 = 6 f2 + 4c - d,
-// smoothness indicators scaled by 4 (4 beta = 13/3 t^2 + t'^2, so eps4 = 4 eps keeps the
-// weights), and weights d_k/(eps+beta_k)^2 multiplied through by 10 (eps+beta_0..2)^2 products.
-__device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
-                                         double eps4, double& num, double& den) {
-  double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
-  double t0 = b - a, t1 = fma(3.0, b, -a);
-  double t2 = c - b, t3 = b + c;
-  double t4 = d - c, t5 = fma(-3.0, c, d);
-  double q0 = eps4 + fma((13.0 / 3.0) * t0, t0, t1 * t1);
-  double q1 = eps4 + fma((13.0 / 3.0) * t2, t2, t3 * t3);
-  double q2 = eps4 + fma((13.0 / 3.0) * t4, t4, t5 * t5);
-  q0 *= q0;
-  q1 *= q1;
-  q2 *= q2;
-  double w0 = q1 * q2, w1 = 6.0 * (q0 * q2), w2 = 3.0 * (q0 * q1);
-  double e0 = fma(-2.0, a, 5.0 * b), e1 = fma(2.0, c, b), e2 = fma(4.0, c, -d);
-  num = fma(w2, e2, fma(w1, e1, w0 * e0));
-  den = 6.0 * (w0 + w1 + w2);
-}
-
-// Characteristic Lax-Friedrichs flux-vector splitting with WENO5 (Section 2.1) at the face
-// between nodes n and n+st: Roe average, local LF speeds (largest |eigenvalue| of each field over
-// the six stencil nodes), projection of w and of the Euler flux at the stencil nodes onto the
-// left eigenvectors (written out through the acoustic-row scalars A, B and the shear rows),
-// WENO5 of the positive part from the left and of the negative part from the right, and
-// projection back with the right eigenvectors.
-//
-// The split values of field k are carried scaled by s_k (4 for the acoustic fields, 2 for the
-// others) to drop the 1/2 and 1/4 factors of the projection and of the splitting; WENO5 is then
-// run with eps scaled by s_k^2, which leaves its weights unchanged, and the result is divided
-// by s_k. All scalings are powers of two.
-template <int DIR>
-__device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long long n, long long st,
-                                          double* f) {
-  constexpr int T1 = DIR == 0 ? 1 : 0;
-  constexpr int T2 = DIR == 2 ? 1 : 2;
-  const Nodes<double>& P = B.n64;
-  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
-  const double* __restrict__ un_p = vel[DIR];
-  // Roe average of nodes n and n + st
-  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
-  double inv = 1.0 / (sl + sr);
-  double wl = sl * inv, wr = sr * inv;
-  double ua[3];
-#pragma unroll
-  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
-  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
-  double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
-  double c2a = C.gm1 * (Ha - 0.5 * q2);
-  double ic = rsqrt(c2a);
-  double ca = c2a * ic;
-  double b1 = C.gm1 * ic * ic;
-  double b2 = 0.5 * q2 * b1;
-  double un_a = ua[DIR];
-
-  // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
-  double lam0 = 0.0, lam1 = 0.0, lam4 = 0.0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    long long nn = n + (q - 2) * st;
-    double un = __ldg(un_p + nn), cs = __ldg(P.c + nn);
-    lam0 = fmax(lam0, fabs(un - cs));
-    lam1 = fmax(lam1, fabs(un));
-    lam4 = fmax(lam4, fabs(un + cs));
-  }
-
-  // scaled split characteristic values s_k (L F +- lam_k L w)/2 at the stencil nodes
-  double gp[5][6], gm[5][6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    long long nn = n + (q - 2) * st;
-    double rho = __ldg(P.rho + nn);
-    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
-    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double un = uu[DIR];
-    double run = rho * un;
-    double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
-    double K = b2 + b1 * (H - udot);
-    double b1p = b1 * p;
-    double Aw = rho * K - b1p;          // acoustic rows: (l0 + l4) w = A_w, (l0 - l4) w = B_w
-    double Af = run * K - b1p * un_a;
-    double du = un_a - un;
-    double Bw = (rho * ic) * du;
-    double Bf = (run * du - p) * ic;
-    double Sw = Aw + Bw, Sf = Af + Bf, Dw = Aw - Bw, Df = Af - Bf;
-    gp[0][q] = fma(lam0, Sw, Sf);
-    gm[0][q] = fma(-lam0, Sw, Sf);
-    gp[4][q] = fma(lam4, Dw, Df);
-    gm[4][q] = fma(-lam4, Dw, Df);
-    double r1 = fma(lam1, rho, run), r2 = fma(-lam1, rho, run);
-    gp[1][q] = r1 - fma(lam1, Aw, Af);
-    gm[1][q] = r2 - fma(-lam1, Aw, Af);
-    double d1 = uu[T1] - ua[T1], d2 = uu[T2] - ua[T2];
-    gp[2][q] = d1 * r1;
-    gm[2][q] = d1 * r2;
-    gp[3][q] = d2 * r1;
-    gm[3][q] = d2 * r2;
-  }
-  double g[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const bool acoustic = (k == 0 || k == 4);
-    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;  // 4 s_k^2 eps
-    double np_, dp_, nm_, dm_;
-    weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
-    weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
-    double v = (gp[k][2] + gm[k][3]) + fma(np_, dm_, nm_ * dp_) / (dp_ * dm_);
-    g[k] = (acoustic ? 0.25 : 0.5) * v;
-  }
-  // back to conserved variables with the right eigenvectors
-  double gs = g[0] + g[1] + g[4];
-  f[0] = gs;
-#pragma unroll
-  for (int dd = 0; dd < 3; ++dd) f[1 + dd] = gs * ua[dd];
-  f[1 + DIR] += ca * (g[4] - g[0]);
-  f[1 + T1] += g[2];
-  f[1 + T2] += g[3];
-  f[4] = Ha * (g[0] + g[4]) + un_a * ca * (g[4] - g[0]) + 0.5 * q2 * g[1] + ua[T1] * g[2] +
-         ua[T2] * g[3];
-}
-
-// FP32 WENO5 (mixed precision), same first-difference form; the nonlinear weights are formed
-// as 10 d_k/(eps+beta_k)^2 directly (products of (eps+beta)^2 could overflow FP32).
-__device__ __forceinline__ float weno5_f(float f0, float f1, float f2, float f3, float f4, float eps4) {
-  float a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
-  float t0 = b - a, t1 = fmaf(3.f, b, -a);
-  float t2 = c - b, t3 = b + c;
-  float t4 = d - c, t5 = fmaf(-3.f, c, d);
-  float q0 = eps4 + fmaf((13.f / 3.f) * t0, t0, t1 * t1);
-  float q1 = eps4 + fmaf((13.f / 3.f) * t2, t2, t3 * t3);
-  float q2 = eps4 + fmaf((13.f / 3.f) * t4, t4, t5 * t5);
-  float w0 = 1.f / (q0 * q0), w1 = 6.f / (q1 * q1), w2 = 3.f / (q2 * q2);
-  float e0 = fmaf(-2.f, a, 5.f * b), e1 = fmaf(2.f, c, b), e2 = fmaf(4.f, c, -d);
-  return f2 + fmaf(w2, e2, fmaf(w1, e1, w0 * e0)) / (6.f * (w0 + w1 + w2));
-}
-
-// Mixed-precision characteristic WENO flux. The projection into characteristic variables is
-// done in FP64: Roe state, eigen-scalars and, per stencil node, the acoustic-row scalars
-// A and B of w and of the Euler flux (where cancellation happens). The LF split, WENO5 and the
-// projection back to conserved variables run in FP32; the result is an FP32 face flux.
-template <int DIR>
-__device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, long long n, long long st,
-                                                float* f) {
-  constexpr int T1 = DIR == 0 ? 1 : 0;
-  constexpr int T2 = DIR == 2 ? 1 : 2;
-  const Nodes<double>& P = B.n64;
-  const Nodes<float>& F = B.n32;
-  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
-  const float* __restrict__ velf[3] = {F.u, F.v, F.w};
-  // FP64 Roe average of nodes n and n + st and the eigen-scalars
-  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
-  double inv = 1.0 / (sl + sr);
-  double wl = sl * inv, wr = sr * inv;
-  double ua[3];
-#pragma unroll
-  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
-  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
-  double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
-  double c2a = C.gm1 * (Ha - 0.5 * q2);
-  double ic = rsqrt(c2a);
-  double ca = c2a * ic;
-  double b1 = C.gm1 * ic * ic;
-  double b2 = 0.5 * q2 * b1;
-  double un_a = ua[DIR];
-  // FP32 local LF speeds
-  float lam0 = 0.f, lam1 = 0.f, lam4 = 0.f;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    long long nn = n + (q - 2) * st;
-    float un = __ldg(velf[DIR] + nn), cs = __ldg(F.c + nn);
-    lam0 = fmaxf(lam0, fabsf(un - cs));
-    lam1 = fmaxf(lam1, fabsf(un));
-    lam4 = fmaxf(lam4, fabsf(un + cs));
-  }
-  const float uat1 = (float)ua[T1], uat2 = (float)ua[T2];
-  float gp[5][6], gm[5][6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    long long nn = n + (q - 2) * st;
-    double rho = __ldg(P.rho + nn);
-    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
-    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double un = uu[DIR];
-    double run = rho * un;
-    double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
-    double K = b2 + b1 * (H - udot);
-    double b1p = b1 * p;
-    double Aw = rho * K - b1p;
-    double Af = run * K - b1p * un_a;
-    double du = un_a - un;
-    double Bw = (rho * ic) * du;
-    double Bf = (run * du - p) * ic;
-    float Sw = (float)(Aw + Bw), Sf = (float)(Af + Bf), Dw = (float)(Aw - Bw), Df = (float)(Af - Bf);
-    float Awf = (float)Aw, Aff = (float)Af;
-    float rhof = __ldg(F.rho + nn), unf = __ldg(velf[DIR] + nn);
-    float runf = rhof * unf;
-    gp[0][q] = fmaf(lam0, Sw, Sf);
-    gm[0][q] = fmaf(-lam0, Sw, Sf);
-    gp[4][q] = fmaf(lam4, Dw, Df);
-    gm[4][q] = fmaf(-lam4, Dw, Df);
-    float r1 = fmaf(lam1, rhof, runf), r2 = fmaf(-lam1, rhof, runf);
-    gp[1][q] = r1 - fmaf(lam1, Awf, Aff);
-    gm[1][q] = r2 - fmaf(-lam1, Awf, Aff);
-    float d1 = __ldg(velf[T1] + nn) - uat1, d2 = __ldg(velf[T2] + nn) - uat2;
-    gp[2][q] = d1 * r1;
-    gm[2][q] = d1 * r2;
-    gp[3][q] = d2 * r1;
-    gm[3][q] = d2 * r2;
-  }
-  const float eps = C.k32.weno_eps;
-  float g[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const bool acoustic = (k == 0 || k == 4);
-    const float eps4 = (acoustic ? 64.f : 16.f) * eps;  // 4 s_k^2 eps
-    float v = weno5_f(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4) +
-              weno5_f(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4);
-    g[k] = (acoustic ? 0.25f : 0.5f) * v;
-  }
-  const float uaf[3] = {(float)ua[0], (float)ua[1], (float)ua[2]};
-  const float caf = (float)ca, Haf = (float)Ha, q2f = (float)q2, unaf = (float)un_a;
-  float gs = g[0] + g[1] + g[4];
-  f[0] = gs;
-#pragma unroll
-  for (int dd = 0; dd < 3; ++dd) f[1 + dd] = gs * uaf[dd];
-  f[1 + DIR] += caf * (g[4] - g[0]);
-  f[1 + T1] += g[2];
-  f[1 + T2] += g[3];
-  f[4] = Haf * (g[0] + g[4]) + unaf * caf * (g[4] - g[0]) + 0.5f * q2f * g[1] + uaf[T1] * g[2] +
-         uaf[T2] * g[3];
-}
-
-// ------------------------------------------------------------------------------ face kernels
-
-// Warp-aggregated append of face q to a compacted list: one atomic per warp and list.
-__device__ __forceinline__ void warp_append(bool mine, unsigned act, int* list, unsigned* count, int q) {
-  unsigned m = __ballot_sync(act, mine);
-  if (!m) return;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
-  base = __shfl_sync(act, base, leader);
-  if (mine) list[base + __popc(m & ((1u << lane) - 1u))] = q;
-}
-
-// Hybrid switch, sensor mode: split the faces of one direction into a WENO list and a central
-// list, so that each flux kernel runs without warp divergence whatever the flagged fraction.
 template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_classify(Dims d, Consts C, Bufs B) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= d.nf[DIR]) return;
-  int i, j, k;
-  face_node<DIR>(d, q, i, j, k);
-  bool fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
-  unsigned act = __activemask();
-  warp_append(fl, act, B.wl[DIR], B.wcount + DIR, (int)q);
-  warp_append(!fl, act, B.cl[DIR], B.wcount + 4 + DIR, (int)q);
+  body_classify<L, DIR, R>(d, C, B, blockIdx.x);
 }
 
-// Central flux at every face of one direction (WENO off) or at the faces of the central list.
 template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list) {
-  long long cnt = use_list ? (long long)B.wcount[4 + DIR] : d.nf[DIR];
-  long long nf = d.nf[DIR];
-  long long st = dir_stride(d, DIR);
-  R* out = face_flux<R>(B, DIR);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long q = use_list ? (long long)B.cl[DIR][t] : t;
-    int i, j, k;
-    face_node<DIR>(d, q, i, j, k);
-    R f[5];
-    central_flux<L, DIR, R>(C, B, gidx(d, i, j, k), st, f);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[c * nf + q] = f[c];
-  }
+  body_central<L, DIR, R>(d, C, B, use_list, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                          (long long)gridDim.x * blockDim.x);
 }
 
-// Characteristic WENO flux at the faces of the WENO list (sensor mode) or at every face (WENO
-// everywhere); FP64, or the mixed-precision variant writing FP32 face fluxes.
 template <int DIR, bool MIXED>
 __global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
-  const bool all = C.weno_mode == 2;
-  long long nf = d.nf[DIR];
-  long long cnt = all ? nf : (long long)B.wcount[DIR];
-  long long st = dir_stride(d, DIR);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long q = all ? t : (long long)B.wl[DIR][t];
-    int i, j, k;
-    face_node<DIR>(d, q, i, j, k);
-    if (MIXED) {
-      float f[5];
-      weno_flux_mixed<DIR>(C, B, gidx(d, i, j, k), st, f);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) B.fh32[DIR][c * nf + q] = f[c];
-    } else {
-      double f[5];
-      weno_flux<DIR>(C, B, gidx(d, i, j, k), st, f);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) B.fh64[DIR][c * nf + q] = f[c];
-    }
-  }
+  body_weno<DIR, MIXED>(d, C, B, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                        (long long)gridDim.x * blockDim.x);
 }
 
-// ------------------------------------------------------------------------------ assembly
-
-// Viscous terms in Laplacian form at node n (Section 2.1 and Eqs. sigma, heat_vec):
-//   V_i = mu lap u_i + mu/3 d_i(div) + d_j mu (d_j u_i + d_i u_j) - 2/3 div d_i mu,
-//   V_E = u_i V_i + sigma_ij d_j u_i + k lap T + d_j k d_j T,  k = cp mu / Pr,
-// first and second derivatives of order 2L; along y, d/dy = (1/y_eta) d/deta and
-// d2/dy2 = (f_etaeta - (y_etaeta/y_eta) f_eta)/y_eta^2; d_i(div) from the ghost-filled div.
-template <int L, typename R>
-__device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, const Dims& d, long long n,
-                                             int j, R* V) {
-  const Nodes<R>& P = nodes<R>(B);
-  const Coefs<R>& K = coefs<R>(C);
-  const Metric<R>& M = metric<R>(B);
-  const long long sy = d.px, sz = d.plane;
-  const R hy = __ldg(M.inv_hy + j), c2 = __ldg(M.c2y + j), c1 = __ldg(M.c1y + j);
-  const R* __restrict__ fld[4] = {P.u, P.v, P.w, P.T};
-  R du[3][3], lap[3], dT[3], lapT = R(0);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    R s1, s2, d0, d1v, d2v, l0;
-    dsum12<L>(fld[a], n, 1, K.a, K.b, s1, s2);
-    d0 = s1 * K.inv_dx;
-    l0 = s2 * K.inv_dx2;
-    dsum12<L>(fld[a], n, sy, K.a, K.b, s1, s2);
-    d1v = s1 * hy;
-    l0 += s2 * c2 - s1 * c1;
-    dsum12<L>(fld[a], n, sz, K.a, K.b, s1, s2);
-    d2v = s1 * K.inv_dz;
-    l0 += s2 * K.inv_dz2;
-    if (a < 3) {
-      du[a][0] = d0;
-      du[a][1] = d1v;
-      du[a][2] = d2v;
-      lap[a] = l0;
-    } else {
-      dT[0] = d0;
-      dT[1] = d1v;
-      dT[2] = d2v;
-      lapT = l0;
-    }
-  }
-  R dmu[3], ddiv[3];
-  dmu[0] = dsum<L>(P.mu, n, 1, K.a) * K.inv_dx;
-  dmu[1] = dsum<L>(P.mu, n, sy, K.a) * hy;
-  dmu[2] = dsum<L>(P.mu, n, sz, K.a) * K.inv_dz;
-  ddiv[0] = dsum<L>(P.div, n, 1, K.a) * K.inv_dx;
-  ddiv[1] = dsum<L>(P.div, n, sy, K.a) * hy;
-  ddiv[2] = dsum<L>(P.div, n, sz, K.a) * K.inv_dz;
-  const R mu = __ldg(P.mu + n);
-  const R div = du[0][0] + du[1][1] + du[2][2];
-  R Vm[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R s = dmu[0] * (du[a][0] + du[0][a]) + dmu[1] * (du[a][1] + du[1][a]) +
-          dmu[2] * (du[a][2] + du[2][a]);
-    Vm[a] = mu * lap[a] + mu * ddiv[a] * R(1.0 / 3.0) + s - R(2.0 / 3.0) * div * dmu[a];
-  }
-  const R uu[3] = {__ldg(P.u + n), __ldg(P.v + n), __ldg(P.w + n)};
-  R work = uu[0] * Vm[0] + uu[1] * Vm[1] + uu[2] * Vm[2];
-  // sigma_ij d_j u_i = mu [ sum_ij (d_j u_i + d_i u_j) d_j u_i - 2/3 div^2 ]
-  R diss = R(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) diss += (du[a][b] + du[b][a]) * du[a][b];
-  diss = mu * (diss - R(2.0 / 3.0) * div * div);
-  R heat = K.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
-  V[0] = R(0);
-  V[1] = Vm[0];
-  V[2] = Vm[1];
-  V[3] = Vm[2];
-  V[4] = work + diss + heat;
-}
-
-// Residual per node: R = -sum_d (f_{s+1} - f_s)/h_d (Eq. num_flux, with the staggered-wall rule)
-// plus the viscous terms, in precision R; stored in FP64 with the forcing partial sums.
 template <int L, typename R>
 __global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, double* __restrict__ Rout) {
   __shared__ double sh[32];
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double fpart = 0.0;
-  if (q < d.N) {
-    int i = (int)(q % d.nx);
-    long long r = q / d.nx;
-    int j = (int)(r % d.ny);
-    int k = (int)(r / d.ny);
-    const Coefs<R>& K = coefs<R>(C);
-    R res[5] = {R(0), R(0), R(0), R(0), R(0)};
-    double mass64 = 0.0;
-    if (C.convective) {
-      long long qx = ((long long)k * d.ny + j) * (d.nx + 1) + i;
-      long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
-      long long qz = ((long long)k * d.ny + j) * d.nx + i;
-      long long sxy = (long long)d.nx * d.ny;
-      R hy = __ldg(metric<R>(B).inv_hy + j);
-      bool wlo = C.wall_y && j == 0, whi = C.wall_y && j == d.ny - 1;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const R* fx = face_flux<R>(B, 0) + m * d.nf[0];
-        const R* fy = face_flux<R>(B, 1) + m * d.nf[1];
-        const R* fz = face_flux<R>(B, 2) + m * d.nf[2];
-        R ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
-        // staggered wall interface: no mass, x/z momentum or energy crosses it
-        if (m != 2) {
-          if (wlo) ylo = R(0);
-          if (whi) yhi = R(0);
-        }
-        res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
-                   (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * K.inv_dz);
-        if (m == 0 && sizeof(R) != sizeof(double)) {
-          // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
-          // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
-          // FP64 round-off as in the FP64 path
-          mass64 = -(((double)__ldg(fx + qx + 1) - (double)__ldg(fx + qx)) * C.k64.inv_dx +
-                     ((double)yhi - (double)ylo) * __ldg(B.m64.inv_hy + j) +
-                     ((double)__ldg(fz + qz + sxy) - (double)__ldg(fz + qz)) * C.k64.inv_dz);
-        }
-      }
-    }
-    if (C.viscous) {
-      R V[5];
-      viscous_node<L, R>(C, B, d, gidx(d, i, j, k), j, V);
-#pragma unroll
-      for (int m = 1; m < 5; ++m) res[m] += V[m];
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = (double)res[m];
-    if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
-    fpart = (double)res[1] * __ldg(B.vol + j);
-  }
-  if (C.forcing) {
-    double s = block_sum(fpart, sh);
-    if (threadIdx.x == 0) B.red[blockIdx.x] = s;
-  }
+  body_assemble<L, R>(d, C, B, Rout, blockIdx.x, sh);
 }
 
 // ------------------------------------------------------------------------------ launchers

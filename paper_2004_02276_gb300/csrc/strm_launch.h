@@ -12,6 +12,15 @@ namespace strm {
 // Set the thread-local message returned by strm_last_error and return code.
 int record_error(int code, const std::string& msg);
 
+}  // namespace strm
+
+struct strm_ctx;
+
+namespace strm {
+
+// The grid, constants and workspace buffers of a context, and the SM count it launches for.
+void ctx_parts(strm_ctx* x, Dims* d, Consts* C, Bufs* B, int* sms);
+
 int reduce_blocks(const Dims& d);
 void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w, bool want_cfl,
                   cudaStream_t s);

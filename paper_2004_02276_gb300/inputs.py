@@ -166,3 +166,20 @@ def primitive_state(case: Case, rho, u, v, w, T) -> np.ndarray:
     out[3] = rho * w
     out[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
     return out
+
+
+def ensemble_cases(seed: int = 0, n: int = 64, precision: str = "fp64") -> list:
+    """The batched workload: n independent channel instances with grid dimensions drawn from
+    {32..192} x {32..128} x {32..128}, bulk Mach number from U[0.3, 3.0] and bulk Reynolds number
+    from U[2000, 8000] (SplitMix64 stream ``seed``; same domain, walls and scheme as C1/C2)."""
+    r = uniform(seed, (n, 5))
+    cases = []
+    for e in range(n):
+        nx = 32 + int(r[e, 0] * 161)
+        ny = 32 + int(r[e, 1] * 97)
+        nz = 32 + int(r[e, 2] * 97)
+        mach = 0.3 + 2.7 * r[e, 3]
+        re = 2000.0 + 6000.0 * r[e, 4]
+        cases.append(Case(name=f"ensemble-{e}", nx=nx, ny=ny, nz=nz, mach=mach, reynolds=re,
+                          precision=precision, seed=seed * 1000 + e))
+    return cases

@@ -1,0 +1,87 @@
+"""Batched ensemble (many independent grids in one launch per kernel type, one CUDA graph per
+RK step): every instance must compute exactly what a context of its own computes, since both
+run the same kernel bodies with the same per-instance reduction order. Checked bitwise through
+the C ABI, in FP64 and mixed precision, before and after the autotuner picks launch shapes."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_02276_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def mixed_bag(precision):
+    return [
+        inputs.Case(nx=40, ny=24, nz=18, mach=0.5, reynolds=2500.0, precision=precision),
+        inputs.Case(nx=33, ny=37, nz=9, mach=2.4, reynolds=7000.0, precision=precision),
+        inputs.Case(nx=64, ny=16, nz=30, y_wall=False, forcing=False, precision=precision),
+        inputs.Case(nx=17, ny=21, nz=13, weno_mode="off", precision=precision),
+        inputs.Case(nx=24, ny=12, nz=20, weno_mode="all", beta=0.0, precision=precision),
+        inputs.Case(nx=50, ny=3, nz=7, mach=3.0, precision=precision),
+    ]
+
+
+def single_runs(cases, nsteps):
+    out, times = [], []
+    for c in cases:
+        s = binding.Solver(c)
+        w = torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda()
+        r = torch.zeros_like(w)
+        s.advance_n(w, r, nsteps, cfl=0.8)
+        out.append(w.cpu().numpy())
+        times.append(s.time()[0])
+        s.close()
+    return out, times
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_equals_independent_contexts(precision):
+    cases = mixed_bag(precision)
+    ref, tref = single_runs(cases, 4)
+    E = binding.Ensemble(cases)
+    ws = [torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda() for c in cases]
+    rs = [torch.zeros_like(w) for w in ws]
+    E.advance(ws, rs, 4, cfl=0.8)
+    torch.cuda.synchronize()
+    for e, c in enumerate(cases):
+        assert np.array_equal(ws[e].cpu().numpy(), ref[e]), (precision, e)
+    assert E.times() == tref
+    tot = E.totals(ws)
+    assert all(np.isfinite(t).all() for t in tot)
+    E.close()
+
+
+def test_tuned_ensemble_still_exact():
+    cases = mixed_bag("fp64")
+    ref, _ = single_runs(cases, 3)
+    E = binding.Ensemble(cases)
+    ws = [torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda() for c in cases]
+    rs = [torch.zeros_like(w) for w in ws]
+    choice = E.tune(ws, rs)
+    assert choice[0] in (64, 128, 256) and choice[1] in (4, 8, 16) and choice[2] in (8, 16, 32)
+    E.advance(ws, rs, 3, cfl=0.8)
+    for e in range(len(cases)):
+        assert np.array_equal(ws[e].cpu().numpy(), ref[e]), e
+    E.close()
+
+
+def test_ensemble_rejects_mixed_orders():
+    cases = [inputs.Case(nx=8, ny=6, nz=4), inputs.Case(nx=8, ny=6, nz=4, L=2)]
+    with pytest.raises(binding.StrmError):
+        binding.Ensemble(cases)
+
+
+def test_ensemble_workload_draws():
+    cases = inputs.ensemble_cases(seed=0)
+    assert len(cases) == 64
+    assert all(32 <= c.nx <= 192 and 32 <= c.ny <= 128 and 32 <= c.nz <= 128 for c in cases)
+    assert all(0.3 <= c.mach <= 3.0 and 2000 <= c.reynolds <= 8000 for c in cases)
