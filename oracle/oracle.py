@@ -19,7 +19,12 @@ class OrcCfg(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
-        ("y_map", ctypes.c_int), ("beta", ctypes.c_double), ("bc_y", ctypes.c_int),
+        ("y_map", ctypes.c_int), ("beta", ctypes.c_double),
+        ("bc_xmin", ctypes.c_int), ("bc_xmax", ctypes.c_int),
+        ("bc_ymin", ctypes.c_int), ("bc_ymax", ctypes.c_int),
+        ("ref", ctypes.c_double * 5), ("shock", ctypes.c_int),
+        ("shock_theta", ctypes.c_double), ("shock_ximp", ctypes.c_double),
+        ("i_recycle", ctypes.c_int), ("delta_in", ctypes.c_double),
         ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double), ("r_gas", ctypes.c_double),
         ("visc_law", ctypes.c_int), ("mu_ref", ctypes.c_double), ("t_ref", ctypes.c_double),
         ("visc_exp", ctypes.c_double), ("suth_s", ctypes.c_double),
@@ -31,6 +36,8 @@ class OrcCfg(ctypes.Structure):
 
 
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
+BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3}
+Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2}
 VISC_LAWS = {"power": 0, "sutherland": 1}
 
 
@@ -60,6 +67,9 @@ def lib():
         _lib.orc_weno5.argtypes = [dp, d]
         _lib.orc_weno5.restype = d
         _lib.orc_ghosts.restype = i
+        _lib.orc_oblique_shock.argtypes = [d, d, d, dp, dp, dp, dp]
+        _lib.orc_recycle_scale.argtypes = [cp, dp]
+        _lib.orc_recycle_scale.restype = d
     return _lib
 
 
@@ -78,9 +88,23 @@ def make_cfg(case, **over) -> OrcCfg:
     c.nx, c.ny, c.nz = get("nx"), get("ny"), get("nz")
     c.lx, c.ly, c.lz = get("lx"), get("ly"), get("lz")
     beta = get("beta", 0.0)
-    c.y_map = 1 if beta and beta > 0 else 0
+    ymap = get("y_map", "tanh")
+    c.y_map = Y_MAPS[ymap] if beta and beta > 0 else 0
     c.beta = beta if beta else 0.0
-    c.bc_y = 1 if get("y_wall", True) else 0
+    ywall = get("y_wall", True)
+    c.bc_xmin = BC_KINDS[get("bc_xmin", None) or "periodic"]
+    c.bc_xmax = BC_KINDS[get("bc_xmax", None) or "periodic"]
+    c.bc_ymin = BC_KINDS[get("bc_ymin", None) or ("wall" if ywall else "periodic")]
+    c.bc_ymax = BC_KINDS[get("bc_ymax", None) or ("wall" if ywall else "periodic")]
+    ref = get("ref", None)
+    if ref is not None:
+        for m in range(5):
+            c.ref[m] = ref[m]
+    c.shock = int(bool(get("shock", False)))
+    c.shock_theta = get("shock_theta", 0.0)
+    c.shock_ximp = get("shock_ximp", 0.0)
+    c.i_recycle = get("i_recycle", 0)
+    c.delta_in = get("delta_in", 1.0)
     c.gamma, c.prandtl = get("gamma"), get("prandtl")
     c.r_gas = get("r_gas")
     c.visc_law = VISC_LAWS[get("visc_law", "power")]
@@ -187,6 +211,18 @@ def eigvecs(direction, gamma, u, v, w, H):
     Lm, Rm = np.empty(25), np.empty(25)
     lib().orc_eigvecs(int(direction), gamma, u, v, w, H, _dp(Lm), _dp(Rm))
     return Lm.reshape(5, 5), Rm.reshape(5, 5)
+
+
+def oblique_shock(gamma, mach, theta):
+    """(beta, p2/p1, rho2/rho1, M2) of the weak oblique shock; theta in radians."""
+    out = [ctypes.c_double() for _ in range(4)]
+    if lib().orc_oblique_shock(gamma, mach, theta, *[ctypes.byref(o) for o in out]):
+        raise ValueError("deflection beyond the attached-shock limit")
+    return tuple(o.value for o in out)
+
+
+def recycle_scale(cfg, w):
+    return lib().orc_recycle_scale(ctypes.byref(cfg), _dp(_state(cfg, w)))
 
 
 def weno5(f, eps=1e-6):

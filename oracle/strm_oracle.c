@@ -23,6 +23,17 @@
  *   - Staggered isothermal wall: mirrored ghosts, zero convective flux of mass, x/z momentum
  *     and energy through the wall interface.
  *   - Forcing is applied at every RK stage; the CFL step uses the convective limit only.
+ *   - Characteristic (non-reflecting) faces, Section 3.2: ghost states from the eigenvectors at
+ *     the boundary node; outgoing characteristic variables extrapolated at zeroth order,
+ *     incoming ones taken from a reference state: at the top face the free stream (or the
+ *     post-shock state), at an outflow face the boundary node's own state at the reference
+ *     pressure (a subsonic outflow only prescribes the far-field pressure; the outflow plane
+ *     crosses the boundary layer, where the free-stream state is not a valid reference).
+ *   - Inflow: rescaled recycling (the paper's digital filtering needs a Reynolds-stress
+ *     dataset): ghost planes copy planes upstream of a recycling plane with the wall-normal
+ *     coordinate stretched by delta_r / delta_in (outer scaling only).
+ *   - Oblique shock at the top, Section 3.3: top ghosts downstream of the shock foot see the
+ *     weak-branch Rankine-Hugoniot post-shock state.
  */
 #include "strm_oracle.h"
 
@@ -81,11 +92,20 @@ static int central_coeffs(int L, double* a, double* b) {
 }
 
 /* Wall-normal mapping y(eta), eta in [0,1], nodes at eta_j = (j+1/2)/ny (staggered: the
- * walls eta = 0, 1 are interfaces). Tanh clustering toward both walls, y in [-ly/2, ly/2]. */
+ * walls eta = 0, 1 are interfaces). Tanh clustering toward both walls, y in [-ly/2, ly/2]; or
+ * toward the wall y = 0 only, y = ly (1 - tanh(beta (1-eta)) / tanh beta) in [0, ly]. */
 void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
   for (int j = 0; j < c->ny; ++j) {
     double eta = (j + 0.5) / c->ny;
-    if (c->y_map == ORC_MAP_TANH) {
+    if (c->y_map == ORC_MAP_TANH_ONESIDED) {
+      double s = c->beta * (1.0 - eta);
+      double th = tanh(s);
+      double sech2 = 1.0 - th * th;
+      double A = c->ly / tanh(c->beta);
+      y[j] = c->ly - A * th;
+      yeta[j] = A * c->beta * sech2;
+      yetaeta[j] = 2.0 * A * c->beta * c->beta * sech2 * th;
+    } else if (c->y_map == ORC_MAP_TANH) {
       double s = c->beta * (2.0 * eta - 1.0);
       double A = 0.5 * c->ly / tanh(c->beta);
       double th = tanh(s);
@@ -101,9 +121,19 @@ void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
   }
 }
 
+/* Height of the wall-side boundary eta = 0 in the mapping. */
+static double map_y0(const orc_cfg* c) {
+  return c->y_map == ORC_MAP_TANH_ONESIDED ? 0.0 : -0.5 * c->ly;
+}
+
 static int grid_init(grid_t* g, const orc_cfg* c) {
   if (c->nx < 1 || c->ny < 1 || c->nz < 1) return -1;
-  if (c->bc_y == ORC_BC_WALL && c->ny < G) return -1;
+  if ((c->bc_ymin == ORC_BC_WALL || c->bc_ymax == ORC_BC_WALL) && c->ny < G) return -1;
+  if ((c->bc_xmin == ORC_BC_PERIODIC) != (c->bc_xmax == ORC_BC_PERIODIC)) return -1;
+  if ((c->bc_ymin == ORC_BC_PERIODIC) != (c->bc_ymax == ORC_BC_PERIODIC)) return -1;
+  if (c->bc_xmax == ORC_BC_RECYCLE || c->bc_ymin == ORC_BC_RECYCLE || c->bc_ymax == ORC_BC_RECYCLE) return -1;
+  if (c->bc_xmin == ORC_BC_RECYCLE && (c->i_recycle < G - 1 || c->i_recycle >= c->nx || !(c->delta_in > 0)))
+    return -1;
   g->c = c;
   g->nx = c->nx; g->ny = c->ny; g->nz = c->nz;
   g->nxg = c->nx + 2 * G; g->nyg = c->ny + 2 * G; g->nzg = c->nz + 2 * G;
@@ -142,6 +172,8 @@ static double viscosity(const orc_cfg* c, double T) {
 
 /* ---------------------------------------------------------------- ghost fill of w */
 
+static void load_interior(const grid_t* g, const double* w, double* wg[5]);
+
 /* Isothermal no-slip wall on the staggered mesh: the ghost node mirrors an interior node
  * across the wall interface; velocity changes sign, T_g = 2 T_w - T, p_g = p, rho_g from the
  * equation of state, E from E = cv T + |u|^2/2. */
@@ -163,25 +195,228 @@ static void wall_ghost(const grid_t* g, const double* win, double* wout) {
   wout[4] = rhog * (g->cv * Tg + 0.5 * (ug * ug + vg * vg + wg * wg));
 }
 
-/* Fill the ghost layers of the five ghosted conserved arrays. Only the faces are filled
- * (no edges or corners): every stencil of the method runs along one grid line. */
+/* Conserved state from primitives (rho, u, v, w, p): T = p/(rho R), E = cv T + |u|^2/2. */
+static void prim_to_cons(const grid_t* g, const double* q, double* w) {
+  double T = q[4] / (q[0] * g->c->r_gas);
+  w[0] = q[0];
+  w[1] = q[0] * q[1];
+  w[2] = q[0] * q[2];
+  w[3] = q[0] * q[3];
+  w[4] = q[0] * (g->cv * T + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]));
+}
+
+/* Primitives (rho, u, v, w, p) and T from the conserved state. */
+static void cons_to_prim(const grid_t* g, const double* w, double* q, double* T) {
+  double rho = w[0];
+  double u = w[1] / rho, v = w[2] / rho, ww = w[3] / rho;
+  double t = (w[4] / rho - 0.5 * (u * u + v * v + ww * ww)) / g->cv;
+  q[0] = rho;
+  q[1] = u;
+  q[2] = v;
+  q[3] = ww;
+  q[4] = rho * g->c->r_gas * t;
+  *T = t;
+}
+
+/* Weak-branch oblique shock (Section 3.3): theta(beta) = atan(2 cot(beta) (M^2 sin^2 beta - 1) /
+ * (M^2 (gamma + cos 2 beta) + 2)) rises from 0 at the Mach angle to its maximum and falls back to
+ * 0 at 90 degrees; the weak solution is the root on the rising part (bisection), then the
+ * normal-shock relations with M1n = M sin(beta). */
+static double oblique_theta(double gamma, double M, double b) {
+  double sb = sin(b);
+  return atan(2.0 / tan(b) * (M * M * sb * sb - 1.0) / (M * M * (gamma + cos(2.0 * b)) + 2.0));
+}
+
+int orc_oblique_shock(double gamma, double M, double theta, double* beta, double* p_ratio,
+                      double* rho_ratio, double* mach2) {
+  double pi = acos(-1.0);
+  double lo = asin(1.0 / M), hi = 0.5 * pi;
+  /* maximum of theta(beta) by ternary search */
+  for (int it = 0; it < 200; ++it) {
+    double m1 = lo + (hi - lo) / 3.0, m2 = hi - (hi - lo) / 3.0;
+    if (oblique_theta(gamma, M, m1) < oblique_theta(gamma, M, m2)) lo = m1;
+    else hi = m2;
+  }
+  double bmax = 0.5 * (lo + hi);
+  if (theta > oblique_theta(gamma, M, bmax)) return -1;
+  lo = asin(1.0 / M);
+  hi = bmax;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (oblique_theta(gamma, M, mid) < theta) lo = mid;
+    else hi = mid;
+  }
+  double b = 0.5 * (lo + hi);
+  double m1n = M * sin(b);
+  *beta = b;
+  *p_ratio = 1.0 + 2.0 * gamma / (gamma + 1.0) * (m1n * m1n - 1.0);
+  *rho_ratio = (gamma + 1.0) * m1n * m1n / ((gamma - 1.0) * m1n * m1n + 2.0);
+  double m2n2 = (m1n * m1n + 2.0 / (gamma - 1.0)) / (2.0 * gamma / (gamma - 1.0) * m1n * m1n - 1.0);
+  *mach2 = sqrt(m2n2) / sin(b - theta);
+  return 0;
+}
+
+/* Post-shock primitives behind the incident shock: the upstream reference stream (u along x)
+ * deflected by theta toward the wall; x position of the shock foot on the top boundary. */
+static void shock_state(const grid_t* g, double* q2, double* x_foot) {
+  const orc_cfg* c = g->c;
+  const double* q1 = c->ref;
+  double V1 = q1[1];
+  double c1 = sqrt(c->gamma * q1[4] / q1[0]);
+  double b, pr, rr, m2;
+  orc_oblique_shock(c->gamma, V1 / c1, c->shock_theta, &b, &pr, &rr, &m2);
+  double un1 = V1 * sin(b), ut = V1 * cos(b);
+  double un2 = un1 / rr;
+  q2[0] = q1[0] * rr;
+  q2[1] = ut * cos(b) + un2 * sin(b);
+  q2[2] = -ut * sin(b) + un2 * cos(b);
+  q2[3] = 0.0;
+  q2[4] = q1[4] * pr;
+  /* the shock line descends at angle beta from the foot (x_foot, top) to (x_imp, wall); the
+   * wall (eta = 0) and the top (eta = 1) are ly apart */
+  *x_foot = c->shock_ximp - c->ly / tan(b);
+}
+
+/* Non-reflecting characteristic ghost (Section 3.2: characteristic decomposition normal to the
+ * boundary). Eigenvectors at the boundary node state wb along dir; a characteristic variable
+ * whose speed points out of the domain (outward = +1 for the max face, -1 for the min face) is
+ * extrapolated from the boundary node at zeroth order, the others are taken from the reference
+ * primitives qref. */
+static void char_ghost(const grid_t* g, const double* wb, const double* qref, int dir, int outward,
+                       double* wout) {
+  double q[5], T, wr[5], Lm[25], Rm[25], W[5];
+  cons_to_prim(g, wb, q, &T);
+  double H = (wb[4] + q[4]) / q[0];
+  orc_eigvecs(dir, g->c->gamma, q[1], q[2], q[3], H, Lm, Rm);
+  double cs = sqrt(g->c->gamma * q[4] / q[0]);
+  double un = q[1 + dir];
+  double lam[5] = {un - cs, un, un, un, un + cs};
+  prim_to_cons(g, qref, wr);
+  for (int k = 0; k < 5; ++k) {
+    const double* src = (outward * lam[k] > 0.0) ? wb : wr;
+    double s = 0.0;
+    for (int m = 0; m < 5; ++m) s += Lm[k * 5 + m] * src[m];
+    W[k] = s;
+  }
+  for (int m = 0; m < 5; ++m) {
+    double s = 0.0;
+    for (int k = 0; k < 5; ++k) s += Rm[m * 5 + k] * W[k];
+    wout[m] = s;
+  }
+}
+
+/* Spanwise-mean streamwise velocity at the recycling plane and the thickness delta_r where it
+ * first reaches 0.99 of the reference velocity (linear interpolation between nodes; heights
+ * above the wall eta = 0). Returns s = delta_r / delta_in (1 if the profile never reaches it). */
+static double recycle_scale_g(const grid_t* g, double* const wg[5]) {
+  const orc_cfg* c = g->c;
+  double y0 = map_y0(c), target = 0.99 * c->ref[1];
+  double prev_u = 0.0, prev_h = 0.0; /* the wall: u = 0 at height 0 */
+  for (int j = 0; j < g->ny; ++j) {
+    double sum = 0.0;
+    for (int k = 0; k < g->nz; ++k) {
+      ptrdiff_t n = gidx(g, c->i_recycle, j, k);
+      sum += wg[1][n] / wg[0][n];
+    }
+    double ub = sum / g->nz, h = g->y[j] - y0;
+    if (ub >= target) {
+      double dr = prev_h + (target - prev_u) * (h - prev_h) / (ub - prev_u);
+      return dr / c->delta_in;
+    }
+    prev_u = ub;
+    prev_h = h;
+  }
+  return 1.0;
+}
+
+double orc_recycle_scale(const orc_cfg* c, const double* w) {
+  grid_t g;
+  if (grid_init(&g, c)) return -1.0;
+  if (c->bc_xmin != ORC_BC_RECYCLE) {
+    grid_free(&g);
+    return 1.0;
+  }
+  double* wg[5];
+  for (int m = 0; m < 5; ++m) wg[m] = alloc_nan(g.ng);
+  load_interior(&g, w, wg);
+  double s = recycle_scale_g(&g, wg);
+  for (int m = 0; m < 5; ++m) free(wg[m]);
+  grid_free(&g);
+  return s;
+}
+
+/* Rescaled recycling inflow: ghost plane i = -1-q copies interior plane i_recycle - q with the
+ * wall-normal coordinate stretched, the value at height h being the recycled plane's value at
+ * height s*h (primitives u, v, w, T, p interpolated linearly between nodes; below the first node
+ * between the wall state u = v = w = 0, T = T_w, p = p_0 and the first node; above the last node
+ * the last node's value). */
+static void fill_recycle(const grid_t* g, double* wg[5], double s) {
+  const orc_cfg* c = g->c;
+  double y0 = map_y0(c);
+  for (int q = 0; q < G; ++q) {
+    int is = c->i_recycle - q;
+    for (int k = 0; k < g->nz; ++k)
+      for (int j = 0; j < g->ny; ++j) {
+        double ht = s * (g->y[j] - y0);
+        double a[5], b[5], Ta, Tb, alpha;
+        double wa[5], wb[5];
+        int jb;
+        for (jb = 0; jb < g->ny && g->y[jb] - y0 < ht; ++jb) {}
+        if (jb == g->ny) {
+          for (int m = 0; m < 5; ++m) wb[m] = wg[m][gidx(g, is, g->ny - 1, k)];
+          cons_to_prim(g, wb, b, &Tb);
+          for (int m = 0; m < 5; ++m) a[m] = b[m];
+          Ta = Tb;
+          alpha = 1.0;
+        } else {
+          for (int m = 0; m < 5; ++m) wb[m] = wg[m][gidx(g, is, jb, k)];
+          cons_to_prim(g, wb, b, &Tb);
+          double ha, hb = g->y[jb] - y0;
+          if (jb == 0) {
+            a[1] = a[2] = a[3] = 0.0;
+            a[4] = b[4];
+            Ta = c->t_wall;
+            ha = 0.0;
+          } else {
+            for (int m = 0; m < 5; ++m) wa[m] = wg[m][gidx(g, is, jb - 1, k)];
+            cons_to_prim(g, wa, a, &Ta);
+            ha = g->y[jb - 1] - y0;
+          }
+          alpha = (ht - ha) / (hb - ha);
+        }
+        double qg[5];
+        double Tg = (1.0 - alpha) * Ta + alpha * Tb;
+        for (int m = 1; m < 5; ++m) qg[m] = (1.0 - alpha) * a[m] + alpha * b[m];
+        qg[0] = qg[4] / (c->r_gas * Tg);
+        double out[5];
+        prim_to_cons(g, qg, out);
+        for (int m = 0; m < 5; ++m) wg[m][gidx(g, -1 - q, j, k)] = out[m];
+      }
+  }
+}
+
+/* Fill the ghost layers of the five ghosted conserved arrays face by face. Only the faces are
+ * filled (no edges or corners): every stencil of the method runs along one grid line. */
 static void fill_ghosts_w(const grid_t* g, double* wg[5]) {
+  const orc_cfg* c = g->c;
   int nx = g->nx, ny = g->ny, nz = g->nz;
+  /* periodic faces */
   for (int m = 0; m < 5; ++m) {
     double* f = wg[m];
-    for (int k = 0; k < nz; ++k)
-      for (int j = 0; j < ny; ++j)
-        for (int q = 1; q <= G; ++q) {
-          f[gidx(g, -q, j, k)] = f[gidx(g, wrap(-q, nx), j, k)];
-          f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, wrap(nx - 1 + q, nx), j, k)];
-        }
+    if (c->bc_xmin == ORC_BC_PERIODIC)
+      for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+          for (int q = 1; q <= G; ++q) {
+            f[gidx(g, -q, j, k)] = f[gidx(g, wrap(-q, nx), j, k)];
+            f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, wrap(nx - 1 + q, nx), j, k)];
+          }
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i)
         for (int q = 1; q <= G; ++q) {
           f[gidx(g, i, j, -q)] = f[gidx(g, i, j, wrap(-q, nz))];
           f[gidx(g, i, j, nz - 1 + q)] = f[gidx(g, i, j, wrap(nz - 1 + q, nz))];
         }
-    if (g->c->bc_y == ORC_BC_PERIODIC)
+    if (c->bc_ymin == ORC_BC_PERIODIC)
       for (int k = 0; k < nz; ++k)
         for (int i = 0; i < nx; ++i)
           for (int q = 1; q <= G; ++q) {
@@ -189,32 +424,70 @@ static void fill_ghosts_w(const grid_t* g, double* wg[5]) {
             f[gidx(g, i, ny - 1 + q, k)] = f[gidx(g, i, wrap(ny - 1 + q, ny), k)];
           }
   }
-  if (g->c->bc_y == ORC_BC_WALL) {
+  double in[5], out[5];
+  /* x faces (outflow-type characteristic faces see the boundary state at the reference
+   * pressure) */
+  if (c->bc_xmin == ORC_BC_RECYCLE) fill_recycle(g, wg, recycle_scale_g(g, wg));
+  if (c->bc_xmin == ORC_BC_CHAR || c->bc_xmax == ORC_BC_CHAR)
     for (int k = 0; k < nz; ++k)
-      for (int i = 0; i < nx; ++i)
-        for (int q = 0; q < G; ++q) {
-          double in[5], out[5];
-          /* lower wall: ghost j = -1-q mirrors j = q */
+      for (int j = 0; j < ny; ++j)
+        for (int side = 0; side < 2; ++side) {
+          if ((side == 0 ? c->bc_xmin : c->bc_xmax) != ORC_BC_CHAR) continue;
+          int ib = side == 0 ? 0 : nx - 1;
+          double qb[5], Tb;
+          for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, ib, j, k)];
+          cons_to_prim(g, in, qb, &Tb);
+          qb[4] = c->ref[4];
+          char_ghost(g, in, qb, 0, side == 0 ? -1 : 1, out);
+          for (int q = 1; q <= G; ++q)
+            for (int m = 0; m < 5; ++m) wg[m][gidx(g, side == 0 ? -q : nx - 1 + q, j, k)] = out[m];
+        }
+  /* y faces: walls mirror, characteristic faces from the boundary row */
+  double qshock[5], x_foot = 0.0;
+  if (c->shock) shock_state(g, qshock, &x_foot);
+  for (int k = 0; k < nz; ++k)
+    for (int i = 0; i < nx; ++i) {
+      for (int q = 0; q < G; ++q) {
+        if (c->bc_ymin == ORC_BC_WALL) { /* ghost j = -1-q mirrors j = q */
           for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, q, k)];
           wall_ghost(g, in, out);
           for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, -1 - q, k)] = out[m];
-          /* upper wall: ghost j = ny+q mirrors j = ny-1-q */
+        }
+        if (c->bc_ymax == ORC_BC_WALL) { /* ghost j = ny+q mirrors j = ny-1-q */
           for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, ny - 1 - q, k)];
           wall_ghost(g, in, out);
           for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, ny + q, k)] = out[m];
         }
-  }
+      }
+      if (c->bc_ymin == ORC_BC_CHAR) {
+        for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, 0, k)];
+        char_ghost(g, in, c->ref, 1, -1, out);
+        for (int q = 1; q <= G; ++q)
+          for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, -q, k)] = out[m];
+      }
+      if (c->bc_ymax == ORC_BC_CHAR) {
+        double xi = (i + 0.5) * g->dx;
+        const double* qr = (c->shock && xi >= x_foot) ? qshock : c->ref;
+        for (int m = 0; m < 5; ++m) in[m] = wg[m][gidx(g, i, ny - 1, k)];
+        char_ghost(g, in, qr, 1, 1, out);
+        for (int q = 1; q <= G; ++q)
+          for (int m = 0; m < 5; ++m) wg[m][gidx(g, i, ny - 1 + q, k)] = out[m];
+      }
+    }
 }
 
-/* Ghost fill of a node scalar (sensor theta, node divergence): periodic copy, and an even
- * mirror across a wall. */
+/* Ghost fill of a node scalar (sensor theta, node divergence): periodic copy, even mirror across
+ * a wall, copy of the boundary node at characteristic and inflow faces. */
 static void fill_ghosts_scalar(const grid_t* g, double* f) {
+  const orc_cfg* c = g->c;
   int nx = g->nx, ny = g->ny, nz = g->nz;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int q = 1; q <= G; ++q) {
-        f[gidx(g, -q, j, k)] = f[gidx(g, wrap(-q, nx), j, k)];
-        f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, wrap(nx - 1 + q, nx), j, k)];
+        int lo = c->bc_xmin == ORC_BC_PERIODIC ? wrap(-q, nx) : 0;
+        int hi = c->bc_xmax == ORC_BC_PERIODIC ? wrap(nx - 1 + q, nx) : nx - 1;
+        f[gidx(g, -q, j, k)] = f[gidx(g, lo, j, k)];
+        f[gidx(g, nx - 1 + q, j, k)] = f[gidx(g, hi, j, k)];
       }
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i)
@@ -225,13 +498,15 @@ static void fill_ghosts_scalar(const grid_t* g, double* f) {
   for (int k = 0; k < nz; ++k)
     for (int i = 0; i < nx; ++i)
       for (int q = 0; q < G; ++q) {
-        if (g->c->bc_y == ORC_BC_WALL) {
-          f[gidx(g, i, -1 - q, k)] = f[gidx(g, i, q, k)];
-          f[gidx(g, i, ny + q, k)] = f[gidx(g, i, ny - 1 - q, k)];
-        } else {
-          f[gidx(g, i, -1 - q, k)] = f[gidx(g, i, wrap(-1 - q, ny), k)];
-          f[gidx(g, i, ny + q, k)] = f[gidx(g, i, wrap(ny + q, ny), k)];
-        }
+        int lo, hi;
+        if (c->bc_ymin == ORC_BC_PERIODIC) lo = wrap(-1 - q, ny);
+        else if (c->bc_ymin == ORC_BC_WALL) lo = q;
+        else lo = 0;
+        if (c->bc_ymax == ORC_BC_PERIODIC) hi = wrap(ny + q, ny);
+        else if (c->bc_ymax == ORC_BC_WALL) hi = ny - 1 - q;
+        else hi = ny - 1;
+        f[gidx(g, i, -1 - q, k)] = f[gidx(g, i, lo, k)];
+        f[gidx(g, i, ny + q, k)] = f[gidx(g, i, hi, k)];
       }
 }
 
@@ -523,7 +798,8 @@ static void convective_dir(const grid_t* g, const prims_t* P, double* const wg[5
   int nb = dir == 2 ? g->ny : g->nz; /* second transverse */
   ptrdiff_t st = dir_stride(g, dir);
   ptrdiff_t Nint = (ptrdiff_t)g->nx * g->ny * g->nz;
-  int wall = dir == 1 && g->c->bc_y == ORC_BC_WALL;
+  int wall_lo = dir == 1 && g->c->bc_ymin == ORC_BC_WALL;
+  int wall_hi = dir == 1 && g->c->bc_ymax == ORC_BC_WALL;
 #pragma omp parallel for schedule(static)
   for (int b = 0; b < nb; ++b) {
     double* fl = malloc(sizeof(double) * 5 * (size_t)(nd + 1));
@@ -545,7 +821,7 @@ static void convective_dir(const grid_t* g, const prims_t* P, double* const wg[5
         }
         if (fw) weno_flux(g, P, wg, n, st, dir, fl + 5 * s);
         else central_flux(g, P, n, st, dir, fl + 5 * s);
-        if (wall && (s == 0 || s == nd)) {
+        if ((wall_lo && s == 0) || (wall_hi && s == nd)) {
           /* staggered wall interface: no mass, x/z momentum or energy crosses the wall */
           fl[5 * s + 0] = 0.0;
           fl[5 * s + 1] = 0.0;

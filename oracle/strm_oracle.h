@@ -22,8 +22,8 @@
 extern "C" {
 #endif
 
-enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1 };
-enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1 };
+enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1, ORC_MAP_TANH_ONESIDED = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_CHAR = 2, ORC_BC_RECYCLE = 3 };
 enum { ORC_WENO_OFF = 0, ORC_WENO_SENSOR = 1, ORC_WENO_ALL = 2 };
 enum { ORC_VISC_POWER = 0, ORC_VISC_SUTHERLAND = 1 };
 
@@ -31,9 +31,18 @@ typedef struct {
   /* grid: nx*ny*nz interior nodes; y nodes at eta_j = (j+1/2)/ny */
   int nx, ny, nz;
   double lx, ly, lz;
-  int y_map;            /* ORC_MAP_UNIFORM or ORC_MAP_TANH */
+  int y_map;            /* ORC_MAP_UNIFORM, ORC_MAP_TANH (both walls) or _TANH_ONESIDED (wall at y=0) */
   double beta;          /* tanh stretching parameter */
-  int bc_y;             /* ORC_BC_PERIODIC or ORC_BC_WALL (x and z are periodic) */
+  /* face kinds (z is periodic): x faces PERIODIC, RECYCLE (x-min only) or CHAR; y faces
+   * PERIODIC, WALL or CHAR */
+  int bc_xmin, bc_xmax, bc_ymin, bc_ymax;
+  double ref[5];        /* reference primitives (rho, u, v, w, p) seen by characteristic faces */
+  int shock;            /* 1: y-max characteristic ghosts downstream of the shock foot see the
+                           post-shock state of an oblique shock of deflection shock_theta that
+                           reaches the wall at x = shock_ximp */
+  double shock_theta, shock_ximp;
+  int i_recycle;        /* recycling plane (interior x index >= 2) */
+  double delta_in;      /* inflow boundary-layer thickness (99 % of ref u) */
   /* gas: p = rho R T, E = cv T + |u|^2/2, k = cp mu / Pr */
   double gamma, prandtl, r_gas;
   int visc_law;         /* mu = mu_ref (T/t_ref)^visc_exp, or Sutherland with constant suth_s */
@@ -83,6 +92,15 @@ void orc_eigvecs(int dir, double gamma, double u, double v, double w, double H,
 
 /* WENO5-JS reconstruction at i+1/2 from f[0..4] = f_{i-2..i+2}. */
 double orc_weno5(const double* f, double eps);
+
+/* Weak-branch oblique shock of deflection theta (radians) in a stream of Mach number mach:
+ * writes the shock angle beta and the ratios p2/p1, rho2/rho1 and the post-shock Mach number.
+ * Returns 0, or -1 if the deflection exceeds the attached-shock limit. */
+int orc_oblique_shock(double gamma, double mach, double theta, double* beta, double* p_ratio,
+                      double* rho_ratio, double* mach2);
+
+/* Recycling rescale factor s = delta_r / delta_in for the state w (1 if no recycling face). */
+double orc_recycle_scale(const orc_cfg* c, const double* w);
 
 /* Number of ghost layers used by the oracle. */
 int orc_ghosts(void);

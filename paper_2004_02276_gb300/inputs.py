@@ -40,9 +40,15 @@ def uniform(seed: int, shape) -> np.ndarray:
 
 @dataclasses.dataclass(frozen=True)
 class Case:
-    """A workload: grid, gas and scheme parameters (channel defaults)."""
+    """A workload: grid, gas and scheme parameters (channel defaults).
+
+    kind "channel": rho_b = u_b = h = T_w = 1, R = 1/(gamma M_b^2), mu_w = 2/Re_b.
+    kind "bl" (boundary layer, optionally with an impinging oblique shock): free stream
+    rho = u = T = 1, length delta_in = 1, R = 1/(gamma M^2), mu_inf = 1/Re_delta, T_w = t_wall.
+    """
 
     name: str = "channel"
+    kind: str = "channel"
     nx: int = 64
     ny: int = 48
     nz: int = 32
@@ -50,7 +56,17 @@ class Case:
     ly: float = 2.0
     lz: float = math.pi
     beta: float = 1.5            # tanh wall clustering; 0 gives a uniform y grid
+    y_map: str = "tanh"          # "tanh": clustered at both walls; "tanh1": at y = 0 only
     y_wall: bool = True          # isothermal staggered walls in y (else periodic)
+    bc_xmin: str = None          # face kinds ("periodic", "wall", "char", "recycle"); None:
+    bc_xmax: str = None          #   x periodic, y walls or periodic per y_wall
+    bc_ymin: str = None
+    bc_ymax: str = None
+    shock: bool = False          # oblique shock imposed at the top (characteristic) face
+    shock_theta: float = 0.0     # flow deflection of the shock (radians)
+    shock_ximp: float = 0.0      # x where the incident shock reaches the wall
+    i_recycle: int = 0           # recycling plane (x index) of a recycling inflow
+    delta_in: float = 1.0        # inflow boundary-layer thickness
     gamma: float = 1.4
     prandtl: float = 0.72
     mach: float = 1.5            # bulk Mach number u_b / c_w
@@ -80,11 +96,18 @@ class Case:
 
     @property
     def mu_ref(self) -> float:
-        return 2.0 / self.reynolds
+        return 2.0 / self.reynolds if self.kind == "channel" else 1.0 / self.reynolds
 
     @property
     def t_ref(self) -> float:
-        return self.t_wall
+        return self.t_wall if self.kind == "channel" else 1.0
+
+    @property
+    def ref(self):
+        """Free-stream primitives (rho, u, v, w, p) of a boundary-layer case."""
+        if self.kind == "channel":
+            return None
+        return (1.0, 1.0, 0.0, 0.0, self.r_gas)
 
     @property
     def npts(self) -> int:
@@ -94,15 +117,38 @@ class Case:
         return dataclasses.replace(self, **kw)
 
 
-# The five benchmark workloads' channel members; C1 is the small parity case, C2 the bench case.
+# The benchmark workloads: C1 is the small channel parity case, C2 the bench case, C3 the
+# supersonic boundary layer and C4 the shock/boundary-layer interaction.
 C1 = Case(name="channel-64x48x32", nx=64, ny=48, nz=32, reynolds=3000.0, steps=20)
 C2 = Case(name="channel-256x192x128", nx=256, ny=192, nz=128, reynolds=7000.0, steps=200)
 
 
+def bl_case(name, nx, ny, nz, lx, ly, lz, shock=False, **kw) -> Case:
+    """Supersonic zero-pressure-gradient boundary layer (Section 3.2): M = 2, Re_delta_in =
+    10000 (Re_theta ~ 1000), T_w/T_inf = 1.7, wall-clustered tanh grid, rescaled recycling
+    inflow from 0.8 lx, characteristic outflow and top, isothermal wall; with shock=True an
+    8-degree oblique shock imposed at the top (Section 3.3) reaching the wall at 0.6 lx."""
+    base = dict(name=name, kind="bl", nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz, beta=2.5,
+                y_map="tanh1", mach=2.0, reynolds=10000.0, t_wall=1.7, forcing=False,
+                bc_xmin="recycle", bc_xmax="char", bc_ymin="wall", bc_ymax="char",
+                i_recycle=int(0.8 * nx), delta_in=1.0, u0=1.0, l0=1.0, noise=0.05,
+                shock=shock, shock_theta=math.radians(8.0) if shock else 0.0,
+                shock_ximp=0.6 * lx)
+    base.update(kw)
+    return Case(**base)
+
+
+C3 = bl_case("bl-1024x256x256", 1024, 256, 256, 26.25, 12.0, 5.0)
+C4 = bl_case("sbli-2048x384x256", 2048, 384, 256, 50.0, 12.0, 5.33, shock=True, noise=0.001)
+
+
 def node_y(case: Case) -> np.ndarray:
     """Wall-normal node positions used to lay out the initial profile (nodes at the cell
-    centres of a tanh-clustered grid between the walls y = -ly/2 and y = ly/2)."""
+    centres of a tanh-clustered grid between the walls y = -ly/2 and y = ly/2, or of a grid
+    clustered at the wall y = 0 up to y = ly for "tanh1")."""
     eta = (np.arange(case.ny) + 0.5) / case.ny
+    if case.beta and case.beta > 0 and case.y_map == "tanh1":
+        return case.ly * (1.0 - np.tanh(case.beta * (1.0 - eta)) / math.tanh(case.beta))
     if case.beta and case.beta > 0:
         return 0.5 * case.ly * np.tanh(case.beta * (2.0 * eta - 1.0)) / math.tanh(case.beta)
     return case.ly * (eta - 0.5)
@@ -132,6 +178,30 @@ def channel_state(case: Case, seed: int | None = None) -> np.ndarray:
     out[3] = rho * w
     out[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
     return out
+
+
+def bl_state(case: Case, seed: int | None = None) -> np.ndarray:
+    """Initial boundary layer: u/u_inf = (h/delta_in)^(1/7) below delta_in and 1 above,
+    temperature from the Crocco-Busemann relation T = T_w + (T_r - T_w) u + (1 - T_r) u^2 with
+    the recovery temperature T_r = 1 + r (gamma-1)/2 M^2, r = Pr^(1/3), uniform pressure, and
+    uniform velocity noise of amplitude ``case.noise`` inside the layer (SplitMix64 stream)."""
+    seed = case.seed if seed is None else seed
+    nz, ny, nx = case.nz, case.ny, case.nx
+    yy = node_y(case)
+    h = yy - (0.0 if case.y_map == "tanh1" else -0.5 * case.ly)
+    ub = np.minimum(np.maximum(h / case.delta_in, 0.0) ** (1.0 / 7.0), 1.0)
+    tr = 1.0 + case.prandtl ** (1.0 / 3.0) * 0.5 * (case.gamma - 1.0) * case.mach ** 2
+    T1 = case.t_wall + (tr - case.t_wall) * ub + (1.0 - tr) * ub * ub
+    r = uniform(seed, (3, nz, ny, nx))
+    inside = (h < case.delta_in)[None, :, None]
+    noise = case.noise * (2.0 * r - 1.0) * inside
+    u = ub[None, :, None] + noise[0]
+    v = noise[1]
+    w = noise[2]
+    T = np.broadcast_to(T1[None, :, None], (nz, ny, nx))
+    p = case.r_gas  # p_inf = rho_inf R T_inf
+    rho = p / (case.r_gas * T)
+    return primitive_state(case, rho, u, v, w, T)
 
 
 def random_state(case: Case, seed: int, amp_u: float = 0.3, amp_rho: float = 0.2,
