@@ -20,9 +20,10 @@
  *     variants) synchronise that stream; the others return without waiting.
  *   - Concurrency: a context is not thread safe; use one context per host thread/stream.
  *
- * Grid (Section 3.1): nx*ny*nz nodes; x and z uniform and periodic; y nodes at
- * eta_j = (j + 1/2)/ny mapped by y = (ly/2) tanh(beta (2 eta - 1))/tanh(beta) (beta = 0 gives
- * a uniform grid), so that walls at eta = 0 and 1 fall on interfaces (staggered wall).
+ * Grid (Sections 3.1-3.3): nx*ny*nz nodes; x and z uniform (x_i = (i + 1/2) lx/nx); y nodes at
+ * eta_j = (j + 1/2)/ny mapped by y = (ly/2) tanh(beta (2 eta - 1))/tanh(beta) (both walls), by
+ * y = ly (1 - tanh(beta (1 - eta))/tanh(beta)) (one wall at y = 0), or uniformly, so that walls
+ * at eta = 0 and 1 fall on interfaces (staggered wall). z is periodic; x and y periodic by default.
  * Non-dimensional gas: p = rho R T, E = cv T + |u|^2/2, H = E + p/rho, k = cp mu/Pr.
  */
 #ifndef STRM_H
@@ -43,9 +44,16 @@ enum {
   STRM_ETIMEOUT = -5    /* reserved for bounded device-side waits */
 };
 
-enum { STRM_MAP_UNIFORM = 0, STRM_MAP_TANH = 1 };
-enum { STRM_BC_PERIODIC = 0, STRM_BC_WALL_ISOTHERMAL = 1 };
-enum { STRM_FACE_YMIN_YMAX = 0 };
+enum { STRM_MAP_UNIFORM = 0, STRM_MAP_TANH = 1, STRM_MAP_TANH_ONESIDED = 2 };
+enum {
+  STRM_BC_PERIODIC = 0,        /* no params */
+  STRM_BC_WALL_ISOTHERMAL = 1, /* y faces; no params */
+  STRM_BC_CHARACTERISTIC = 2,  /* 5 params: reference rho, u, v, w, p */
+  STRM_BC_RECYCLE_INFLOW = 3,  /* x-min; 7 params: reference rho, u, v, w, p, recycling plane i, delta_in */
+  STRM_BC_SHOCK_TOP = 4        /* y-max; 7 params: free stream rho, u, v, w, p, deflection theta
+                                  (radians), x where the incident shock reaches the wall */
+};
+enum { STRM_FACE_YMIN_YMAX = 0, STRM_FACE_XMIN = 1, STRM_FACE_XMAX = 2, STRM_FACE_YMIN = 3, STRM_FACE_YMAX = 4 };
 enum { STRM_WENO_OFF = 0, STRM_WENO_SENSOR = 1, STRM_WENO_ALL = 2 };
 enum { STRM_VISC_POWER = 0, STRM_VISC_SUTHERLAND = 1 };
 /* STRM_PREC_FP64: every operation in FP64. STRM_PREC_MIXED: flux, sensor, WENO and viscous
@@ -96,9 +104,23 @@ size_t strm_workspace_bytes(const strm_grid* g, const strm_scheme* s);
 int strm_init_grid(strm_ctx** ctx, const strm_grid* g, const strm_phys* p, const strm_scheme* s,
                    void* workspace, size_t workspace_bytes, void* stream);
 
-/* Boundary condition of the y faces (x and z are always periodic). kind =
- * STRM_BC_PERIODIC or STRM_BC_WALL_ISOTHERMAL (no-slip, T = t_wall, staggered: Section 3.1).
- * params/nparams are reserved and must be NULL/0. */
+/* Boundary kind of a face (z faces are periodic). STRM_FACE_YMIN_YMAX sets both y faces to
+ * periodic or wall. A periodic face needs a periodic opposite face (checked at the next
+ * evaluation). Kinds:
+ *   WALL_ISOTHERMAL: no-slip, T = t_wall, staggered (Section 3.1): mirrored ghosts, no mass,
+ *     tangential-momentum or energy flux through the wall face.
+ *   CHARACTERISTIC (Section 3.2, non-reflecting top and outflow): ghosts from the eigenvectors at
+ *     the boundary node; outgoing characteristic variables extrapolated at zeroth order, incoming
+ *     ones from a reference state: at y faces the reference primitives; at x faces (outflow) the
+ *     boundary node's state at the reference pressure, since the outflow plane crosses the
+ *     boundary layer and a subsonic outflow prescribes only the far-field pressure.
+ *   RECYCLE_INFLOW (x-min): ghost plane -1-q copies interior plane i_recycle-q with heights
+ *     stretched by delta_r/delta_in, delta_r where the spanwise-mean u of the recycling plane first
+ *     reaches 0.99 u_ref (a rescaled recycling inflow; the paper's digital-filter inflow needs a
+ *     Reynolds-stress dataset).
+ *   SHOCK_TOP (y-max, Section 3.3): characteristic face whose reference is, downstream of the
+ *     shock foot x_imp - ly/tan(beta), the weak oblique-shock post-shock state of deflection theta.
+ * Returns STRM_EINVAL for a wrong face, kind or parameter count. */
 int strm_set_bc(strm_ctx* ctx, int face, int kind, const double* params, int nparams);
 
 /* rhs <- R(w): convective (central or WENO per the sensor), viscous and forcing terms

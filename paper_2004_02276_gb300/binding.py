@@ -20,6 +20,9 @@ _STATUS = {-1: "EINVAL", -2: "ECUDA", -3: "ENONFINITE", -4: "ENOMEM", -5: "ETIME
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
 VISC_LAWS = {"power": 0, "sutherland": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2}
+FACES = {"xmin": 1, "xmax": 2, "ymin": 3, "ymax": 4}
+BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3, "shock": 4}
 
 
 class StrmError(RuntimeError):
@@ -110,7 +113,8 @@ def _check(fn, rc):
 def structs(case):
     """ABI structs for a workload (``inputs.Case`` or an object with the same attributes)."""
     beta = getattr(case, "beta", 0.0) or 0.0
-    g = Grid(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, 1 if beta > 0 else 0, beta)
+    ymap = Y_MAPS[getattr(case, "y_map", "tanh")] if beta > 0 else 0
+    g = Grid(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, ymap, beta)
     p = Phys(case.gamma, case.prandtl, case.r_gas, VISC_LAWS[getattr(case, "visc_law", "power")],
              case.mu_ref, getattr(case, "t_ref", 1.0), getattr(case, "visc_exp", 0.76),
              getattr(case, "suth_s", 0.0), getattr(case, "t_wall", 1.0),
@@ -127,6 +131,41 @@ def structs(case):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def face_settings(case):
+    """(face, kind, params) calls that give a context the boundary kinds of a workload."""
+    ywall = getattr(case, "y_wall", False)
+    kinds = {
+        "xmin": getattr(case, "bc_xmin", None) or "periodic",
+        "xmax": getattr(case, "bc_xmax", None) or "periodic",
+        "ymin": getattr(case, "bc_ymin", None) or ("wall" if ywall else "periodic"),
+        "ymax": getattr(case, "bc_ymax", None) or ("wall" if ywall else "periodic"),
+    }
+    ref = list(getattr(case, "ref", None) or (1.0, 0.0, 0.0, 0.0, 1.0))
+    out = []
+    for face, kind in kinds.items():
+        if kind in ("periodic", "wall"):
+            out.append((FACES[face], BC_KINDS[kind], None))
+        elif kind == "char" and face == "ymax" and getattr(case, "shock", False):
+            out.append((FACES[face], BC_KINDS["shock"], ref + [case.shock_theta, case.shock_ximp]))
+        elif kind == "char":
+            out.append((FACES[face], BC_KINDS[kind], ref))
+        elif kind == "recycle":
+            out.append((FACES[face], BC_KINDS[kind], ref + [float(case.i_recycle), case.delta_in]))
+        else:
+            raise ValueError(f"unknown boundary kind {kind!r}")
+    return out
+
+
+def apply_faces(lib_, ctx, case):
+    for face, kind, params in face_settings(case):
+        if params is None:
+            rc = lib_.strm_set_bc(ctx, face, kind, None, 0)
+        else:
+            arr = (ctypes.c_double * len(params))(*params)
+            rc = lib_.strm_set_bc(ctx, face, kind, arr, len(params))
+        _check("strm_set_bc", rc)
 
 
 def conserved_totals_static(case, w, stream=None):
@@ -163,8 +202,7 @@ class Solver:
             ctypes.byref(ctx), ctypes.byref(self.g), ctypes.byref(self.p), ctypes.byref(self.s),
             _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
         self.ctx = ctx
-        if getattr(case, "y_wall", False):
-            _check("strm_set_bc", L.strm_set_bc(self.ctx, 0, 1, None, 0))
+        apply_faces(L, self.ctx, case)
 
     @property
     def shape(self):

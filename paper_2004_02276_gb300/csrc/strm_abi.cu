@@ -57,7 +57,8 @@ struct Layout {
 
 bool valid_grid(const strm_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->lx > 0 && g->ly > 0 && g->lz > 0 &&
-         (g->y_map == STRM_MAP_UNIFORM || (g->y_map == STRM_MAP_TANH && g->beta > 0));
+         (g->y_map == STRM_MAP_UNIFORM ||
+          ((g->y_map == STRM_MAP_TANH || g->y_map == STRM_MAP_TANH_ONESIDED) && g->beta > 0));
 }
 
 bool valid_scheme(const strm_scheme* s) {
@@ -113,7 +114,7 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   L.off_scal = off;
   off = align_up(off + sizeof(double) * kScalCount);
   L.off_metric = off;
-  off = align_up(off + sizeof(double) * 4 * (size_t)d.ny);
+  off = align_up(off + sizeof(double) * 6 * (size_t)d.ny);  // 4 metrics, heights, recycle means
   L.off_metric32 = off;
   off = align_up(off + sizeof(float) * 3 * (size_t)d.ny);
   L.total = off;
@@ -157,6 +158,47 @@ struct strm_ctx {
 };
 
 namespace {
+
+// Weak-branch oblique shock (Section 3.3): the deflection theta(beta) = atan(2 cot beta
+// (M^2 sin^2 beta - 1) / (M^2 (gamma + cos 2 beta) + 2)) grows from 0 at the Mach angle to a
+// maximum; the weak shock angle is the root below that maximum (found by bisection after a
+// golden-section search for the maximum), followed by the normal-shock relations.
+double deflection(double gamma, double M, double beta) {
+  double sb = std::sin(beta);
+  return std::atan(2.0 / std::tan(beta) * (M * M * sb * sb - 1.0) / (M * M * (gamma + std::cos(2.0 * beta)) + 2.0));
+}
+
+bool oblique_shock(double gamma, double M, double theta, double* beta, double* pr, double* rr, double* m2) {
+  if (!(M > 1.0) || !(theta > 0.0)) return false;
+  const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+  double a = std::asin(1.0 / M), b = 0.5 * std::acos(-1.0);
+  double x1 = b - g * (b - a), x2 = a + g * (b - a);
+  for (int it = 0; it < 200; ++it) {
+    if (deflection(gamma, M, x1) < deflection(gamma, M, x2)) {
+      a = x1;
+      x1 = x2;
+      x2 = a + g * (b - a);
+    } else {
+      b = x2;
+      x2 = x1;
+      x1 = b - g * (b - a);
+    }
+  }
+  double bmax = 0.5 * (a + b);
+  if (theta > deflection(gamma, M, bmax)) return false;
+  double lo = std::asin(1.0 / M), hi = bmax;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    (deflection(gamma, M, mid) < theta ? lo : hi) = mid;
+  }
+  double bs = 0.5 * (lo + hi), mn = M * std::sin(bs);
+  *beta = bs;
+  *pr = 1.0 + 2.0 * gamma / (gamma + 1.0) * (mn * mn - 1.0);
+  *rr = (gamma + 1.0) * mn * mn / ((gamma - 1.0) * mn * mn + 2.0);
+  double m2n2 = (mn * mn + 2.0 / (gamma - 1.0)) / (2.0 * gamma / (gamma - 1.0) * mn * mn - 1.0);
+  *m2 = std::sqrt(m2n2) / std::sin(bs - theta);
+  return true;
+}
 
 template <typename R>
 void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const strm_grid& g) {
@@ -226,25 +268,36 @@ void build_metrics(strm_ctx* x) {
   const strm_grid& g = x->g;
   int ny = g.ny;
   double deta = 1.0 / ny, dx = g.lx / g.nx, dz = g.lz / g.nz;
-  x->metric_host.assign(4 * (size_t)ny, 0.0);
+  x->metric_host.assign(5 * (size_t)ny, 0.0);
   double vt = 0.0;
   for (int j = 0; j < ny; ++j) {
-    double eta = (j + 0.5) * deta, ye, yee;
-    if (g.y_map == STRM_MAP_TANH) {
+    double eta = (j + 0.5) * deta, ye, yee, h;
+    if (g.y_map == STRM_MAP_TANH_ONESIDED) {
+      // y = ly (1 - tanh(beta (1 - eta)) / tanh(beta)), wall at y = 0
+      double A = g.ly / std::tanh(g.beta);
+      double th = std::tanh(g.beta * (1.0 - eta));
+      double sech2 = 1.0 - th * th;
+      ye = A * g.beta * sech2;
+      yee = 2.0 * A * g.beta * g.beta * sech2 * th;
+      h = g.ly - A * th;
+    } else if (g.y_map == STRM_MAP_TANH) {
       double A = 0.5 * g.ly / std::tanh(g.beta);
       double th = std::tanh(g.beta * (2.0 * eta - 1.0));
       double sech2 = 1.0 - th * th;
       ye = 2.0 * g.beta * A * sech2;
       yee = -8.0 * g.beta * g.beta * A * sech2 * th;
+      h = A * th + 0.5 * g.ly;
     } else {
       ye = g.ly;
       yee = 0.0;
+      h = g.ly * eta;
     }
     double ih = 1.0 / (ye * deta);
     x->metric_host[j] = ih;
     x->metric_host[ny + j] = ih * ih;
     x->metric_host[2 * ny + j] = yee / (ye * ye * ye * deta);
     x->metric_host[3 * ny + j] = dx * (ye * deta) * dz;
+    x->metric_host[4 * ny + j] = h;  // height above the wall eta = 0
     vt += x->metric_host[3 * ny + j];
   }
   x->metric_host32.resize(3 * (size_t)ny);
@@ -316,9 +369,12 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   const Dims& d = x->d;
   const Consts& C = x->C;
   const Bufs& B = x->B;
+  if ((C.bc[0] == kBcPeriodic) != (C.bc[1] == kBcPeriodic) || (C.bc[2] == kBcPeriodic) != (C.bc[3] == kBcPeriodic))
+    return fail(STRM_EINVAL, "a periodic face needs a periodic opposite face");
   STRM_CK(cudaMemsetAsync(B.wcount, 0, 8 * sizeof(unsigned), st));
   STRM_LAUNCH(STRM_K_PRIMS, launch_prims(d, C, B, w, dt_mode && dt_fixed <= 0.0, st));
   if (dt_mode) STRM_LAUNCH(STRM_K_DT, launch_dt_finalize(d, B, cfl, dt_fixed, st));
+  if (C.bc[0] == kBcRecycle) STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_recycle(d, C, B, st));
   STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
   STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, st));
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
@@ -393,7 +449,13 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->d = L.d;
   x->stream = (cudaStream_t)stream;
   set_consts(x);
-  x->C.wall_y = 0;
+  for (int f = 0; f < 4; ++f) x->C.bc[f] = kBcPeriodic;
+  x->C.shock = 0;
+  x->C.i_recycle = 0;
+  x->C.delta_in = 1.0;
+  x->C.dx = g->lx / g->nx;
+  for (int m = 0; m < 5; ++m) x->C.ref[m] = x->C.shock_ref[m] = 0.0;
+  x->C.x_foot = 0.0;
   char* ws = (char*)workspace;
   Nodes<double>& N64 = x->B.n64;
   Nodes<float>& N32 = x->B.n32;
@@ -426,6 +488,8 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->B.m64.c2y = met + g->ny;
   x->B.m64.c1y = met + 2 * g->ny;
   x->B.vol = met + 3 * g->ny;
+  x->B.hy = met + 4 * g->ny;
+  x->B.ubar = met + 5 * g->ny;
   x->B.m32.inv_hy = met32;
   x->B.m32.c2y = met32 + g->ny;
   x->B.m32.c1y = met32 + 2 * g->ny;
@@ -434,7 +498,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 4 * g->ny,
+    e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 5 * g->ny,
                         cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(met32, x->metric_host32.data(), sizeof(float) * 3 * g->ny,
@@ -452,15 +516,71 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
 
 int strm_set_bc(strm_ctx* x, int face, int kind, const double* params, int nparams) {
   if (!x) return fail(STRM_EINVAL, "null context");
-  if (face != STRM_FACE_YMIN_YMAX) return fail(STRM_EINVAL, "only the y faces take a boundary kind");
-  if (params || nparams) return fail(STRM_EINVAL, "params are reserved (NULL, 0)");
-  if (kind == STRM_BC_PERIODIC) {
-    x->C.wall_y = 0;
-  } else if (kind == STRM_BC_WALL_ISOTHERMAL) {
-    if (x->g.ny < G) return fail(STRM_EINVAL, "walls need ny >= 3");
-    x->C.wall_y = 1;
-  } else {
-    return fail(STRM_EINVAL, "unknown boundary kind");
+  Consts& C = x->C;
+  auto need = [&](int n) { return params && nparams == n; };
+  auto set_ref = [&](double* dst) {
+    for (int m = 0; m < 5; ++m) dst[m] = params[m];
+    return params[0] > 0 && params[4] > 0;
+  };
+  switch (face) {
+    case STRM_FACE_YMIN_YMAX:
+      if (kind != STRM_BC_PERIODIC && kind != STRM_BC_WALL_ISOTHERMAL)
+        return fail(STRM_EINVAL, "both y faces take periodic or wall");
+      if (params || nparams) return fail(STRM_EINVAL, "periodic and wall faces take no params");
+      if (kind == STRM_BC_WALL_ISOTHERMAL && x->g.ny < G) return fail(STRM_EINVAL, "walls need ny >= 3");
+      C.bc[2] = C.bc[3] = kind == STRM_BC_PERIODIC ? kBcPeriodic : kBcWall;
+      break;
+    case STRM_FACE_XMIN:
+    case STRM_FACE_XMAX:
+    case STRM_FACE_YMIN:
+    case STRM_FACE_YMAX: {
+      int slot = face - STRM_FACE_XMIN;  // 0 xmin, 1 xmax, 2 ymin, 3 ymax
+      bool xface = slot < 2;
+      if (kind == STRM_BC_PERIODIC) {
+        if (params || nparams) return fail(STRM_EINVAL, "periodic faces take no params");
+        C.bc[slot] = kBcPeriodic;
+      } else if (kind == STRM_BC_WALL_ISOTHERMAL) {
+        if (xface) return fail(STRM_EINVAL, "walls are y faces");
+        if (params || nparams) return fail(STRM_EINVAL, "wall faces take no params");
+        if (x->g.ny < G) return fail(STRM_EINVAL, "walls need ny >= 3");
+        C.bc[slot] = kBcWall;
+      } else if (kind == STRM_BC_CHARACTERISTIC) {
+        if (!need(5) || !set_ref(C.ref)) return fail(STRM_EINVAL, "characteristic faces take 5 params: rho u v w p (rho, p > 0)");
+        C.bc[slot] = kBcChar;
+        if (slot == 3) C.shock = 0;
+      } else if (kind == STRM_BC_RECYCLE_INFLOW) {
+        if (slot != 0) return fail(STRM_EINVAL, "recycling inflow is an x-min face");
+        if (!need(7) || !set_ref(C.ref)) return fail(STRM_EINVAL, "recycling inflow takes 7 params: rho u v w p i_recycle delta_in");
+        int ir = (int)params[5];
+        if (ir != params[5] || ir < G - 1 || ir >= x->g.nx || !(params[6] > 0))
+          return fail(STRM_EINVAL, "recycling plane must be an interior x index >= 2 and delta_in > 0");
+        C.i_recycle = ir;
+        C.delta_in = params[6];
+        C.bc[0] = kBcRecycle;
+      } else if (kind == STRM_BC_SHOCK_TOP) {
+        if (slot != 3) return fail(STRM_EINVAL, "the oblique-shock reference is a y-max face");
+        if (!need(7) || !set_ref(C.ref)) return fail(STRM_EINVAL, "shock top takes 7 params: rho u v w p theta x_imp");
+        double beta, pr, rr, m2;
+        double c1 = std::sqrt(C.gamma * params[4] / params[0]);
+        if (!oblique_shock(C.gamma, params[1] / c1, params[5], &beta, &pr, &rr, &m2))
+          return fail(STRM_EINVAL, "deflection beyond the attached oblique-shock limit");
+        // post-shock state: the stream deflected by theta toward the wall, shock foot on the top
+        double V1 = params[1], un1 = V1 * std::sin(beta), ut = V1 * std::cos(beta), un2 = un1 / rr;
+        C.shock_ref[0] = params[0] * rr;
+        C.shock_ref[1] = ut * std::cos(beta) + un2 * std::sin(beta);
+        C.shock_ref[2] = -ut * std::sin(beta) + un2 * std::cos(beta);
+        C.shock_ref[3] = 0.0;
+        C.shock_ref[4] = params[4] * pr;
+        C.x_foot = params[6] - x->g.ly / std::tan(beta);
+        C.shock = 1;
+        C.bc[3] = kBcChar;
+      } else {
+        return fail(STRM_EINVAL, "unknown boundary kind");
+      }
+      break;
+    }
+    default:
+      return fail(STRM_EINVAL, "unknown face");
   }
   if (x->gexec) {  // the captured graph holds the old constants
     cudaGraphExecDestroy(x->gexec);
@@ -577,6 +697,7 @@ int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsign
                 unsigned char* fy, unsigned char* fz) {
   if (!x || !w) return fail(STRM_EINVAL, "null context or state");
   launch_prims(x->d, x->C, x->B, w, false, x->stream);
+  if (x->C.bc[0] == kBcRecycle) launch_recycle(x->d, x->C, x->B, x->stream);
   launch_ghost_prims(x->d, x->C, x->B, x->stream);
   launch_sensor(x->d, x->C, x->B, x->stream);
   launch_export_sensor(x->d, x->C, x->B, theta, div, x->stream);

@@ -27,7 +27,7 @@ struct Inst {
   double* r_old;
 };
 
-enum { kKindNode = 0, kKindGhost = 1, kKindFace = 2, kKinds = 5 };  // faces: 2, 3, 4
+enum { kKindNode = 0, kKindGhost = 1, kKindFace = 2, kKindRow = 5, kKinds = 6 };  // faces: 2, 3, 4
 
 struct BatchIndex {
   const Inst* inst;  // device table [n]
@@ -83,12 +83,25 @@ __global__ void kb_dt_finalize(BatchIndex X, double cfl, double dt_fixed) {
   body_dt_finalize(I.B, inst_blocks(X, kKindNode, blockIdx.x), cfl, dt_fixed, sh);
 }
 
-template <bool MIXED>
 __global__ void __launch_bounds__(256) kb_ghost_prims(BatchIndex X) {
   int blk;
   const Inst& I = block_inst(X, kKindGhost, blk);
-  if (MIXED) body_ghost_prims_mixed(I.d, I.C, I.B, ghost_count(I.d), blk);
-  else body_ghost_prims(I.d, I.C, I.B, ghost_count(I.d), blk);
+  body_ghost_prims(I.d, I.C, I.B, ghost_count(I.d), blk);
+}
+
+// recycling inflow: spanwise means (one block per row j of every recycling instance), then the
+// rescale factor (one block per instance)
+__global__ void kb_recycle_mean(BatchIndex X) {
+  __shared__ double sh[32];
+  int blk;
+  const Inst& I = block_inst(X, kKindRow, blk);
+  if (I.C.bc[0] != kBcRecycle) return;
+  body_recycle_mean(I.d, I.C, I.B, blk, sh);
+}
+
+__global__ void kb_recycle_scale(BatchIndex X) {
+  const Inst& I = X.inst[blockIdx.x];
+  if (I.C.bc[0] == kBcRecycle && threadIdx.x == 0) body_recycle_scale(I.d, I.C, I.B);
 }
 
 template <int L, typename R>
@@ -183,6 +196,7 @@ struct strm_ensemble {
   int n = 0;
   int L = 3;
   bool mixed = false;
+  bool any_recycle = false;
   cudaStream_t stream = nullptr;
   int sms = 0;
   std::vector<strm_ctx*> ctx;
@@ -220,7 +234,11 @@ void enqueue_rhs_t(const strm_ensemble* E, bool dt_mode, double cfl, double dt_f
   kb_zero_counts<<<nblocks(E->n, 32), 32, 0, st>>>(X);
   kb_prims<MIXED><<<E->total_blocks[kKindNode], 256, 0, st>>>(X, dt_mode && dt_fixed <= 0.0 ? 1 : 0);
   if (dt_mode) kb_dt_finalize<<<E->n, 1024, 0, st>>>(X, cfl, dt_fixed);
-  kb_ghost_prims<MIXED><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
+  if (E->any_recycle) {
+    kb_recycle_mean<<<E->total_blocks[kKindRow], 256, 0, st>>>(X);
+    kb_recycle_scale<<<E->n, 32, 0, st>>>(X);
+  }
+  kb_ghost_prims<<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
   kb_sensor<L, R><<<E->total_blocks[kKindNode], 256, 0, st>>>(X);
   kb_ghost_scalars<R><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
   kb_classify<L, 0, R><<<E->total_blocks[kKindFace + 0], 256, 0, st>>>(X);
@@ -335,6 +353,7 @@ int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, con
     E->ctx.push_back(c);
     Inst& I = E->inst_host[e];
     ctx_parts(c, &I.d, &I.C, &I.B, &E->sms);
+    if (I.C.bc[0] == kBcRecycle) E->any_recycle = true;
     I.w = I.r_old = nullptr;
     off += b;
   }
@@ -345,9 +364,14 @@ int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, con
     int acc = 0;
     for (int e = 0; e < n; ++e) {
       const Dims& d = E->inst_host[e].d;
-      long long cnt = k == kKindNode ? d.N : (k == kKindGhost ? ghost_count_host(d) : d.nf[k - kKindFace]);
+      int nb;
+      if (k == kKindRow) nb = d.ny;  // one block per row
+      else {
+        long long cnt = k == kKindNode ? d.N : (k == kKindGhost ? ghost_count_host(d) : d.nf[k - kKindFace]);
+        nb = (int)nblocks(cnt, 256);
+      }
       E->start_host[k * (n + 1) + e] = acc;
-      acc += (int)nblocks(cnt, 256);
+      acc += nb;
     }
     E->start_host[k * (n + 1) + n] = acc;
     E->total_blocks[k] = acc;

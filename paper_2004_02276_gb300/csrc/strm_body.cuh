@@ -125,20 +125,19 @@ __device__ __forceinline__ void body_dt_finalize(const Bufs& B, int nparts, doub
 // ---------------------------------------------------------------------------------- ghost fills
 
 // Thread layout of a face ghost fill: x faces (2G * ny * nz), then y faces (nx * 2G * nz), then
-// z faces (nx * ny * 2G). Edges and corners are never read and stay untouched.
-__device__ __forceinline__ bool ghost_target(const Dims& d, long long q, int& face, int& i, int& j,
-                                             int& k, int& si, int& sj, int& sk, int& mirror) {
+// z faces (nx * ny * 2G). The ghost node is (i, j, k); side is 0 for the min face, 1 for the max
+// face; layer 0..G-1 counts away from the boundary. Edges and corners are never read.
+__device__ __forceinline__ bool ghost_target(const Dims& d, long long q, int& face, int& side, int& layer,
+                                             int& i, int& j, int& k) {
   long long nxf = 2LL * G * d.ny * d.nz, nyf = 2LL * G * d.nx * d.nz, nzf = 2LL * G * d.nx * d.ny;
-  mirror = 0;
   if (q < nxf) {
     int g = (int)(q % (2 * G));
     long long r = q / (2 * G);
     j = (int)(r % d.ny);
     k = (int)(r / d.ny);
-    i = g < G ? -1 - g : d.nx + (g - G);
-    si = wrapi(i, d.nx);
-    sj = j;
-    sk = k;
+    side = g < G ? 0 : 1;
+    layer = g < G ? g : g - G;
+    i = side == 0 ? -1 - layer : d.nx + layer;
     face = 0;
     return true;
   }
@@ -148,12 +147,10 @@ __device__ __forceinline__ bool ghost_target(const Dims& d, long long q, int& fa
     long long r = q / d.nx;
     int g = (int)(r % (2 * G));
     k = (int)(r / (2 * G));
-    j = g < G ? -1 - g : d.ny + (g - G);
-    si = i;
-    sk = k;
+    side = g < G ? 0 : 1;
+    layer = g < G ? g : g - G;
+    j = side == 0 ? -1 - layer : d.ny + layer;
     face = 1;
-    sj = wrapi(j, d.ny);
-    mirror = g < G ? g : d.ny - 1 - (g - G);  // wall mirror: j=-1-q <-> q, j=ny+q <-> ny-1-q
     return true;
   }
   q -= nyf;
@@ -162,14 +159,60 @@ __device__ __forceinline__ bool ghost_target(const Dims& d, long long q, int& fa
     long long r = q / d.nx;
     j = (int)(r % d.ny);
     int g = (int)(r / d.ny);
-    k = g < G ? -1 - g : d.nz + (g - G);
-    si = i;
-    sj = j;
-    sk = wrapi(k, d.nz);
+    side = g < G ? 0 : 1;
+    layer = g < G ? g : g - G;
+    k = side == 0 ? -1 - layer : d.nz + layer;
     face = 2;
     return true;
   }
   return false;
+}
+
+// Primitive state of a node (FP64).
+struct PState {
+  double rho, u, v, w, p, T;
+};
+
+__device__ __forceinline__ PState load_pstate(const Nodes<double>& P, long long n) {
+  return PState{P.rho[n], P.u[n], P.v[n], P.w[n], P.p[n], P.T[n]};
+}
+
+__device__ __forceinline__ PState pstate_from_prims(const Consts& C, const double* q) {
+  // (rho, u, v, w, p) -> with T = p / (rho R)
+  return PState{q[0], q[1], q[2], q[3], q[4], q[4] / (q[0] * C.r_gas)};
+}
+
+// Write a ghost state: FP64 fields (all of them in FP64 precision; the projection's in mixed
+// precision) and, in mixed precision, the FP32 copies with c and mu(T) in FP32.
+__device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, long long dst, const PState& g) {
+  const Nodes<double>& P = B.n64;
+  P.rho[dst] = g.rho;
+  P.u[dst] = g.u;
+  P.v[dst] = g.v;
+  P.w[dst] = g.w;
+  P.p[dst] = g.p;
+  P.T[dst] = g.T;
+  // explicit rounding: the same bits whichever kernel (single grid or batched) inlines this
+  double q2 = __fma_rn(g.u, g.u, __fma_rn(g.v, g.v, __dmul_rn(g.w, g.w)));
+  double H = __fma_rn(C.cp, g.T, __dmul_rn(0.5, q2));
+  P.H[dst] = H;
+  P.srho[dst] = sqrt(g.rho);
+  if (!C.mixed) {
+    P.c[dst] = sqrt(C.gamma * g.p / g.rho);
+    P.mu[dst] = viscosity(C.k64, C.visc_law, g.T);
+  } else {
+    const Nodes<float>& F = B.n32;
+    float rf = (float)g.rho, pf = (float)g.p, Tf = (float)g.T;
+    F.rho[dst] = rf;
+    F.u[dst] = (float)g.u;
+    F.v[dst] = (float)g.v;
+    F.w[dst] = (float)g.w;
+    F.p[dst] = pf;
+    F.T[dst] = Tf;
+    F.H[dst] = (float)H;
+    F.c[dst] = sqrtf(C.k32.gamma * pf / rf);
+    F.mu[dst] = viscosity(C.k32, C.visc_law, Tf);
+  }
 }
 
 template <typename R>
@@ -187,99 +230,215 @@ __device__ __forceinline__ void copy_node(const Nodes<R>& P, long long dst, long
   }
 }
 
+__device__ __forceinline__ void copy_ghost(const Consts& C, const Bufs& B, long long dst, long long src) {
+  copy_node(B.n64, dst, src, !C.mixed);
+  B.n64.srho[dst] = B.n64.srho[src];
+  if (C.mixed) copy_node(B.n32, dst, src, true);
+}
+
 // Isothermal no-slip staggered wall: the ghost mirrors an interior node across the wall
 // interface with reversed velocity, T_g = 2 T_w - T, p_g = p, rho_g = p_g/(R T_g).
-struct WallGhost {
-  double rho, u, v, w, p, T, H;
-};
-
-__device__ __forceinline__ WallGhost wall_state(const Consts& C, const Nodes<double>& P, long long src) {
-  WallGhost g;
-  g.u = -P.u[src];
-  g.v = -P.v[src];
-  g.w = -P.w[src];
-  g.p = P.p[src];
-  g.T = 2.0 * C.t_wall - P.T[src];
+__device__ __forceinline__ PState wall_pstate(const Consts& C, const PState& s) {
+  PState g;
+  g.u = -s.u;
+  g.v = -s.v;
+  g.w = -s.w;
+  g.p = s.p;
+  g.T = 2.0 * C.t_wall - s.T;
   g.rho = g.p / (C.r_gas * g.T);
-  g.H = C.cp * g.T + 0.5 * (g.u * g.u + g.v * g.v + g.w * g.w);
   return g;
 }
 
-__device__ __forceinline__ void store_wall64(const Nodes<double>& P, long long dst, const WallGhost& g) {
-  P.rho[dst] = g.rho;
-  P.u[dst] = g.u;
-  P.v[dst] = g.v;
-  P.w[dst] = g.w;
-  P.p[dst] = g.p;
-  P.T[dst] = g.T;
-  P.H[dst] = g.H;
-  P.srho[dst] = sqrt(g.rho);
+// Non-reflecting characteristic ghost (Section 3.2, characteristic decomposition normal to the
+// boundary): eigenvectors of the Euler flux along dir at the boundary node b; a characteristic
+// variable whose speed points out of the domain (outward = +1 at a max face, -1 at a min face)
+// is extrapolated from b at zeroth order, the others come from the reference state r. The left
+// eigenvector rows are applied through the acoustic scalars A = b2 x0 + b1 (x4 - u.m),
+// Bn = (u_n x0 - m_n)/c and the shear rows; the right eigenvectors map back.
+__device__ __forceinline__ PState char_pstate(const Consts& C, const PState& b, const PState& r, int dir,
+                                              int outward) {
+  const double ub[3] = {b.u, b.v, b.w};
+  const int t1 = dir == 0 ? 1 : 0, t2 = dir == 2 ? 1 : 2;
+  double q2 = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+  double H = C.cp * b.T + 0.5 * q2;
+  double c = sqrt(C.gamma * b.p / b.rho);
+  double ic = 1.0 / c;
+  double b1 = C.gm1 * ic * ic, b2 = 0.5 * q2 * b1;
+  double un = ub[dir];
+  // conserved states of b and r
+  double xb[5] = {b.rho, b.rho * b.u, b.rho * b.v, b.rho * b.w, b.rho * (C.cv * b.T + 0.5 * q2)};
+  double xr[5] = {r.rho, r.rho * r.u, r.rho * r.v, r.rho * r.w,
+                  r.rho * (C.cv * r.T + 0.5 * (r.u * r.u + r.v * r.v + r.w * r.w))};
+  double Wb[5], Wr[5];
+  const double* xs[2] = {xb, xr};
+  double* Ws[2] = {Wb, Wr};
+  for (int s = 0; s < 2; ++s) {
+    const double* x = xs[s];
+    double um = ub[0] * x[1] + ub[1] * x[2] + ub[2] * x[3];
+    double A = b2 * x[0] + b1 * (x[4] - um);
+    double Bn = (un * x[0] - x[1 + dir]) * ic;
+    Ws[s][0] = 0.5 * (A + Bn);
+    Ws[s][1] = x[0] - A;
+    Ws[s][2] = x[1 + t1] - ub[t1] * x[0];
+    Ws[s][3] = x[1 + t2] - ub[t2] * x[0];
+    Ws[s][4] = 0.5 * (A - Bn);
+  }
+  const double lam[5] = {un - c, un, un, un, un + c};
+  double W[5];
+  for (int k = 0; k < 5; ++k) W[k] = (outward * lam[k] > 0.0) ? Wb[k] : Wr[k];
+  double gs = W[0] + W[1] + W[4];
+  double x[5];
+  x[0] = gs;
+  for (int dd = 0; dd < 3; ++dd) x[1 + dd] = gs * ub[dd];
+  x[1 + dir] += c * (W[4] - W[0]);
+  x[1 + t1] += W[2];
+  x[1 + t2] += W[3];
+  x[4] = H * (W[0] + W[4]) + un * c * (W[4] - W[0]) + 0.5 * q2 * W[1] + ub[t1] * W[2] + ub[t2] * W[3];
+  PState g;
+  g.rho = x[0];
+  double ir = 1.0 / g.rho;
+  g.u = x[1] * ir;
+  g.v = x[2] * ir;
+  g.w = x[3] * ir;
+  g.T = (x[4] * ir - 0.5 * (g.u * g.u + g.v * g.v + g.w * g.w)) * C.inv_cv;
+  g.p = g.rho * C.r_gas * g.T;
+  return g;
 }
 
+// Rescaled recycling inflow (reading): ghost plane i = -1-layer takes interior plane
+// i_recycle - layer with the wall-normal coordinate stretched by s = delta_r / delta_in: the
+// value at height h is the recycled plane's value at height s h, u, v, w, T, p interpolated
+// linearly between nodes (below the first node between the wall state u = v = w = 0, T = T_w,
+// p = p_0 and the first node; above the last node, the last node's value); rho = p / (R T).
+__device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C, const Bufs& B, int layer,
+                                                 int j, int k) {
+  const Nodes<double>& P = B.n64;
+  double s = B.scal[kScalRecycle];
+  double ht = s * __ldg(B.hy + j);
+  int is = C.i_recycle - layer;
+  // first node jb with h[jb] >= ht
+  int lo = 0, hi = d.ny;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(B.hy + mid) < ht) lo = mid + 1;
+    else hi = mid;
+  }
+  int jb = lo;
+  PState a, bb;
+  double alpha;
+  if (jb == d.ny) {
+    bb = load_pstate(P, gidx(d, is, d.ny - 1, k));
+    a = bb;
+    alpha = 1.0;
+  } else {
+    bb = load_pstate(P, gidx(d, is, jb, k));
+    double ha, hb = __ldg(B.hy + jb);
+    if (jb == 0) {
+      a = PState{0.0, 0.0, 0.0, 0.0, bb.p, C.t_wall};
+      ha = 0.0;
+    } else {
+      a = load_pstate(P, gidx(d, is, jb - 1, k));
+      ha = __ldg(B.hy + jb - 1);
+    }
+    alpha = (ht - ha) / (hb - ha);
+  }
+  // linear interpolation with explicit rounding (no contraction left to the compiler)
+  double am = __dadd_rn(1.0, -alpha);
+  auto lerp = [&](double fa, double fb) { return __fma_rn(alpha, fb, __dmul_rn(am, fa)); };
+  PState g;
+  g.T = lerp(a.T, bb.T);
+  g.u = lerp(a.u, bb.u);
+  g.v = lerp(a.v, bb.v);
+  g.w = lerp(a.w, bb.w);
+  g.p = lerp(a.p, bb.p);
+  g.rho = g.p / (C.r_gas * g.T);
+  return g;
+}
+
+// Ghost node primitives by face kind (both precisions).
 __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C, const Bufs& B,
                                                  long long nthreads, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   if (q >= nthreads) return;
-  int face, i, j, k, si, sj, sk, mirror;
-  if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
+  int face, side, layer, i, j, k;
+  if (!ghost_target(d, q, face, side, layer, i, j, k)) return;
   const Nodes<double>& P = B.n64;
   long long dst = gidx(d, i, j, k);
-  if (face == 1 && C.wall_y) {
-    WallGhost g = wall_state(C, P, gidx(d, i, mirror, k));
-    store_wall64(P, dst, g);
-    P.c[dst] = sqrt(C.gamma * g.p / g.rho);
-    P.mu[dst] = viscosity(C.k64, C.visc_law, g.T);
-  } else {
-    long long src = gidx(d, si, sj, sk);
-    copy_node(P, dst, src, true);
-    P.srho[dst] = P.srho[src];
+  int kind = face == 2 ? kBcPeriodic : C.bc[2 * face + side];
+  if (kind == kBcPeriodic) {
+    int si = face == 0 ? wrapi(i, d.nx) : i, sj = face == 1 ? wrapi(j, d.ny) : j;
+    int sk = face == 2 ? wrapi(k, d.nz) : k;
+    copy_ghost(C, B, dst, gidx(d, si, sj, sk));
+    return;
   }
+  PState g;
+  if (kind == kBcWall) {
+    int jm = side == 0 ? layer : d.ny - 1 - layer;  // j=-1-l <-> l, j=ny+l <-> ny-1-l
+    g = wall_pstate(C, load_pstate(P, gidx(d, i, jm, k)));
+  } else if (kind == kBcRecycle) {
+    g = recycle_pstate(d, C, B, layer, j, k);
+  } else {  // characteristic
+    int ib = face == 0 ? (side == 0 ? 0 : d.nx - 1) : i;
+    int jb = face == 1 ? (side == 0 ? 0 : d.ny - 1) : j;
+    PState bs = load_pstate(P, gidx(d, ib, jb, k));
+    PState rs;
+    if (face == 0) {
+      // outflow-type face: the boundary state at the reference pressure (a subsonic outflow
+      // only prescribes the far-field pressure; the plane crosses the boundary layer)
+      rs = bs;
+      rs.p = C.ref[4];
+      rs.T = rs.p / (rs.rho * C.r_gas);
+    } else {
+      bool post = C.shock && side == 1 && (i + 0.5) * C.dx >= C.x_foot;
+      rs = pstate_from_prims(C, post ? C.shock_ref : C.ref);
+    }
+    g = char_pstate(C, bs, rs, face, side == 0 ? -1 : 1);
+  }
+  store_pstate(C, B, dst, g);
 }
 
-// Mixed precision: FP64 fields by the same rules, FP32 copies from them (c, mu in FP32).
-__device__ __forceinline__ void body_ghost_prims_mixed(const Dims& d, const Consts& C, const Bufs& B,
-                                                       long long nthreads, int blk) {
-  long long q = (long long)blk * blockDim.x + threadIdx.x;
-  if (q >= nthreads) return;
-  int face, i, j, k, si, sj, sk, mirror;
-  if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
-  const Nodes<double>& P = B.n64;
-  const Nodes<float>& F = B.n32;
-  long long dst = gidx(d, i, j, k);
-  if (face == 1 && C.wall_y) {
-    WallGhost g = wall_state(C, P, gidx(d, i, mirror, k));
-    store_wall64(P, dst, g);
-    float rf = (float)g.rho, pf = (float)g.p, Tf = (float)g.T;
-    F.rho[dst] = rf;
-    F.u[dst] = (float)g.u;
-    F.v[dst] = (float)g.v;
-    F.w[dst] = (float)g.w;
-    F.p[dst] = pf;
-    F.T[dst] = Tf;
-    F.H[dst] = (float)g.H;
-    F.c[dst] = sqrtf(C.k32.gamma * pf / rf);
-    F.mu[dst] = viscosity(C.k32, C.visc_law, Tf);
-  } else {
-    long long src = gidx(d, si, sj, sk);
-    copy_node(P, dst, src, false);
-    P.srho[dst] = P.srho[src];
-    copy_node(F, dst, src, true);
-  }
-}
-
-// theta and the node divergence: periodic copies, even mirror across a wall.
+// theta and the node divergence: periodic copies, even mirror across a wall, copy of the
+// boundary node at characteristic and inflow faces.
 template <typename R>
 __device__ __forceinline__ void body_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B,
                                                    long long nthreads, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   if (q >= nthreads) return;
-  int face, i, j, k, si, sj, sk, mirror;
-  if (!ghost_target(d, q, face, i, j, k, si, sj, sk, mirror)) return;
+  int face, side, layer, i, j, k;
+  if (!ghost_target(d, q, face, side, layer, i, j, k)) return;
   const Nodes<R>& P = nodes<R>(B);
-  long long dst = gidx(d, i, j, k);
-  long long src = (face == 1 && C.wall_y) ? gidx(d, i, mirror, k) : gidx(d, si, sj, sk);
+  int si = theta_source(i, d.nx, C.bc[0], C.bc[1]);
+  int sj = theta_source(j, d.ny, C.bc[2], C.bc[3]);
+  int sk = theta_source(k, d.nz, kBcPeriodic, kBcPeriodic);
+  long long dst = gidx(d, i, j, k), src = gidx(d, si, sj, sk);
   P.theta[dst] = P.theta[src];
   P.div[dst] = P.div[src];
+}
+
+// Spanwise mean of u at the recycling plane, one block per row j (fixed reduction order).
+__device__ __forceinline__ void body_recycle_mean(const Dims& d, const Consts& C, const Bufs& B, int j,
+                                                  double* sh) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < d.nz; k += blockDim.x) s += B.n64.u[gidx(d, C.i_recycle, j, k)];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) B.ubar[j] = s / d.nz;
+}
+
+// delta_r: the height where the spanwise-mean u first reaches 0.99 of the reference u (linear
+// interpolation from the wall, where u = 0); s = delta_r / delta_in, 1 if never reached.
+__device__ __forceinline__ void body_recycle_scale(const Dims& d, const Consts& C, const Bufs& B) {
+  double target = 0.99 * C.ref[1], pu = 0.0, ph = 0.0, s = 1.0;
+  for (int j = 0; j < d.ny; ++j) {
+    double ub = B.ubar[j], h = B.hy[j];
+    if (ub >= target) {
+      double dr = ph + (target - pu) * (h - ph) / (ub - pu);
+      s = dr / C.delta_in;
+      break;
+    }
+    pu = ub;
+    ph = h;
+  }
+  B.scal[kScalRecycle] = s;
 }
 
 // ---------------------------------------------------------------------------------- sensor
@@ -813,7 +972,7 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
       long long qz = ((long long)k * d.ny + j) * d.nx + i;
       long long sxy = (long long)d.nx * d.ny;
       R hy = __ldg(metric<R>(B).inv_hy + j);
-      bool wlo = C.wall_y && j == 0, whi = C.wall_y && j == d.ny - 1;
+      bool wlo = C.bc[2] == kBcWall && j == 0, whi = C.bc[3] == kBcWall && j == d.ny - 1;
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
         const R* fx = face_flux<R>(B, 0) + m * d.nf[0];

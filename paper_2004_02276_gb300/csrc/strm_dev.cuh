@@ -51,11 +51,24 @@ struct Coefs {
   R gamma, gm1, r_gas, cp, t_wall, mu_ref, inv_tref, visc_exp, suth_s;
 };
 
+// Face kinds: x faces periodic, recycling inflow (x-min) or characteristic; y faces periodic,
+// isothermal wall or characteristic (y-max optionally with the post-shock reference state
+// downstream of the shock foot); z periodic.
+enum { kBcPeriodic = 0, kBcWall = 1, kBcChar = 2, kBcRecycle = 3 };
+
 struct Consts {
   // gas (FP64)
   double gamma, gm1, r_gas, inv_r, cv, inv_cv, cp, cp_pr;
   double mu_ref, inv_tref, visc_exp, suth_s, t_wall;
-  int visc_law, wall_y, forcing;
+  int visc_law, forcing;
+  // boundaries: kinds of the x-min, x-max, y-min, y-max faces; reference primitives
+  // (rho, u, v, w, p) of characteristic faces; oblique shock; recycling inflow
+  int bc[4];
+  double ref[5];
+  int shock;
+  double shock_ref[5], x_foot;
+  int i_recycle;
+  double delta_in, dx;
   // scheme
   int L, weno_mode, convective, viscous, mixed;
   double vtot;  // total metric volume
@@ -77,6 +90,8 @@ struct Bufs {
   Metric<double> m64;
   Metric<float> m32;
   const double* vol;                            // node volume dx (y_eta deta) dz per j
+  const double* hy;                             // node height above the wall eta = 0, per j
+  double* ubar;                                 // spanwise-mean u at the recycling plane, per j
 };
 
 template <typename R> __device__ __forceinline__ const Nodes<R>& nodes(const Bufs& B);
@@ -93,7 +108,7 @@ template <> __device__ __forceinline__ const Coefs<double>& coefs<double>(const 
 template <> __device__ __forceinline__ const Coefs<float>& coefs<float>(const Consts& C) { return C.k32; }
 
 // device scalars
-enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalCount = 16 };
+enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalRecycle = 4, kScalCount = 16 };
 
 __device__ __forceinline__ long long gidx(const Dims& d, int i, int j, int k) {
   return ((long long)(k + G) * d.py + (j + G)) * d.px + (i + GX);
@@ -179,13 +194,16 @@ __device__ __forceinline__ R face_theta_max(const R* __restrict__ theta, long lo
   return tmax;
 }
 
-// Interior node whose theta a ghost node along y carries (periodic copy or even wall mirror);
-// along x and z the ghosts are periodic copies.
-__device__ __forceinline__ int theta_source(int idx, int n, bool wall) {
-  if (!wall) return wrapi(idx, n);
-  if (idx < 0) return -1 - idx;
-  if (idx >= n) return 2 * n - 1 - idx;
-  return idx;
+// Interior node whose theta a ghost node carries along a direction with face kinds lo/hi:
+// periodic copy, even mirror across a wall, copy of the boundary node at other faces.
+__device__ __forceinline__ int theta_source(int idx, int n, int lo, int hi) {
+  if (idx >= 0 && idx < n) return idx;
+  if (idx < 0) {
+    if (lo == kBcPeriodic) return wrapi(idx, n);
+    return lo == kBcWall ? -1 - idx : 0;
+  }
+  if (hi == kBcPeriodic) return wrapi(idx, n);
+  return hi == kBcWall ? 2 * n - 1 - idx : n - 1;
 }
 
 // Hybrid switch decision for the face whose left node is (i,j,k) along dir. FP64 precision
@@ -204,9 +222,9 @@ __device__ __forceinline__ bool face_decision(const Dims& d, const Consts& C, co
   double t64 = 0.0;
   for (int q = -L + 1; q <= L; ++q) {
     int ii = i + (dir == 0 ? q : 0), jj = j + (dir == 1 ? q : 0), kk = k + (dir == 2 ? q : 0);
-    ii = theta_source(ii, d.nx, false);
-    jj = theta_source(jj, d.ny, C.wall_y != 0);
-    kk = theta_source(kk, d.nz, false);
+    ii = theta_source(ii, d.nx, C.bc[0], C.bc[1]);
+    jj = theta_source(jj, d.ny, C.bc[2], C.bc[3]);
+    kk = theta_source(kk, d.nz, kBcPeriodic, kBcPeriodic);
     double dv;
     t64 = fmax(t64, theta_node<L, double>(d, C, B, ii, jj, kk, dv));
   }

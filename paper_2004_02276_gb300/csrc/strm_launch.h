@@ -26,6 +26,7 @@ void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w
                   cudaStream_t s);
 void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixed, cudaStream_t s);
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+void launch_recycle(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);

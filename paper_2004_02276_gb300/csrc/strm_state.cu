@@ -27,9 +27,12 @@ __global__ void __launch_bounds__(256) k_ghost_prims(Dims d, Consts C, Bufs B, l
   body_ghost_prims(d, C, B, nthreads, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) k_ghost_prims_mixed(Dims d, Consts C, Bufs B, long long nthreads) {
-  body_ghost_prims_mixed(d, C, B, nthreads, blockIdx.x);
+__global__ void k_recycle_mean(Dims d, Consts C, Bufs B) {
+  __shared__ double sh[32];
+  body_recycle_mean(d, C, B, blockIdx.x, sh);
 }
+
+__global__ void k_recycle_scale(Dims d, Consts C, Bufs B) { body_recycle_scale(d, C, B); }
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_ghost_scalars(Dims d, Consts C, Bufs B, long long nthreads) {
@@ -146,10 +149,12 @@ static long long ghost_threads(const Dims& d) {
 
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
   long long n = ghost_threads(d);
-  if (C.mixed)
-    k_ghost_prims_mixed<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
-  else
-    k_ghost_prims<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+  k_ghost_prims<<<blocks_for(n, 256), 256, 0, s>>>(d, C, B, n);
+}
+
+void launch_recycle(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
+  k_recycle_mean<<<d.ny, 256, 0, s>>>(d, C, B);
+  k_recycle_scale<<<1, 1, 0, s>>>(d, C, B);
 }
 
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {

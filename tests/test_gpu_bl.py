@@ -1,0 +1,120 @@
+"""Boundary-layer and shock/boundary-layer workloads on the GPU against the FP64 oracle:
+recycling inflow, characteristic outflow and top, isothermal wall on a one-sided tanh grid,
+and the oblique shock imposed at the top (Sections 3.2, 3.3)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2004_02276_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel_max(a, b):
+    return np.array([np.abs(a[m] - b[m]).max() / max(np.abs(b[m]).max(), 1e-300) for m in range(5)])
+
+
+def rel_l2(a, b):
+    return np.array([np.linalg.norm(a[m] - b[m]) / max(np.linalg.norm(b[m]), 1e-300) for m in range(5)])
+
+
+BL = inputs.bl_case("bl-48x40x12", 48, 40, 12, 7.0, 6.0, 1.5)
+SBLI = inputs.bl_case("sbli-64x40x12", 64, 40, 12, 12.0, 6.0, 1.5, shock=True, noise=0.003)
+OPEN = inputs.bl_case("open-40x24x10", 40, 24, 10, 6.0, 6.0, 1.5, bc_xmin="char", bc_ymin="char",
+                      weno_mode="all")
+
+
+@pytest.mark.parametrize("case", [BL, SBLI, OPEN], ids=lambda c: c.name)
+def test_rhs_and_flags_match_oracle(case):
+    w0 = inputs.bl_state(case, seed=4)
+    cfg = O.make_cfg(case)
+    ref = O.rhs(cfg, w0)
+    _, _, fx_o, fy_o, fz_o = O.sensor(cfg, w0)
+    s = binding.Solver(case)
+    w = torch.from_numpy(w0).cuda()
+    r = s.compute_rhs(w).cpu().numpy()
+    _, _, fx, fy, fz = (t.cpu().numpy() for t in s.sensor(w))
+    s.close()
+    assert np.array_equal(fx, fx_o) and np.array_equal(fy, fy_o) and np.array_equal(fz, fz_o)
+    err = rel_max(r, ref)
+    assert err.max() <= TOL, err
+
+
+@pytest.mark.parametrize("case", [BL, SBLI], ids=lambda c: c.name)
+def test_ten_steps_match_oracle(case):
+    w0 = inputs.bl_state(case, seed=5)
+    wo, to, _ = O.advance(O.make_cfg(case), w0, 10, cfl=case.cfl)
+    s = binding.Solver(case)
+    w = torch.from_numpy(w0).cuda()
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 10, cfl=case.cfl)
+    t, _ = s.time()
+    wg = w.cpu().numpy()
+    s.close()
+    err = rel_l2(wg, wo)
+    assert err.max() <= TOL, err
+    assert abs(t - to) <= 1e-13 * to
+
+
+def test_mixed_precision_boundary_layer():
+    case = SBLI.replace(precision="mixed")
+    w0 = inputs.bl_state(case, seed=5)
+    wo, _, _ = O.advance(O.make_cfg(case), w0, 10, cfl=case.cfl)
+    s = binding.Solver(case)
+    w = torch.from_numpy(w0).cuda()
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 10, cfl=case.cfl)
+    wg = w.cpu().numpy()
+    s.close()
+    err = rel_l2(wg, wo)
+    assert np.isfinite(wg).all()
+    assert max(err[0], err[1], err[4]) <= 1e-4, err
+    print("mixed SBLI relative L2 error after 10 steps:", err)
+
+
+@pytest.mark.slow
+def test_c3_full_size_rhs_matches_oracle():
+    """The 1024x256x256 boundary layer: the full right-hand side, every element, and five GPU
+    steps that stay finite."""
+    case = inputs.C3
+    w0 = inputs.bl_state(case, seed=0)
+    s = binding.Solver(case)
+    w = torch.from_numpy(w0).cuda()
+    r = s.compute_rhs(w).cpu().numpy()
+    ref = O.rhs(O.make_cfg(case), w0)
+    err = rel_max(r, ref)
+    del ref, r
+    assert err.max() <= TOL, err
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 5, cfl=case.cfl)
+    assert torch.isfinite(w).all()
+    s.close()
+
+
+@pytest.mark.slow
+def test_c4_full_size_steps():
+    """The 2048x384x256 shock/boundary-layer interaction on the GPU: finite after 5 steps with
+    the shock entering through the top, WENO on a minority of the faces."""
+    case = inputs.C4
+    s = binding.Solver(case)
+    w = torch.from_numpy(inputs.bl_state(case, seed=0)).cuda()
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 5, cfl=case.cfl)
+    s.compute_rhs(w)
+    counts = s.weno_counts()
+    frac = sum(counts) / (3.0 * case.npts)
+    print("C4 WENO face fraction after 5 steps:", frac)
+    assert torch.isfinite(w).all()
+    assert 0.0 < frac < 0.5
+    s.close()
