@@ -569,26 +569,30 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
 // ------------------------------------------------------------------------------ WENO5
 
 // Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2} = (f0..f4), written in first differences
-// a..d of the stencil: value = f2 + num/den with
-//   6 q_0 = 6 f2 + 5b - 2a,  6 q_1 = 6 f2 + b + 2c,  6 q_2 = 6 f2 + 4c - d,
+// a..d of the stencil: value = f2 + num/(6 den) with the candidates
+//   6 p_0 = 6 f2 + 5b - 2a,  6 p_1 = 6 f2 + b + 2c,  6 p_2 = 6 f2 + 4c - d,
 // smoothness indicators scaled by 4 (4 beta = 13/3 t^2 + t'^2, so eps4 = 4 eps keeps the
-// weights), and weights d_k/(eps+beta_k)^2 multiplied through by 10 (eps+beta_0..2)^2 products.
+// weights), and the weights d_k/(eps+beta_k)^2 multiplied through by 10 (eps+beta_0..2)^2
+// products. The caller folds the 1/6 into its own scaling.
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
                                          double eps4, double& num, double& den) {
   double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
   double t0 = b - a, t1 = fma(3.0, b, -a);
   double t2 = c - b, t3 = b + c;
   double t4 = d - c, t5 = fma(-3.0, c, d);
-  double q0 = eps4 + fma((13.0 / 3.0) * t0, t0, t1 * t1);
-  double q1 = eps4 + fma((13.0 / 3.0) * t2, t2, t3 * t3);
-  double q2 = eps4 + fma((13.0 / 3.0) * t4, t4, t5 * t5);
-  q0 *= q0;
-  q1 *= q1;
-  q2 *= q2;
-  double w0 = q1 * q2, w1 = 6.0 * (q0 * q2), w2 = 3.0 * (q0 * q1);
-  double e0 = fma(-2.0, a, 5.0 * b), e1 = fma(2.0, c, b), e2 = fma(4.0, c, -d);
-  num = fma(w2, e2, fma(w1, e1, w0 * e0));
-  den = 6.0 * (w0 + w1 + w2);
+  // q_k = 4 beta_k + eps4
+  double q0 = fma(t1, t1, fma((13.0 / 3.0) * t0, t0, eps4));
+  double q1 = fma(t3, t3, fma((13.0 / 3.0) * t2, t2, eps4));
+  double q2 = fma(t5, t5, fma((13.0 / 3.0) * t4, t4, eps4));
+  double Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
+  // weights d_k / Q_k times Q0 Q1 Q2: (w0, 6 v1, 3 v2); the 6 and 3 ride on the candidates
+  double w0 = Q1 * Q2, v1 = Q0 * Q2, v2 = Q0 * Q1;
+  double c12 = 12.0 * c;
+  double e0 = fma(2.0, t1, -b);  // 5b - 2a: 6 (candidate 0 - f2)
+  double e1 = fma(6.0, b, c12);  // 6 (b + 2c): 36 (candidate 1 - f2)
+  double e2 = fma(-3.0, d, c12); // 3 (4c - d): 18 (candidate 2 - f2)
+  num = fma(v2, e2, fma(v1, e1, w0 * e0));
+  den = fma(3.0, v2, fma(6.0, v1, w0));
 }
 
 // Characteristic Lax-Friedrichs flux-vector splitting with WENO5 (Section 2.1) at the face
@@ -601,7 +605,17 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
 // The split values of field k are carried scaled by s_k (4 for the acoustic fields, 2 for the
 // others) to drop the 1/2 and 1/4 factors of the projection and of the splitting; WENO5 is then
 // run with eps scaled by s_k^2, which leaves its weights unchanged, and the result is divided
-// by s_k. All scalings are powers of two.
+// by s_k. The acoustic difference row is formed as c B (no division by c per node) and the 1/c
+// enters the sums A +- B as an FMA.
+//
+// FP64 is the binding pipe on this path, so the maxima of the non-negative LF speeds are taken
+// on their IEEE bit patterns (monotone in the value for non-negative doubles) on the integer
+// pipe.
+__device__ __forceinline__ long long max_bits(long long m, double x) {
+  long long b = __double_as_longlong(fabs(x));
+  return b > m ? b : m;
+}
+
 template <int DIR>
 __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long long n, long long st,
                                           double* f) {
@@ -623,19 +637,21 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
   double ic = rsqrt(c2a);
   double ca = c2a * ic;
   double b1 = C.gm1 * ic * ic;
-  double b2 = 0.5 * q2 * b1;
+  double b2 = (0.5 * q2) * b1;
   double un_a = ua[DIR];
 
   // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
-  double lam0 = 0.0, lam1 = 0.0, lam4 = 0.0;
+  long long m0 = 0, m1 = 0, m4 = 0;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
     double un = __ldg(un_p + nn), cs = __ldg(P.c + nn);
-    lam0 = fmax(lam0, fabs(un - cs));
-    lam1 = fmax(lam1, fabs(un));
-    lam4 = fmax(lam4, fabs(un + cs));
+    m0 = max_bits(m0, un - cs);
+    m1 = max_bits(m1, un);
+    m4 = max_bits(m4, un + cs);
   }
+  const double lam0 = __longlong_as_double(m0), lam1 = __longlong_as_double(m1),
+               lam4 = __longlong_as_double(m4);
 
   // scaled split characteristic values s_k (L F +- lam_k L w)/2 at the stencil nodes
   double gp[5][6], gm[5][6];
@@ -648,14 +664,14 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     double un = uu[DIR];
     double run = rho * un;
     double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
-    double K = b2 + b1 * (H - udot);
+    double K = fma(b1, H - udot, b2);
     double b1p = b1 * p;
-    double Aw = rho * K - b1p;          // acoustic rows: (l0 + l4) w = A_w, (l0 - l4) w = B_w
-    double Af = run * K - b1p * un_a;
+    double Aw = fma(rho, K, -b1p);  // acoustic rows: (l0 + l4) w = A_w, c (l0 - l4) w = cB_w
+    double Af = fma(run, K, -b1p * un_a);
     double du = un_a - un;
-    double Bw = (rho * ic) * du;
-    double Bf = (run * du - p) * ic;
-    double Sw = Aw + Bw, Sf = Af + Bf, Dw = Aw - Bw, Df = Af - Bf;
+    double cBw = rho * du;
+    double cBf = fma(run, du, -p);
+    double Sw = fma(ic, cBw, Aw), Sf = fma(ic, cBf, Af), Dw = fma(-ic, cBw, Aw), Df = fma(-ic, cBf, Af);
     gp[0][q] = fma(lam0, Sw, Sf);
     gm[0][q] = fma(-lam0, Sw, Sf);
     gp[4][q] = fma(lam4, Dw, Df);
@@ -673,23 +689,24 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const bool acoustic = (k == 0 || k == 4);
-    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;  // 4 s_k^2 eps
+    const double s = acoustic ? 0.25 : 0.5;
+    // 4 s_k^2 eps
+    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;
     double np_, dp_, nm_, dm_;
     weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
     weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
-    double v = (gp[k][2] + gm[k][3]) + fma(np_, dm_, nm_ * dp_) / (dp_ * dm_);
-    g[k] = (acoustic ? 0.25 : 0.5) * v;
+    g[k] = fma(s * (1.0 / 6.0), fma(np_, dm_, nm_ * dp_) / (dp_ * dm_), s * (gp[k][2] + gm[k][3]));
   }
   // back to conserved variables with the right eigenvectors
-  double gs = g[0] + g[1] + g[4];
+  double s04 = g[0] + g[4], cd40 = ca * (g[4] - g[0]);
+  double gs = s04 + g[1];
   f[0] = gs;
 #pragma unroll
   for (int dd = 0; dd < 3; ++dd) f[1 + dd] = gs * ua[dd];
-  f[1 + DIR] += ca * (g[4] - g[0]);
+  f[1 + DIR] += cd40;
   f[1 + T1] += g[2];
   f[1 + T2] += g[3];
-  f[4] = Ha * (g[0] + g[4]) + un_a * ca * (g[4] - g[0]) + 0.5 * q2 * g[1] + ua[T1] * g[2] +
-         ua[T2] * g[3];
+  f[4] = Ha * s04 + un_a * cd40 + 0.5 * q2 * g[1] + ua[T1] * g[2] + ua[T2] * g[3];
 }
 
 // FP32 WENO5 (mixed precision), same first-difference form; the nonlinear weights are formed
@@ -761,9 +778,9 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     double Aw = rho * K - b1p;
     double Af = run * K - b1p * un_a;
     double du = un_a - un;
-    double Bw = (rho * ic) * du;
-    double Bf = (run * du - p) * ic;
-    float Sw = (float)(Aw + Bw), Sf = (float)(Af + Bf), Dw = (float)(Aw - Bw), Df = (float)(Af - Bf);
+    double cBw = rho * du, cBf = fma(run, du, -p);
+    float Sw = (float)fma(ic, cBw, Aw), Sf = (float)fma(ic, cBf, Af), Dw = (float)fma(-ic, cBw, Aw),
+          Df = (float)fma(-ic, cBf, Af);
     float Awf = (float)Aw, Aff = (float)Af;
     float rhof = __ldg(F.rho + nn), unf = __ldg(velf[DIR] + nn);
     float runf = rhof * unf;
