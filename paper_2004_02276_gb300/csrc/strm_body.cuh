@@ -30,7 +30,8 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
     node_ijk(d, q, i, j, k);
     const Nodes<double>& P = B.n64;
     double rho = w[q];
-    double ir = 1.0 / rho;
+    double rs = rsqrt(rho);  // 1/rho and sqrt(rho) from one reciprocal square root
+    double ir = rs * rs;
     double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
     double E = w[4 * d.N + q] * ir;
     double T = (E - 0.5 * (u * u + v * v + ww * ww)) * C.inv_cv;
@@ -46,7 +47,7 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
     P.H[n] = E + p * ir;
     P.c[n] = c;
     P.mu[n] = viscosity(C.k64, C.visc_law, T);
-    P.srho[n] = sqrt(rho);
+    P.srho[n] = rho * rs;
     if (want_cfl)
       spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
   }
@@ -70,7 +71,8 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     const Nodes<double>& P = B.n64;
     const Nodes<float>& F = B.n32;
     double rho = w[q];
-    double ir = 1.0 / rho;
+    double rs = rsqrt(rho);
+    double ir = rs * rs;
     double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
     double E = w[4 * d.N + q] * ir;
     double T = (E - 0.5 * (u * u + v * v + ww * ww)) * C.inv_cv;
@@ -84,7 +86,7 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     P.T[n] = T;
     P.p[n] = p;
     P.H[n] = H;
-    P.srho[n] = sqrt(rho);
+    P.srho[n] = rho * rs;
     float rf = (float)rho, pf = (float)p, Tf = (float)T;
     float cf = sqrtf(C.k32.gamma * pf / rf);
     F.rho[n] = rf;
@@ -612,8 +614,37 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
 // on their IEEE bit patterns (monotone in the value for non-negative doubles) on the integer
 // pipe.
 __device__ __forceinline__ long long max_bits(long long m, double x) {
-  long long b = __double_as_longlong(fabs(x));
+  long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;  // |x|, sign bit cleared
   return b > m ? b : m;
+}
+
+// Reciprocals of five positive doubles with one division (prefix-product method): each value
+// is first brought to [1, 2) by replacing its exponent field (integer operations), the five
+// mantissas are inverted together, and each reciprocal gets its exponent back by an integer
+// subtraction on its exponent field. Valid for positive normal inputs below 2^1022 (the
+// reciprocals stay normal); a NaN input yields a finite value here, so callers
+// multiply by a numerator that carries the NaN.
+__device__ __forceinline__ void recip5(const double* y, double* r) {
+  double m[5];
+  long long e[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long b = __double_as_longlong(y[k]);
+    e[k] = ((b >> 52) & 0x7ff) - 1023;
+    m[k] = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  }
+  double p1 = m[0] * m[1], p2 = p1 * m[2], p3 = p2 * m[3], p4 = p3 * m[4];
+  double inv = 1.0 / p4;
+  double i4 = inv * p3;
+  inv *= m[4];
+  double i3 = inv * p2;
+  inv *= m[3];
+  double i2 = inv * p1;
+  inv *= m[2];
+  double i1 = inv * m[0], i0 = inv * m[1];
+  const double im[5] = {i0, i1, i2, i3, i4};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r[k] = __longlong_as_double(__double_as_longlong(im[k]) - (e[k] << 52));
 }
 
 template <int DIR>
@@ -663,8 +694,8 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
     double un = uu[DIR];
     double run = rho * un;
-    double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
-    double K = fma(b1, H - udot, b2);
+    double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
+    double K = fma(b1, hu, b2);
     double b1p = b1 * p;
     double Aw = fma(rho, K, -b1p);  // acoustic rows: (l0 + l4) w = A_w, c (l0 - l4) w = cB_w
     double Af = fma(run, K, -b1p * un_a);
@@ -685,17 +716,25 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     gp[3][q] = d2 * r1;
     gm[3][q] = d2 * r2;
   }
-  double g[5];
+  // per field: the + and - reconstructions over one common denominator, the five
+  // denominators inverted together
+  double num[5], den[5], rden[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const bool acoustic = (k == 0 || k == 4);
-    const double s = acoustic ? 0.25 : 0.5;
-    // 4 s_k^2 eps
-    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;
+    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;  // 4 s_k^2 eps
     double np_, dp_, nm_, dm_;
     weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
     weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
-    g[k] = fma(s * (1.0 / 6.0), fma(np_, dm_, nm_ * dp_) / (dp_ * dm_), s * (gp[k][2] + gm[k][3]));
+    num[k] = fma(np_, dm_, nm_ * dp_);
+    den[k] = dp_ * dm_;
+  }
+  recip5(den, rden);
+  double g[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const double s = (k == 0 || k == 4) ? 0.25 : 0.5;
+    g[k] = fma(s * (1.0 / 6.0), num[k] * rden[k], s * (gp[k][2] + gm[k][3]));
   }
   // back to conserved variables with the right eigenvectors
   double s04 = g[0] + g[4], cd40 = ca * (g[4] - g[0]);
@@ -944,22 +983,23 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
   ddiv[2] = dsum<L>(P.div, n, sz, K.a) * K.inv_dz;
   const R mu = __ldg(P.mu + n);
   const R div = du[0][0] + du[1][1] + du[2][2];
+  const R tdiv = R(2.0 / 3.0) * div;
+  // symmetric strain sums S_ab = d_b u_a + d_a u_b
+  const R S00 = R(2) * du[0][0], S11 = R(2) * du[1][1], S22 = R(2) * du[2][2];
+  const R S01 = du[0][1] + du[1][0], S02 = du[0][2] + du[2][0], S12 = du[1][2] + du[2][1];
+  R sm[3];
+  sm[0] = fma(dmu[0], S00, fma(dmu[1], S01, dmu[2] * S02));
+  sm[1] = fma(dmu[0], S01, fma(dmu[1], S11, dmu[2] * S12));
+  sm[2] = fma(dmu[0], S02, fma(dmu[1], S12, dmu[2] * S22));
   R Vm[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R s = dmu[0] * (du[a][0] + du[0][a]) + dmu[1] * (du[a][1] + du[1][a]) +
-          dmu[2] * (du[a][2] + du[2][a]);
-    Vm[a] = mu * lap[a] + mu * ddiv[a] * R(1.0 / 3.0) + s - R(2.0 / 3.0) * div * dmu[a];
-  }
+  for (int a = 0; a < 3; ++a) Vm[a] = fma(mu, fma(ddiv[a], R(1.0 / 3.0), lap[a]), fma(-tdiv, dmu[a], sm[a]));
   const R uu[3] = {__ldg(P.u + n), __ldg(P.v + n), __ldg(P.w + n)};
-  R work = uu[0] * Vm[0] + uu[1] * Vm[1] + uu[2] * Vm[2];
-  // sigma_ij d_j u_i = mu [ sum_ij (d_j u_i + d_i u_j) d_j u_i - 2/3 div^2 ]
-  R diss = R(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) diss += (du[a][b] + du[b][a]) * du[a][b];
-  diss = mu * (diss - R(2.0 / 3.0) * div * div);
+  R work = fma(uu[0], Vm[0], fma(uu[1], Vm[1], uu[2] * Vm[2]));
+  // sigma_ij d_j u_i = mu [ sum_ab S_ab d_b u_a - 2/3 div^2 ], and by symmetry
+  // sum_ab S_ab d_b u_a = sum_a S_aa d_a u_a + sum_{a<b} S_ab^2
+  R diss = fma(S00, du[0][0], fma(S11, du[1][1], fma(S22, du[2][2], fma(S01, S01, fma(S02, S02, S12 * S12)))));
+  diss = mu * fma(-tdiv, div, diss);
   R heat = K.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
   V[0] = R(0);
   V[1] = Vm[0];
