@@ -33,8 +33,8 @@ UNIT = "grid-pt RK-stage updates/s"
 CASE = inputs.C2
 
 # Algorithmic FP64 flops per unit of work of each kernel (add/sub/mul = 1, FMA = 2, division and
-# square root = 1), counted from the operations each kernel's formulation performs; the counts are
-# derived line by line in the design doc. Units: faces for the face kernels, interior nodes otherwise.
+# square root = 1), counted from the operations each kernel's formulation performs. Units: faces
+# for the face kernels, interior nodes otherwise.
 FLOPS_PER_UNIT = {
     "weno_x": 900, "weno_y": 900, "weno_z": 900,
     "faces_x": 151, "faces_y": 151, "faces_z": 151,
@@ -44,9 +44,11 @@ FLOPS_PER_UNIT = {
 # (Roe state and eigen-scalars 30, acoustic-row scalars 25 per stencil node); the FP32 flux
 # arithmetic (~700 flops per face) runs on the FP32 pipes at 62x the FP64 rate.
 FLOPS_PER_UNIT_MIXED = {"weno_x": 180, "weno_y": 180, "weno_z": 180}
-# DRAM bytes (read + write) per unit from one ncu capture of each kernel on the 192x144x96 channel
-# (profiles/k_weno_channel-192x144x96_fp64.md), scaled to a launch by the units it processes.
-DRAM_BYTES_PER_UNIT = {"weno_x": 107.2, "weno_y": 212.8, "weno_z": 299.4}
+# DRAM bytes (read + write) per WENO face from one ncu capture of the current kernels on the
+# 192x144x96 channel (dram__bytes_read.sum + dram__bytes_write.sum of the launch over its WENO
+# faces), scaled to a launch by the faces it processes.
+DRAM_BYTES_PER_UNIT = {"weno_x": 107.3, "weno_y": 210.6, "weno_z": 297.4}
+DRAM_BYTES_PER_UNIT_MIXED = {"weno_x": 103.9, "weno_y": 164.9, "weno_z": 279.1}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 (the profiling recipe's unit table); a probe of
 # dependent-chain-free DFMA on this pool measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 1.25
@@ -281,7 +283,7 @@ def run_ours(args, world, rank, local):
     if not args.no_mixed:
         # mixed precision: FP32 flux/sensor/WENO/viscous arithmetic, FP64 state and projection
         mcase = case.replace(precision="mixed")
-        mm, msolver, wm, _ = measure(mcase, args, world, local, FLOPS_PER_UNIT_MIXED, {})
+        mm, msolver, wm, _ = measure(mcase, args, world, local, FLOPS_PER_UNIT_MIXED, DRAM_BYTES_PER_UNIT_MIXED)
         wmix = wm.cpu().numpy()
         msolver.close()
         steps_done = args.warmup + 2 * args.steps
