@@ -37,7 +37,7 @@ class OrcCfg(ctypes.Structure):
 
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
 BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3}
-Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2}
+Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2, "erf": 3, "sinh1": 4}
 VISC_LAWS = {"power": 0, "sutherland": 1}
 
 

@@ -92,8 +92,11 @@ static int central_coeffs(int L, double* a, double* b) {
 }
 
 /* Wall-normal mapping y(eta), eta in [0,1], nodes at eta_j = (j+1/2)/ny (staggered: the
- * walls eta = 0, 1 are interfaces). Tanh clustering toward both walls, y in [-ly/2, ly/2]; or
- * toward the wall y = 0 only, y = ly (1 - tanh(beta (1-eta)) / tanh beta) in [0, ly]. */
+ * walls eta = 0, 1 are interfaces). Clustering toward both walls, y in [-ly/2, ly/2]:
+ * tanh, y = (ly/2) tanh(beta (2 eta - 1)) / tanh beta, or the error function of Section 3.1,
+ * y = (ly/2) erf(beta (2 eta - 1)) / erf beta. Toward the wall y = 0 only, y in [0, ly]:
+ * y = ly (1 - tanh(beta (1-eta)) / tanh beta), or the hyperbolic sine of Section 3.2,
+ * y = ly sinh(beta eta) / sinh beta. The derivatives are the analytic ones. */
 void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
   for (int j = 0; j < c->ny; ++j) {
     double eta = (j + 0.5) / c->ny;
@@ -113,6 +116,18 @@ void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
       y[j] = A * th;
       yeta[j] = 2.0 * c->beta * A * sech2;
       yetaeta[j] = -8.0 * c->beta * c->beta * A * sech2 * th;
+    } else if (c->y_map == ORC_MAP_ERF) {
+      double s = 2.0 * eta - 1.0;
+      double E = erf(c->beta);
+      y[j] = 0.5 * c->ly * erf(c->beta * s) / E;
+      /* d/deta erf(beta s) = (2/sqrt(pi)) exp(-beta^2 s^2) * 2 beta */
+      yeta[j] = 0.5 * c->ly / E * (2.0 / sqrt(acos(-1.0))) * exp(-c->beta * c->beta * s * s) * 2.0 * c->beta;
+      yetaeta[j] = yeta[j] * (-2.0 * c->beta * c->beta * s) * 2.0;
+    } else if (c->y_map == ORC_MAP_SINH_ONESIDED) {
+      double S = sinh(c->beta);
+      y[j] = c->ly * sinh(c->beta * eta) / S;
+      yeta[j] = c->ly * c->beta * cosh(c->beta * eta) / S;
+      yetaeta[j] = c->ly * c->beta * c->beta * sinh(c->beta * eta) / S;
     } else {
       y[j] = c->ly * (eta - 0.5);
       yeta[j] = c->ly;
@@ -123,7 +138,7 @@ void orc_metrics(const orc_cfg* c, double* y, double* yeta, double* yetaeta) {
 
 /* Height of the wall-side boundary eta = 0 in the mapping. */
 static double map_y0(const orc_cfg* c) {
-  return c->y_map == ORC_MAP_TANH_ONESIDED ? 0.0 : -0.5 * c->ly;
+  return (c->y_map == ORC_MAP_TANH_ONESIDED || c->y_map == ORC_MAP_SINH_ONESIDED) ? 0.0 : -0.5 * c->ly;
 }
 
 static int grid_init(grid_t* g, const orc_cfg* c) {

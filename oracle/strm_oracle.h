@@ -22,7 +22,8 @@
 extern "C" {
 #endif
 
-enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1, ORC_MAP_TANH_ONESIDED = 2 };
+enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1, ORC_MAP_TANH_ONESIDED = 2, ORC_MAP_ERF = 3,
+       ORC_MAP_SINH_ONESIDED = 4 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_CHAR = 2, ORC_BC_RECYCLE = 3 };
 enum { ORC_WENO_OFF = 0, ORC_WENO_SENSOR = 1, ORC_WENO_ALL = 2 };
 enum { ORC_VISC_POWER = 0, ORC_VISC_SUTHERLAND = 1 };
@@ -31,8 +32,9 @@ typedef struct {
   /* grid: nx*ny*nz interior nodes; y nodes at eta_j = (j+1/2)/ny */
   int nx, ny, nz;
   double lx, ly, lz;
-  int y_map;            /* ORC_MAP_UNIFORM, ORC_MAP_TANH (both walls) or _TANH_ONESIDED (wall at y=0) */
-  double beta;          /* tanh stretching parameter */
+  int y_map;            /* ORC_MAP_UNIFORM, ORC_MAP_TANH or ORC_MAP_ERF (both walls), or
+                           ORC_MAP_TANH_ONESIDED or ORC_MAP_SINH_ONESIDED (wall at y = 0) */
+  double beta;          /* stretching parameter of the map */
   /* face kinds (z is periodic): x faces PERIODIC, RECYCLE (x-min only) or CHAR; y faces
    * PERIODIC, WALL or CHAR */
   int bc_xmin, bc_xmax, bc_ymin, bc_ymax;

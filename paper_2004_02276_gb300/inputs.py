@@ -56,7 +56,7 @@ class Case:
     ly: float = 2.0
     lz: float = math.pi
     beta: float = 1.5            # tanh wall clustering; 0 gives a uniform y grid
-    y_map: str = "tanh"          # "tanh": clustered at both walls; "tanh1": at y = 0 only
+    y_map: str = "tanh"          # "tanh", "erf": clustered at both walls; "tanh1", "sinh1": at y = 0 only
     y_wall: bool = True          # isothermal staggered walls in y (else periodic)
     bc_xmin: str = None          # face kinds ("periodic", "wall", "char", "recycle"); None:
     bc_xmax: str = None          #   x periodic, y walls or periodic per y_wall
@@ -121,6 +121,13 @@ class Case:
 # supersonic boundary layer and C4 the shock/boundary-layer interaction.
 C1 = Case(name="channel-64x48x32", nx=64, ny=48, nz=32, reynolds=3000.0, steps=20)
 C2 = Case(name="channel-256x192x128", nx=256, ny=192, nz=128, reynolds=7000.0, steps=200)
+# The paper's own channel settings (Section 3.1) on the 64x48x32 grid: fourth-order central and
+# viscous stencils (L = 2), Sutherland's law (T_w = 288.15 K), error-function clustering with
+# beta = 1.4 (largest/smallest wall-normal spacing exp(beta^2) = 7.1, as 5.7/0.8 wall units in
+# the paper), M_b = 1.5, Re_b = 14725 on a 6 pi x 2 x 2 pi box.
+PAPER_CHANNEL = Case(name="paper-channel-64x48x32", nx=64, ny=48, nz=32, lx=6 * math.pi,
+                     lz=2 * math.pi, reynolds=14725.0, L=2, visc_law="sutherland", y_map="erf",
+                     beta=1.4, steps=20)
 
 
 def bl_case(name, nx, ny, nz, lx, ly, lz, shock=False, **kw) -> Case:
@@ -144,14 +151,24 @@ C4 = bl_case("sbli-2048x384x256", 2048, 384, 256, 50.0, 12.0, 5.33, shock=True, 
 
 def node_y(case: Case) -> np.ndarray:
     """Wall-normal node positions used to lay out the initial profile (nodes at the cell
-    centres of a tanh-clustered grid between the walls y = -ly/2 and y = ly/2, or of a grid
-    clustered at the wall y = 0 up to y = ly for "tanh1")."""
+    centres of a grid clustered toward both walls y = -ly/2 and y = ly/2, "tanh" or "erf", or
+    toward the wall y = 0 up to y = ly, "tanh1" or "sinh1")."""
     eta = (np.arange(case.ny) + 0.5) / case.ny
-    if case.beta and case.beta > 0 and case.y_map == "tanh1":
-        return case.ly * (1.0 - np.tanh(case.beta * (1.0 - eta)) / math.tanh(case.beta))
-    if case.beta and case.beta > 0:
-        return 0.5 * case.ly * np.tanh(case.beta * (2.0 * eta - 1.0)) / math.tanh(case.beta)
-    return case.ly * (eta - 0.5)
+    b = case.beta
+    if not (b and b > 0):
+        return case.ly * (eta - 0.5)
+    if case.y_map == "tanh1":
+        return case.ly * (1.0 - np.tanh(b * (1.0 - eta)) / math.tanh(b))
+    if case.y_map == "sinh1":
+        return case.ly * np.sinh(b * eta) / math.sinh(b)
+    if case.y_map == "erf":
+        return 0.5 * case.ly * np.array([math.erf(b * (2.0 * e - 1.0)) for e in eta]) / math.erf(b)
+    return 0.5 * case.ly * np.tanh(b * (2.0 * eta - 1.0)) / math.tanh(b)
+
+
+def one_sided(case: Case) -> bool:
+    """True for maps with a single wall at y = 0."""
+    return case.y_map in ("tanh1", "sinh1")
 
 
 def channel_state(case: Case, seed: int | None = None) -> np.ndarray:
@@ -188,7 +205,7 @@ def bl_state(case: Case, seed: int | None = None) -> np.ndarray:
     seed = case.seed if seed is None else seed
     nz, ny, nx = case.nz, case.ny, case.nx
     yy = node_y(case)
-    h = yy - (0.0 if case.y_map == "tanh1" else -0.5 * case.ly)
+    h = yy - (0.0 if one_sided(case) else -0.5 * case.ly)
     ub = np.minimum(np.maximum(h / case.delta_in, 0.0) ** (1.0 / 7.0), 1.0)
     tr = 1.0 + case.prandtl ** (1.0 / 3.0) * 0.5 * (case.gamma - 1.0) * case.mach ** 2
     T1 = case.t_wall + (tr - case.t_wall) * ub + (1.0 - tr) * ub * ub

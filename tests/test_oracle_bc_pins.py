@@ -210,3 +210,56 @@ def test_boundary_layer_step_is_finite_and_bounded(orc):
         st, dt = orc.rk_step(cfg, st)
     assert np.isfinite(st).all() and dt > 0
     assert abs(st[0].sum() / m0 - 1.0) < 0.05  # open domain: mass changes only through the faces
+
+
+# ----------------------------------------------------------------------- wall-normal maps
+
+MAPS = ["tanh", "erf", "tanh1", "sinh1"]
+
+
+def map_case(y_map, ny=400, beta=2.0):
+    return inputs.Case(nx=4, ny=ny, nz=4, ly=2.0, beta=beta, y_map=y_map)
+
+
+@pytest.mark.parametrize("y_map", MAPS)
+def test_map_metrics_consistent(orc, y_map):
+    """The analytic y_eta, y_etaeta agree with finite differences of y, the spacing integrates
+    to L_y, and the map is monotone (Sections 3.1, 3.2 name the maps without formulas)."""
+    c = map_case(y_map)
+    y, ye, yee = orc.metrics(orc.make_cfg(c))
+    deta = 1.0 / c.ny
+    assert np.all(np.diff(y) > 0) and np.all(ye > 0)
+    def d4(f):  # fourth-order central difference
+        return (-f[4:] + 8 * f[3:-1] - 8 * f[1:-3] + f[:-4]) / (12 * deta)
+    np.testing.assert_allclose(d4(y), ye[2:-2], rtol=1e-7)
+    np.testing.assert_allclose(d4(ye), yee[2:-2], rtol=1e-6, atol=1e-7 * np.abs(yee).max())
+    assert abs(ye.sum() * deta - c.ly) < 1e-4 * c.ly  # midpoint rule, O(deta^2)
+
+
+@pytest.mark.parametrize("y_map", MAPS)
+def test_map_clusters_at_walls(orc, y_map):
+    c = map_case(y_map, ny=64)
+    y, ye, yee = orc.metrics(orc.make_cfg(c))
+    eta0 = 0.5 / c.ny
+    # the wall sits at eta = 0: Taylor from the first node, remainder (eta0^2/2) y_etaeta
+    wall = y[0] - eta0 * ye[0]
+    tol = 1.5 * 0.5 * eta0 ** 2 * abs(yee[0]) + 1e-15
+    if y_map in ("tanh", "erf"):
+        assert ye[0] < ye[c.ny // 2] and ye[-1] < ye[c.ny // 2]
+        np.testing.assert_allclose(y, -y[::-1], atol=1e-14)  # odd about the channel centre
+        assert abs(wall + 0.5 * c.ly) < tol
+    else:
+        assert np.all(np.diff(ye) > 0)  # spacing grows away from the wall y = 0
+        assert abs(wall) < tol
+
+
+@pytest.mark.parametrize("y_map", MAPS)
+def test_map_uniform_limit(orc, y_map):
+    """As beta -> 0 every map tends to the uniform one (relative deviation O(beta^2))."""
+    c = map_case(y_map, ny=16, beta=1e-4)
+    y, ye, yee = orc.metrics(orc.make_cfg(c))
+    eta = (np.arange(c.ny) + 0.5) / c.ny
+    y_uniform = c.ly * (eta if y_map in ("tanh1", "sinh1") else eta - 0.5)
+    np.testing.assert_allclose(y, y_uniform, atol=1e-7)
+    np.testing.assert_allclose(ye, c.ly, rtol=1e-7)
+    assert np.abs(yee).max() < 1e-6
