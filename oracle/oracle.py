@@ -70,6 +70,7 @@ def lib():
         _lib.orc_oblique_shock.argtypes = [d, d, d, dp, dp, dp, dp]
         _lib.orc_recycle_scale.argtypes = [cp, dp]
         _lib.orc_recycle_scale.restype = d
+        _lib.orc_stats.argtypes = [cp, dp, i, dp]
     return _lib
 
 
@@ -223,6 +224,22 @@ def oblique_shock(gamma, mach, theta):
 
 def recycle_scale(cfg, w):
     return lib().orc_recycle_scale(ctypes.byref(cfg), _dp(_state(cfg, w)))
+
+
+STAT_NAMES = ["rho", "u", "v", "w", "p", "T", "rho_u", "rho_v", "rho_w", "rho_T", "rho_uu",
+              "rho_vv", "rho_ww", "rho_uv", "rho_uw", "rho_vw", "uu", "vv", "ww", "uv", "pp", "TT",
+              "rhorho", "mu"]
+
+
+def stats(cfg, w, mode=0):
+    """Means of the STAT_NAMES quantities of one state over x and z ([24, ny], mode 0) or over
+    z ([24, ny, nx], mode 1)."""
+    w = _state(cfg, w)
+    shape = (len(STAT_NAMES), cfg.ny) if mode == 0 else (len(STAT_NAMES), cfg.ny, cfg.nx)
+    out = np.empty(shape)
+    if lib().orc_stats(ctypes.byref(cfg), _dp(w), int(mode), _dp(out)):
+        raise ValueError("orc_stats: invalid configuration or mode")
+    return out
 
 
 def weno5(f, eps=1e-6):

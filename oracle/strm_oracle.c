@@ -1066,6 +1066,38 @@ int orc_rk_step(const orc_cfg* c, double* w, double dt, double cfl, double* dt_u
 }
 
 /* Metric-weighted totals: sum over interior nodes of w_m dx (y_eta deta) dz. */
+/* Per-sample statistics: the primitives of each interior node from w (E = cv T + |u|^2/2,
+ * p = rho R T), the 24 products listed in the header, then plain means over the homogeneous
+ * directions (x and z, or z only). */
+int orc_stats(const orc_cfg* c, const double* w, int mode, double* out) {
+  grid_t g;
+  if ((mode != 0 && mode != 1) || grid_init(&g, c)) return -1;
+  ptrdiff_t N = (ptrdiff_t)g.nx * g.ny * g.nz;
+  int nrow = mode == 0 ? g.ny : g.ny * g.nx;
+  for (ptrdiff_t q = 0; q < (ptrdiff_t)ORC_NSTAT * nrow; ++q) out[q] = 0.0;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        ptrdiff_t n = iidx(&g, i, j, k);
+        double rho = w[n];
+        double u = w[N + n] / rho, v = w[2 * N + n] / rho, ww = w[3 * N + n] / rho;
+        double T = (w[4 * N + n] / rho - 0.5 * (u * u + v * v + ww * ww)) / g.cv;
+        double p = rho * c->r_gas * T;
+        double val[ORC_NSTAT] = {rho,          u,          v,           ww,
+                                 p,            T,          rho * u,     rho * v,
+                                 rho * ww,     rho * T,    rho * u * u, rho * v * v,
+                                 rho * ww * ww, rho * u * v, rho * u * ww, rho * v * ww,
+                                 u * u,        v * v,      ww * ww,     u * v,
+                                 p * p,        T * T,      rho * rho,   viscosity(c, T)};
+        int row = mode == 0 ? j : j * g.nx + i;
+        for (int q = 0; q < ORC_NSTAT; ++q) out[(ptrdiff_t)q * nrow + row] += val[q];
+      }
+  double cnt = mode == 0 ? (double)g.nx * g.nz : (double)g.nz;
+  for (ptrdiff_t q = 0; q < (ptrdiff_t)ORC_NSTAT * nrow; ++q) out[q] /= cnt;
+  grid_free(&g);
+  return 0;
+}
+
 int orc_totals(const orc_cfg* c, const double* w, double out[5]) {
   grid_t g;
   if (grid_init(&g, c)) return -1;

@@ -104,6 +104,16 @@ int orc_oblique_shock(double gamma, double mach, double theta, double* beta, dou
 /* Recycling rescale factor s = delta_r / delta_in for the state w (1 if no recycling face). */
 double orc_recycle_scale(const orc_cfg* c, const double* w);
 
+/* Statistics of one state (Section 3: Reynolds and Favre decompositions use averages over the
+ * homogeneous directions and time; this is the spatial part for one sample). Quantities, in
+ * this order (ORC_NSTAT of them):
+ *   rho, u, v, w, p, T, rho u, rho v, rho w, rho T, rho uu, rho vv, rho ww, rho uv, rho uw,
+ *   rho vw, uu, vv, ww, uv, p^2, T^2, rho^2, mu.
+ * mode 0: averages over x and z, out[q][j] (ORC_NSTAT x ny);
+ * mode 1: averages over z, out[q][j][i] (ORC_NSTAT x ny x nx). */
+enum { ORC_NSTAT = 24 };
+int orc_stats(const orc_cfg* c, const double* w, int mode, double* out);
+
 /* Number of ghost layers used by the oracle. */
 int orc_ghosts(void);
 
