@@ -44,7 +44,14 @@ enum {
   STRM_ETIMEOUT = -5    /* reserved for bounded device-side waits */
 };
 
-enum { STRM_MAP_UNIFORM = 0, STRM_MAP_TANH = 1, STRM_MAP_TANH_ONESIDED = 2 };
+/* Wall-normal maps y(eta), eta in [0, 1] (nodes at eta_j = (j + 1/2)/ny):
+ *   UNIFORM          y = ly (eta - 1/2)
+ *   TANH             y = (ly/2) tanh(beta (2 eta - 1)) / tanh(beta)   (both walls)
+ *   TANH_ONESIDED    y = ly (1 - tanh(beta (1 - eta)) / tanh(beta))   (wall at y = 0)
+ *   ERF              y = (ly/2) erf(beta (2 eta - 1)) / erf(beta)     (both walls; Section 3.1)
+ *   SINH_ONESIDED    y = ly sinh(beta eta) / sinh(beta)               (wall at y = 0; Section 3.2) */
+enum { STRM_MAP_UNIFORM = 0, STRM_MAP_TANH = 1, STRM_MAP_TANH_ONESIDED = 2, STRM_MAP_ERF = 3,
+       STRM_MAP_SINH_ONESIDED = 4 };
 enum {
   STRM_BC_PERIODIC = 0,        /* no params */
   STRM_BC_WALL_ISOTHERMAL = 1, /* y faces; no params */
@@ -64,8 +71,8 @@ enum { STRM_PREC_FP64 = 0, STRM_PREC_MIXED = 1 };
 typedef struct {
   int nx, ny, nz;        /* interior nodes, each >= 1 (ny >= 3 with walls) */
   double lx, ly, lz;     /* box lengths */
-  int y_map;             /* STRM_MAP_UNIFORM or STRM_MAP_TANH */
-  double beta;           /* tanh clustering parameter (> 0 for STRM_MAP_TANH) */
+  int y_map;             /* one of STRM_MAP_* */
+  double beta;           /* clustering parameter (> 0 for every map but STRM_MAP_UNIFORM) */
 } strm_grid;
 
 typedef struct {

@@ -20,7 +20,7 @@ _STATUS = {-1: "EINVAL", -2: "ECUDA", -3: "ENONFINITE", -4: "ENOMEM", -5: "ETIME
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
 VISC_LAWS = {"power": 0, "sutherland": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2}
+Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2, "erf": 3, "sinh1": 4}
 FACES = {"xmin": 1, "xmax": 2, "ymin": 3, "ymax": 4}
 BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3, "shock": 4}
 

@@ -58,7 +58,9 @@ struct Layout {
 bool valid_grid(const strm_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->lx > 0 && g->ly > 0 && g->lz > 0 &&
          (g->y_map == STRM_MAP_UNIFORM ||
-          ((g->y_map == STRM_MAP_TANH || g->y_map == STRM_MAP_TANH_ONESIDED) && g->beta > 0));
+          ((g->y_map == STRM_MAP_TANH || g->y_map == STRM_MAP_TANH_ONESIDED || g->y_map == STRM_MAP_ERF ||
+            g->y_map == STRM_MAP_SINH_ONESIDED) &&
+           g->beta > 0));
 }
 
 bool valid_scheme(const strm_scheme* s) {
@@ -287,6 +289,19 @@ void build_metrics(strm_ctx* x) {
       ye = 2.0 * g.beta * A * sech2;
       yee = -8.0 * g.beta * g.beta * A * sech2 * th;
       h = A * th + 0.5 * g.ly;
+    } else if (g.y_map == STRM_MAP_ERF) {
+      // y = (ly/2) erf(beta s) / erf(beta), s = 2 eta - 1: y_eta = (2 ly beta / (sqrt(pi)
+      // erf(beta))) exp(-beta^2 s^2), y_etaeta = -4 beta^2 s y_eta
+      double sv = 2.0 * eta - 1.0, E = std::erf(g.beta);
+      ye = 2.0 * g.ly * g.beta / (std::sqrt(std::acos(-1.0)) * E) * std::exp(-g.beta * g.beta * sv * sv);
+      yee = -4.0 * g.beta * g.beta * sv * ye;
+      h = 0.5 * g.ly * std::erf(g.beta * sv) / E + 0.5 * g.ly;
+    } else if (g.y_map == STRM_MAP_SINH_ONESIDED) {
+      // y = ly sinh(beta eta) / sinh(beta): y_eta = ly beta cosh / sinh(beta), y_etaeta = beta^2 y
+      double S = std::sinh(g.beta);
+      h = g.ly * std::sinh(g.beta * eta) / S;
+      ye = g.ly * g.beta * std::cosh(g.beta * eta) / S;
+      yee = g.beta * g.beta * h;
     } else {
       ye = g.ly;
       yee = 0.0;

@@ -33,9 +33,11 @@ BL = inputs.bl_case("bl-48x40x12", 48, 40, 12, 7.0, 6.0, 1.5)
 SBLI = inputs.bl_case("sbli-64x40x12", 64, 40, 12, 12.0, 6.0, 1.5, shock=True, noise=0.003)
 OPEN = inputs.bl_case("open-40x24x10", 40, 24, 10, 6.0, 6.0, 1.5, bc_xmin="char", bc_ymin="char",
                       weno_mode="all")
+# the paper's boundary-layer clustering (hyperbolic sine, Section 3.2)
+BL_SINH = inputs.bl_case("bl-sinh-48x40x12", 48, 40, 12, 7.0, 6.0, 1.5, y_map="sinh1", beta=4.0)
 
 
-@pytest.mark.parametrize("case", [BL, SBLI, OPEN], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [BL, SBLI, OPEN, BL_SINH], ids=lambda c: c.name)
 def test_rhs_and_flags_match_oracle(case):
     w0 = inputs.bl_state(case, seed=4)
     cfg = O.make_cfg(case)
@@ -51,7 +53,7 @@ def test_rhs_and_flags_match_oracle(case):
     assert err.max() <= TOL, err
 
 
-@pytest.mark.parametrize("case", [BL, SBLI], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [BL, SBLI, BL_SINH], ids=lambda c: c.name)
 def test_ten_steps_match_oracle(case):
     w0 = inputs.bl_state(case, seed=5)
     wo, to, _ = O.advance(O.make_cfg(case), w0, 10, cfl=case.cfl)

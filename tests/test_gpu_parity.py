@@ -53,6 +53,7 @@ CASES = {
                                           forcing=False, visc_law="sutherland"), "random"),
     "line-x-only": (inputs.Case(nx=50, ny=1, nz=1, beta=0.0, y_wall=False, forcing=False,
                                 weno_mode="all"), "random"),
+    "paper-channel-L2-sutherland-erf": (inputs.PAPER_CHANNEL, "channel"),
 }
 
 
@@ -79,9 +80,10 @@ def test_rhs_and_flags_match_oracle(name):
     assert err.max() <= TOL, err
 
 
-def test_c1_twenty_steps_match_oracle():
-    """The FP64 target: relative L2 <= 1e-12 per conserved field after 20 CFL-0.8 steps."""
-    case = inputs.C1
+@pytest.mark.parametrize("case", [inputs.C1, inputs.PAPER_CHANNEL], ids=lambda c: c.name)
+def test_twenty_steps_match_oracle(case):
+    """The FP64 target: relative L2 <= 1e-12 per conserved field after 20 CFL-0.8 steps (the
+    64x48x32 channel, and the same grid with the paper's own settings)."""
     w0 = inputs.channel_state(case, seed=0)
     cfg = O.make_cfg(case)
     wo, to, dts = O.advance(cfg, w0, case.steps, cfl=case.cfl)
