@@ -168,6 +168,39 @@ int strm_sensor(strm_ctx* ctx, const double* w, double* theta, double* div,
 /* Number of WENO faces per direction in the last right-hand-side evaluation. Synchronises. */
 int strm_weno_counts(strm_ctx* ctx, long long counts_host[3]);
 
+/* ---- Flow statistics (Section 3: Reynolds averages over the homogeneous directions and in
+ * time; Favre averages are ratios of the mass-weighted ones, e.g. u~ = (rho u)/rho). Each
+ * sample adds, in FP64 on the device, the spatial means of STRM_NSTAT point-wise quantities,
+ * in this order:
+ *   rho, u, v, w, p, T, rho u, rho v, rho w, rho T, rho uu, rho vv, rho ww, rho uv, rho uw,
+ *   rho vw, uu, vv, ww, uv, p^2, T^2, rho^2, mu.
+ * STRM_STATS_XZ averages over x and z (channel: one row of ny values per quantity);
+ * STRM_STATS_Z averages over z only (spatially developing flows: ny x nx values, x fastest).
+ * The accumulator lives in a caller-owned device buffer; the sums are taken in a fixed order
+ * (one thread per (x, y) column walking z, then one block per row for the x sum). */
+enum { STRM_NSTAT = 24 };
+enum { STRM_STATS_XZ = 0, STRM_STATS_Z = 1 };
+
+/* Device bytes of the statistics buffer for `mode` (0 if ctx is NULL or the mode unknown). */
+size_t strm_stats_bytes(const strm_ctx* ctx, int mode);
+
+/* Attach a caller-owned device buffer of strm_stats_bytes(ctx, mode) bytes (8-byte aligned) and
+ * zero the sums (stream-ordered); resets the sample count and the step counter. buffer = NULL
+ * detaches (no further samples). The buffer must outlive its use by the context. */
+int strm_stats_bind(strm_ctx* ctx, int mode, void* buffer, size_t bytes);
+
+/* Add one sample of the interior state w (stream-ordered). STRM_EINVAL without a buffer. */
+int strm_stats_sample(strm_ctx* ctx, const double* w);
+
+/* Sample automatically after every k-th step taken by strm_rk_step / strm_advance_n (k = 0:
+ * never). Steps are counted from this call. The samples are stream-ordered launches after
+ * the step (not part of the replayed step graph). */
+int strm_stats_every(strm_ctx* ctx, int k);
+
+/* Means over the samples taken so far, out_host[q * rows + r] with rows = ny (XZ) or ny * nx
+ * (Z), and the number of samples (nullable). Synchronises. With no sample yet the means are 0. */
+int strm_stats_read(strm_ctx* ctx, double* out_host, long long* nsamples_host);
+
 /* Kernel classes of the per-kernel timing diagnostics. */
 enum {
   STRM_K_PRIMS = 0, STRM_K_DT, STRM_K_GHOST_PRIMS, STRM_K_SENSOR, STRM_K_GHOST_SENSOR,
@@ -196,8 +229,9 @@ int strm_launch_count(strm_ctx* ctx, long long* launches_host);
 /* ---- Batched ensemble: many independent grids advanced together (different sizes, gas and
  * flow parameters; the same central order L and precision). Each kernel of the right-hand side
  * and of the RK update runs as one launch over all instances, and one RK3 step of the whole
- * ensemble is a CUDA graph replayed per step. Every instance computes exactly what a context of
- * its own would (same kernels, same per-instance reduction order). */
+ * ensemble is a CUDA graph replayed per step. Every instance computes what a context of its own
+ * would (same kernel bodies, same per-instance reduction order), up to where the compiler
+ * contracts a multiply and an add into an FMA, which it decides per kernel. */
 typedef struct strm_ensemble strm_ensemble;
 
 /* Device workspace for n instances (sum of the per-instance workspaces plus the instance

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +73,11 @@ SIGNATURES = {
     "strm_set_time": ([_vp, _d], _i),
     "strm_sensor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "strm_weno_counts": ([_vp, _P(ctypes.c_longlong)], _i),
+    "strm_stats_bytes": ([_vp, _i], _sz),
+    "strm_stats_bind": ([_vp, _i, _vp, _sz], _i),
+    "strm_stats_sample": ([_vp, _vp], _i),
+    "strm_stats_every": ([_vp, _i], _i),
+    "strm_stats_read": ([_vp, _P(_d), _P(ctypes.c_longlong)], _i),
     "strm_kernel_name": ([_i], ctypes.c_char_p),
     "strm_timing": ([_vp, _i], _i),
     "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
@@ -270,6 +276,34 @@ class Solver:
         out = (ctypes.c_longlong * 3)()
         _check("strm_weno_counts", lib().strm_weno_counts(self.ctx, out))
         return list(out)
+
+    STATS_MODES = {"xz": 0, "z": 1}
+    STAT_NAMES = ["rho", "u", "v", "w", "p", "T", "rho_u", "rho_v", "rho_w", "rho_T", "rho_uu",
+                  "rho_vv", "rho_ww", "rho_uv", "rho_uw", "rho_vw", "uu", "vv", "ww", "uv", "pp",
+                  "TT", "rhorho", "mu"]
+
+    def stats_bind(self, mode="xz", every=0):
+        """Allocate and attach a statistics accumulator ("xz": means over x and z per wall-normal
+        row; "z": means over z per (x, y) column) and sample after every `every`-th step."""
+        m = self.STATS_MODES[mode]
+        nbytes = lib().strm_stats_bytes(self.ctx, m)
+        self._stats_buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._stats_mode = mode
+        _check("strm_stats_bind", lib().strm_stats_bind(self.ctx, m, _ptr(self._stats_buf), nbytes))
+        _check("strm_stats_every", lib().strm_stats_every(self.ctx, int(every)))
+
+    def stats_sample(self, w):
+        _check("strm_stats_sample", lib().strm_stats_sample(self.ctx, _ptr(self._state(w))))
+
+    def stats_read(self):
+        """(means [24, ny] or [24, ny, nx] as numpy, number of samples)."""
+        c = self.case
+        shape = (len(self.STAT_NAMES), c.ny) if self._stats_mode == "xz" else (len(self.STAT_NAMES), c.ny, c.nx)
+        out = np.empty(shape)
+        ns = ctypes.c_longlong()
+        _check("strm_stats_read", lib().strm_stats_read(
+            self.ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ns)))
+        return out, ns.value
 
     def timing(self, enable=True):
         _check("strm_timing", lib().strm_timing(self.ctx, int(bool(enable))))

@@ -157,6 +157,13 @@ struct strm_ctx {
   double kms[STRM_K_COUNT] = {};
   long long klaunch[STRM_K_COUNT] = {};
   long long weno_faces[3] = {};
+  // statistics accumulator (caller-owned buffer)
+  double* st_acc = nullptr;  // [STRM_NSTAT][rows]
+  double* st_scr = nullptr;  // x-z mode: [STRM_NSTAT][ny][nx] column sums
+  int st_mode = 0;
+  int st_every = 0;
+  long long st_samples = 0;
+  long long st_steps = 0;
 };
 
 namespace {
@@ -615,10 +622,35 @@ int strm_compute_rhs(strm_ctx* x, const double* w, double* rhs) {
   return STRM_OK;
 }
 
+namespace {
+
+size_t stats_rows(const strm_ctx* x, int mode) {
+  return mode == STRM_STATS_XZ ? (size_t)x->d.ny : (size_t)x->d.ny * x->d.nx;
+}
+
+int enqueue_stats(strm_ctx* x, const double* w) {
+  launch_stats(x->d, x->C, w, x->st_acc, x->st_scr, x->st_mode, x->stream);
+  x->launches += x->st_mode == STRM_STATS_XZ ? 2 : 1;
+  STRM_CK_LAUNCH();
+  ++x->st_samples;
+  return STRM_OK;
+}
+
+// one step taken: sample if the automatic sampling is due
+int after_step(strm_ctx* x, const double* w) {
+  ++x->st_steps;
+  if (x->st_acc && x->st_every > 0 && x->st_steps % x->st_every == 0) return enqueue_stats(x, w);
+  return STRM_OK;
+}
+
+}  // namespace
+
 int strm_rk_step(strm_ctx* x, double* w, double* r_old, double dt, double cfl) {
   int rc = check_step_args(x, w, r_old, dt, cfl);
   if (rc) return rc;
-  return enqueue_step(x, w, r_old, dt, cfl, x->stream);
+  rc = enqueue_step(x, w, r_old, dt, cfl, x->stream);
+  if (rc) return rc;
+  return after_step(x, w);
 }
 
 int strm_advance_n(strm_ctx* x, double* w, double* r_old, int nsteps, double dt, double cfl) {
@@ -629,6 +661,7 @@ int strm_advance_n(strm_ctx* x, double* w, double* r_old, int nsteps, double dt,
   if (x->timing) {  // event timing needs eager launches
     for (int n = 0; n < nsteps; ++n) {
       int erc = enqueue_step(x, w, r_old, dt, cfl, x->stream);
+      if (!erc) erc = after_step(x, w);
       if (erc) return erc;
     }
     return STRM_OK;
@@ -660,8 +693,12 @@ int strm_advance_n(strm_ctx* x, double* w, double* r_old, int nsteps, double dt,
     x->g_dt = dt;
     x->g_cfl = cfl;
   }
-  for (int n = 0; n < nsteps; ++n) STRM_CK(cudaGraphLaunch(x->gexec, x->stream));
-  x->launches += x->graph_kernels * nsteps;
+  for (int n = 0; n < nsteps; ++n) {
+    STRM_CK(cudaGraphLaunch(x->gexec, x->stream));
+    x->launches += x->graph_kernels;
+    int src = after_step(x, w);
+    if (src) return src;
+  }
   return STRM_OK;
 }
 
@@ -674,6 +711,60 @@ int strm_advance_n_host(strm_ctx* x, double* w_host, double* w, double* r_old, i
   if (rc) return rc;
   STRM_CK(cudaMemcpyAsync(w_host, w, bytes, cudaMemcpyDeviceToHost, x->stream));
   STRM_CK(cudaStreamSynchronize(x->stream));
+  return STRM_OK;
+}
+
+size_t strm_stats_bytes(const strm_ctx* x, int mode) {
+  if (!x || (mode != STRM_STATS_XZ && mode != STRM_STATS_Z)) return 0;
+  size_t acc = align_up(sizeof(double) * STRM_NSTAT * stats_rows(x, mode));
+  size_t scr = mode == STRM_STATS_XZ ? align_up(sizeof(double) * STRM_NSTAT * (size_t)x->d.nx * x->d.ny) : 0;
+  return acc + scr;
+}
+
+int strm_stats_bind(strm_ctx* x, int mode, void* buffer, size_t bytes) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  x->st_samples = 0;
+  x->st_steps = 0;
+  if (!buffer) {
+    x->st_acc = x->st_scr = nullptr;
+    return STRM_OK;
+  }
+  size_t need = strm_stats_bytes(x, mode);
+  if (!need) return fail(STRM_EINVAL, "unknown statistics mode");
+  if (bytes < need) return fail(STRM_ENOMEM, "statistics buffer too small: need " + std::to_string(need));
+  if ((uintptr_t)buffer & 7) return fail(STRM_EINVAL, "statistics buffer not 8-byte aligned");
+  x->st_mode = mode;
+  x->st_acc = (double*)buffer;
+  x->st_scr = mode == STRM_STATS_XZ
+                  ? (double*)((char*)buffer + align_up(sizeof(double) * STRM_NSTAT * stats_rows(x, mode)))
+                  : nullptr;
+  STRM_CK(cudaMemsetAsync(x->st_acc, 0, sizeof(double) * STRM_NSTAT * stats_rows(x, mode), x->stream));
+  return STRM_OK;
+}
+
+int strm_stats_sample(strm_ctx* x, const double* w) {
+  if (!x || !w) return fail(STRM_EINVAL, "null context or state");
+  if (!x->st_acc) return fail(STRM_EINVAL, "no statistics buffer bound");
+  return enqueue_stats(x, w);
+}
+
+int strm_stats_every(strm_ctx* x, int k) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  if (k < 0) return fail(STRM_EINVAL, "sampling interval < 0");
+  x->st_every = k;
+  x->st_steps = 0;
+  return STRM_OK;
+}
+
+int strm_stats_read(strm_ctx* x, double* out_host, long long* nsamples_host) {
+  if (!x || !out_host) return fail(STRM_EINVAL, "null context or output");
+  if (!x->st_acc) return fail(STRM_EINVAL, "no statistics buffer bound");
+  size_t n = STRM_NSTAT * stats_rows(x, x->st_mode);
+  STRM_CK(cudaMemcpyAsync(out_host, x->st_acc, sizeof(double) * n, cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
+  double inv = x->st_samples > 0 ? 1.0 / (double)x->st_samples : 0.0;
+  for (size_t q = 0; q < n; ++q) out_host[q] *= inv;
+  if (nsamples_host) *nsamples_host = x->st_samples;
   return STRM_OK;
 }
 

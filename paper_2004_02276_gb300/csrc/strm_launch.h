@@ -27,6 +27,10 @@ void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w
 void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixed, cudaStream_t s);
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_recycle(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// one statistics sample of w: mode 0 adds x-z means to acc[24][ny] (scr holds [24][ny][nx]
+// column sums), mode 1 adds z means to acc[24][ny][nx]
+void launch_stats(const Dims& d, const Consts& C, const double* w, double* acc, double* scr, int mode,
+                  cudaStream_t s);
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
