@@ -25,6 +25,9 @@ class OrcCfg(ctypes.Structure):
         ("ref", ctypes.c_double * 5), ("shock", ctypes.c_int),
         ("shock_theta", ctypes.c_double), ("shock_ximp", ctypes.c_double),
         ("i_recycle", ctypes.c_int), ("delta_in", ctypes.c_double),
+        ("df_prof", ctypes.POINTER(ctypes.c_double)), ("df_psi", ctypes.POINTER(ctypes.c_double)),
+        ("df_count", ctypes.POINTER(ctypes.c_longlong)), ("df_ny", ctypes.c_int),
+        ("df_nz", ctypes.c_int), ("df_tau", ctypes.c_double), ("df_seed", ctypes.c_ulonglong),
         ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double), ("r_gas", ctypes.c_double),
         ("visc_law", ctypes.c_int), ("mu_ref", ctypes.c_double), ("t_ref", ctypes.c_double),
         ("visc_exp", ctypes.c_double), ("suth_s", ctypes.c_double),
@@ -36,7 +39,7 @@ class OrcCfg(ctypes.Structure):
 
 
 WENO_MODES = {"off": 0, "sensor": 1, "all": 2}
-BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3}
+BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3, "df": 4}
 Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2, "erf": 3, "sinh1": 4}
 VISC_LAWS = {"power": 0, "sutherland": 1}
 
@@ -71,6 +74,10 @@ def lib():
         _lib.orc_recycle_scale.argtypes = [cp, dp]
         _lib.orc_recycle_scale.restype = d
         _lib.orc_stats.argtypes = [cp, dp, i, dp]
+        _lib.orc_df_init.argtypes = [cp]
+        _lib.orc_splitmix64.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
+        _lib.orc_splitmix64.restype = ctypes.c_ulonglong
+        _lib.orc_df_plane.argtypes = [cp, ctypes.c_longlong, dp]
     return _lib
 
 
@@ -82,8 +89,22 @@ def _u8(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
 
 
-def make_cfg(case, **over) -> OrcCfg:
-    """Oracle configuration from a workload description; keyword overrides win."""
+class DFState:
+    """The digital-filter inflow data the oracle configuration points to: the mean profiles and
+    Reynolds stresses prof[7, ny] (U, V, T, R11, R12, R22, R33), the fluctuation plane
+    psi[3, nz, ny] and the draw counter, kept alive by this object."""
+
+    def __init__(self, case, prof):
+        self.prof = np.ascontiguousarray(prof, dtype=np.float64)
+        assert self.prof.shape == (7, case.ny)
+        self.psi = np.zeros((3, case.nz, case.ny))
+        self.count = np.zeros(1, dtype=np.int64)
+
+
+def make_cfg(case, df=None, **over) -> OrcCfg:
+    """Oracle configuration from a workload description; keyword overrides win. With a
+    digital-filter inflow face, `df` is the DFState the configuration points to (and the first
+    plane is drawn if its counter is still 0)."""
     get = lambda k, dflt=None: over.get(k, getattr(case, k, dflt))
     c = OrcCfg()
     c.nx, c.ny, c.nz = get("nx"), get("ny"), get("nz")
@@ -106,6 +127,8 @@ def make_cfg(case, **over) -> OrcCfg:
     c.shock_ximp = get("shock_ximp", 0.0)
     c.i_recycle = get("i_recycle", 0)
     c.delta_in = get("delta_in", 1.0)
+    c.df_ny, c.df_nz = get("df_ny", 0), get("df_nz", 0)
+    c.df_tau, c.df_seed = get("df_tau", 0.0), get("df_seed", 0)
     c.gamma, c.prandtl = get("gamma"), get("prandtl")
     c.r_gas = get("r_gas")
     c.visc_law = VISC_LAWS[get("visc_law", "power")]
@@ -120,6 +143,14 @@ def make_cfg(case, **over) -> OrcCfg:
     c.u0, c.l0 = get("u0", 1.0), get("l0", 1.0)
     c.convective = int(bool(get("convective", True)))
     c.viscous = int(bool(get("viscous", True)))
+    if df is not None:
+        c.df_prof = _dp(df.prof)
+        c.df_psi = _dp(df.psi)
+        c.df_count = df.count.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+        c._df = df  # keep the arrays alive with the configuration
+        if df.count[0] == 0 and c.bc_xmin == BC_KINDS["df"]:
+            if lib().orc_df_init(ctypes.byref(c)):
+                raise ValueError("orc_df_init: invalid digital-filter configuration")
     return c
 
 
@@ -239,6 +270,18 @@ def stats(cfg, w, mode=0):
     out = np.empty(shape)
     if lib().orc_stats(ctypes.byref(cfg), _dp(w), int(mode), _dp(out)):
         raise ValueError("orc_stats: invalid configuration or mode")
+    return out
+
+
+def splitmix64(seed, k):
+    return lib().orc_splitmix64(int(seed), int(k))
+
+
+def df_plane(cfg, draw):
+    """Filtered random plane psi[3, nz, ny] of draw number `draw` (no time correlation)."""
+    out = np.empty((3, cfg.nz, cfg.ny))
+    if lib().orc_df_plane(ctypes.byref(cfg), int(draw), _dp(out)):
+        raise ValueError("orc_df_plane: invalid configuration")
     return out
 
 

@@ -39,6 +39,7 @@
 
 #include <math.h>
 #include <stddef.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -148,6 +149,10 @@ static int grid_init(grid_t* g, const orc_cfg* c) {
   if ((c->bc_ymin == ORC_BC_PERIODIC) != (c->bc_ymax == ORC_BC_PERIODIC)) return -1;
   if (c->bc_xmax == ORC_BC_RECYCLE || c->bc_ymin == ORC_BC_RECYCLE || c->bc_ymax == ORC_BC_RECYCLE) return -1;
   if (c->bc_xmin == ORC_BC_RECYCLE && (c->i_recycle < G - 1 || c->i_recycle >= c->nx || !(c->delta_in > 0)))
+    return -1;
+  if (c->bc_xmax == ORC_BC_DF || c->bc_ymin == ORC_BC_DF || c->bc_ymax == ORC_BC_DF) return -1;
+  if (c->bc_xmin == ORC_BC_DF && (!c->df_prof || !c->df_psi || !c->df_count || c->df_ny < 1 ||
+                                  c->df_nz < 1 || !(c->df_tau > 0)))
     return -1;
   g->c = c;
   g->nx = c->nx; g->ny = c->ny; g->nz = c->nz;
@@ -410,6 +415,125 @@ static void fill_recycle(const grid_t* g, double* wg[5], double s) {
   }
 }
 
+/* ---------------------------------------------------------------- digital-filter inflow
+ * Section 3.2 names the method (Klein et al. digital filter, extended to compressible flow by
+ * the strong Reynolds analogy, the filter done as a sequence of one-dimensional convolutions)
+ * without its formulas. Steps, as read from those methods:
+ *  1. random numbers with zero mean and unit variance, r = sqrt(3) (2 u - 1), u uniform from
+ *     SplitMix64, one per (draw, velocity component m, z index k, extended y index);
+ *  2. a Gaussian-shaped filter b_l = exp(-pi l^2 / (2 n^2)) / sqrt(sum_l exp(-pi l^2 / n^2)),
+ *     l = -2n..2n, applied along y (random plane extended by 2n on both sides), then along z
+ *     (periodic);
+ *  3. time correlation: Psi <- Psi exp(-pi dt / (2 tau)) + psi sqrt(1 - exp(-pi dt / tau)),
+ *     once per time step with a fresh filtered plane psi;
+ *  4. velocity fluctuations u'_i = a_ij Psi_j with a the Cholesky factor of the Reynolds stress
+ *     tensor (R13 = R23 = 0);
+ *  5. strong Reynolds analogy at constant pressure: cp T' + U u' = 0, p = ref p, rho = p/(R T).
+ * Every ghost layer of the inflow face takes the same state. */
+
+/* SplitMix64 (Steele, Lea, Flood 2014): output number k + 1 of the generator seeded with seed. */
+static uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+unsigned long long orc_splitmix64(unsigned long long seed, unsigned long long k) {
+  return (unsigned long long)splitmix64((uint64_t)seed, (uint64_t)k);
+}
+
+static double df_random(const orc_cfg* c, long long draw, int m, int k, int je) {
+  uint64_t nye = (uint64_t)c->ny + 4 * (uint64_t)c->df_ny;
+  uint64_t idx = (((uint64_t)draw * 3 + (uint64_t)m) * (uint64_t)c->nz + (uint64_t)k) * nye + (uint64_t)je;
+  double u = (double)(splitmix64(c->df_seed, idx) >> 11) * (1.0 / 9007199254740992.0);
+  return sqrt(3.0) * (2.0 * u - 1.0);
+}
+
+static void df_coefs(int n, double* b) {
+  int N = 2 * n;
+  double s = 0.0;
+  for (int l = -N; l <= N; ++l) {
+    b[l + N] = exp(-acos(-1.0) * l * l / (2.0 * n * n));
+    s += b[l + N] * b[l + N];
+  }
+  for (int l = -N; l <= N; ++l) b[l + N] /= sqrt(s);
+}
+
+int orc_df_plane(const orc_cfg* c, long long draw, double* psi) {
+  int ny = c->ny, nz = c->nz, Ny = 2 * c->df_ny, Nz = 2 * c->df_nz;
+  if (ny < 1 || nz < 1 || c->df_ny < 1 || c->df_nz < 1) return -1;
+  double* by = malloc(sizeof(double) * (2 * Ny + 1));
+  double* bz = malloc(sizeof(double) * (2 * Nz + 1));
+  double* t = malloc(sizeof(double) * 3 * (size_t)nz * ny);
+  df_coefs(c->df_ny, by);
+  df_coefs(c->df_nz, bz);
+  for (int m = 0; m < 3; ++m)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j) {
+        double s = 0.0;
+        for (int l = -Ny; l <= Ny; ++l) s += by[l + Ny] * df_random(c, draw, m, k, j + l + Ny);
+        t[((size_t)m * nz + k) * ny + j] = s;
+      }
+  for (int m = 0; m < 3; ++m)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j) {
+        double s = 0.0;
+        for (int l = -Nz; l <= Nz; ++l) s += bz[l + Nz] * t[((size_t)m * nz + wrap(k + l, nz)) * ny + j];
+        psi[((size_t)m * nz + k) * ny + j] = s;
+      }
+  free(by);
+  free(bz);
+  free(t);
+  return 0;
+}
+
+int orc_df_init(const orc_cfg* c) {
+  if (c->bc_xmin != ORC_BC_DF || !c->df_psi || !c->df_count) return -1;
+  if (orc_df_plane(c, 0, c->df_psi)) return -1;
+  *c->df_count = 1;
+  return 0;
+}
+
+/* Step 3: blend a fresh filtered plane into the time-correlated one. */
+static void df_advance(const orc_cfg* c, double dt) {
+  size_t n = 3 * (size_t)c->nz * c->ny;
+  double* psi = malloc(sizeof(double) * n);
+  orc_df_plane(c, *c->df_count, psi);
+  double pi = acos(-1.0);
+  double e1 = exp(-pi * dt / (2.0 * c->df_tau)), e2 = sqrt(1.0 - exp(-pi * dt / c->df_tau));
+  for (size_t q = 0; q < n; ++q) c->df_psi[q] = c->df_psi[q] * e1 + psi[q] * e2;
+  *c->df_count += 1;
+  free(psi);
+}
+
+/* Steps 4 and 5: the inflow ghost layers from the mean profiles and the fluctuation plane. */
+static void fill_df(const grid_t* g, double* wg[5]) {
+  const orc_cfg* c = g->c;
+  int ny = g->ny, nz = g->nz;
+  const double* P = c->df_prof;
+  double cp = g->cv + c->r_gas;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j) {
+      double U = P[j], V = P[ny + j], Tm = P[2 * ny + j];
+      double R11 = P[3 * ny + j], R12 = P[4 * ny + j], R22 = P[5 * ny + j], R33 = P[6 * ny + j];
+      double a11 = sqrt(R11);
+      double a21 = a11 > 0.0 ? R12 / a11 : 0.0;
+      double a22 = sqrt(fmax(R22 - a21 * a21, 0.0));
+      double a33 = sqrt(R33);
+      const double* ps = c->df_psi;
+      double p0 = ps[((size_t)0 * nz + k) * ny + j], p1 = ps[((size_t)1 * nz + k) * ny + j],
+             p2 = ps[((size_t)2 * nz + k) * ny + j];
+      double up = a11 * p0, vp = a21 * p0 + a22 * p1, wp = a33 * p2;
+      double T = Tm - U * up / cp;
+      double q[5] = {c->ref[4] / (c->r_gas * T), U + up, V + vp, wp, c->ref[4]};
+      double out[5];
+      prim_to_cons(g, q, out);
+      for (int l = 1; l <= G; ++l)
+        for (int m = 0; m < 5; ++m) wg[m][gidx(g, -l, j, k)] = out[m];
+    }
+}
+
 /* Fill the ghost layers of the five ghosted conserved arrays face by face. Only the faces are
  * filled (no edges or corners): every stencil of the method runs along one grid line. */
 static void fill_ghosts_w(const grid_t* g, double* wg[5]) {
@@ -443,6 +567,7 @@ static void fill_ghosts_w(const grid_t* g, double* wg[5]) {
   /* x faces (outflow-type characteristic faces see the boundary state at the reference
    * pressure) */
   if (c->bc_xmin == ORC_BC_RECYCLE) fill_recycle(g, wg, recycle_scale_g(g, wg));
+  if (c->bc_xmin == ORC_BC_DF) fill_df(g, wg);
   if (c->bc_xmin == ORC_BC_CHAR || c->bc_xmax == ORC_BC_CHAR)
     for (int k = 0; k < nz; ++k)
       for (int j = 0; j < ny; ++j)
@@ -1050,6 +1175,12 @@ int orc_rk_step(const orc_cfg* c, double* w, double dt, double cfl, double* dt_u
   long n = 5L * c->nx * c->ny * c->nz;
   if (dt <= 0.0) dt = orc_cfl_dt(c, w, cfl);
   if (dt_used) *dt_used = dt;
+  if (c->bc_xmin == ORC_BC_DF) {
+    grid_t g;
+    if (grid_init(&g, c)) return -1;
+    grid_free(&g);
+    df_advance(c, dt);
+  }
   double* r_old = calloc((size_t)n, sizeof(double));
   double* r = malloc(sizeof(double) * (size_t)n);
   int rc = 0;
@@ -1065,7 +1196,6 @@ int orc_rk_step(const orc_cfg* c, double* w, double dt, double cfl, double* dt_u
   return rc;
 }
 
-/* Metric-weighted totals: sum over interior nodes of w_m dx (y_eta deta) dz. */
 /* Per-sample statistics: the primitives of each interior node from w (E = cv T + |u|^2/2,
  * p = rho R T), the 24 products listed in the header, then plain means over the homogeneous
  * directions (x and z, or z only). */
@@ -1098,6 +1228,7 @@ int orc_stats(const orc_cfg* c, const double* w, int mode, double* out) {
   return 0;
 }
 
+/* Metric-weighted totals: sum over interior nodes of w_m dx (y_eta deta) dz. */
 int orc_totals(const orc_cfg* c, const double* w, double out[5]) {
   grid_t g;
   if (grid_init(&g, c)) return -1;

@@ -24,7 +24,7 @@ extern "C" {
 
 enum { ORC_MAP_UNIFORM = 0, ORC_MAP_TANH = 1, ORC_MAP_TANH_ONESIDED = 2, ORC_MAP_ERF = 3,
        ORC_MAP_SINH_ONESIDED = 4 };
-enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_CHAR = 2, ORC_BC_RECYCLE = 3 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_CHAR = 2, ORC_BC_RECYCLE = 3, ORC_BC_DF = 4 };
 enum { ORC_WENO_OFF = 0, ORC_WENO_SENSOR = 1, ORC_WENO_ALL = 2 };
 enum { ORC_VISC_POWER = 0, ORC_VISC_SUTHERLAND = 1 };
 
@@ -35,7 +35,7 @@ typedef struct {
   int y_map;            /* ORC_MAP_UNIFORM, ORC_MAP_TANH or ORC_MAP_ERF (both walls), or
                            ORC_MAP_TANH_ONESIDED or ORC_MAP_SINH_ONESIDED (wall at y = 0) */
   double beta;          /* stretching parameter of the map */
-  /* face kinds (z is periodic): x faces PERIODIC, RECYCLE (x-min only) or CHAR; y faces
+  /* face kinds (z is periodic): x faces PERIODIC, RECYCLE or DF (x-min only) or CHAR; y faces
    * PERIODIC, WALL or CHAR */
   int bc_xmin, bc_xmax, bc_ymin, bc_ymax;
   double ref[5];        /* reference primitives (rho, u, v, w, p) seen by characteristic faces */
@@ -45,6 +45,18 @@ typedef struct {
   double shock_theta, shock_ximp;
   int i_recycle;        /* recycling plane (interior x index >= 2) */
   double delta_in;      /* inflow boundary-layer thickness (99 % of ref u) */
+  /* digital-filter inflow (bc_xmin == ORC_BC_DF; Section 3.2): mean profiles and Reynolds
+   * stresses per wall-normal node, df_prof[7][ny] = U, V, T, R11, R12, R22, R33; filter
+   * half-widths n in grid points along y and z (support 2n on each side); integral time tau;
+   * generator seed; the fluctuation plane df_psi[3][nz][ny] and the draw counter df_count,
+   * both kept by the caller and updated by orc_df_init and orc_rk_step. The ghost pressure is
+   * ref[4]. */
+  const double* df_prof;
+  double* df_psi;
+  long long* df_count;
+  int df_ny, df_nz;
+  double df_tau;
+  unsigned long long df_seed;
   /* gas: p = rho R T, E = cv T + |u|^2/2, k = cp mu / Pr */
   double gamma, prandtl, r_gas;
   int visc_law;         /* mu = mu_ref (T/t_ref)^visc_exp, or Sutherland with constant suth_s */
@@ -100,6 +112,17 @@ double orc_weno5(const double* f, double eps);
  * Returns 0, or -1 if the deflection exceeds the attached-shock limit. */
 int orc_oblique_shock(double gamma, double mach, double theta, double* beta, double* p_ratio,
                       double* rho_ratio, double* mach2);
+
+/* Digital-filter inflow: draw the first fluctuation plane (draw 0) into df_psi and set
+ * df_count = 1. Each orc_rk_step then blends in a new draw (see the source for the steps). */
+int orc_df_init(const orc_cfg* c);
+
+/* SplitMix64 output number k + 1 for the given seed (the generator of the inflow's random
+ * numbers; exported for its test vector). */
+unsigned long long orc_splitmix64(unsigned long long seed, unsigned long long k);
+
+/* Filtered (not time-correlated) random plane of draw number `draw`, psi[3][nz][ny]. */
+int orc_df_plane(const orc_cfg* c, long long draw, double* psi);
 
 /* Recycling rescale factor s = delta_r / delta_in for the state w (1 if no recycling face). */
 double orc_recycle_scale(const orc_cfg* c, const double* w);

@@ -58,7 +58,7 @@ class Case:
     beta: float = 1.5            # tanh wall clustering; 0 gives a uniform y grid
     y_map: str = "tanh"          # "tanh", "erf": clustered at both walls; "tanh1", "sinh1": at y = 0 only
     y_wall: bool = True          # isothermal staggered walls in y (else periodic)
-    bc_xmin: str = None          # face kinds ("periodic", "wall", "char", "recycle"); None:
+    bc_xmin: str = None          # face kinds ("periodic", "wall", "char", "recycle", "df"); None:
     bc_xmax: str = None          #   x periodic, y walls or periodic per y_wall
     bc_ymin: str = None
     bc_ymax: str = None
@@ -67,6 +67,10 @@ class Case:
     shock_ximp: float = 0.0      # x where the incident shock reaches the wall
     i_recycle: int = 0           # recycling plane (x index) of a recycling inflow
     delta_in: float = 1.0        # inflow boundary-layer thickness
+    df_ny: int = 0               # digital-filter inflow: filter half-widths n (grid points) in y, z,
+    df_nz: int = 0               #   integral time scale and generator seed
+    df_tau: float = 0.0
+    df_seed: int = 0
     gamma: float = 1.4
     prandtl: float = 0.72
     mach: float = 1.5            # bulk Mach number u_b / c_w
@@ -164,6 +168,23 @@ def node_y(case: Case) -> np.ndarray:
     if case.y_map == "erf":
         return 0.5 * case.ly * np.array([math.erf(b * (2.0 * e - 1.0)) for e in eta]) / math.erf(b)
     return 0.5 * case.ly * np.tanh(b * (2.0 * eta - 1.0)) / math.tanh(b)
+
+
+def df_profiles(case: Case) -> np.ndarray:
+    """Inflow data of a digital-filter inflow, [7, ny]: mean U, V, T and the Reynolds stresses
+    R11, R12, R22, R33 at the wall-normal nodes. Synthetic stand-in for a DNS Reynolds-stress
+    profile: U and T as in bl_state (1/7 power law, Crocco-Busemann), and stresses of the shape
+    g(h) = (h/h0) exp(1 - h/h0) with h0 = 0.1 delta_in, faded out above delta_in, amplitudes
+    (0.1, 0.04, 0.06)^2 of u_inf^2 for R11, R22, R33 and a correlation R12 = -0.5 sqrt(R11 R22)."""
+    yy = node_y(case)
+    h = np.maximum(yy - (0.0 if one_sided(case) else -0.5 * case.ly), 0.0) / case.delta_in
+    U = np.minimum(h ** (1.0 / 7.0), 1.0)
+    tr = 1.0 + case.prandtl ** (1.0 / 3.0) * 0.5 * (case.gamma - 1.0) * case.mach ** 2
+    T = case.t_wall + (tr - case.t_wall) * U + (1.0 - tr) * U * U
+    g = (h / 0.1) * np.exp(1.0 - h / 0.1) * 0.5 * (1.0 - np.tanh((h - 1.0) / 0.1))
+    R11, R22, R33 = 0.1 ** 2 * g, 0.04 ** 2 * g, 0.06 ** 2 * g
+    R12 = -0.5 * np.sqrt(R11 * R22)
+    return np.stack([U, np.zeros_like(U), T, R11, R12, R22, R33])
 
 
 def one_sided(case: Case) -> bool:
