@@ -57,8 +57,9 @@ enum {
   STRM_BC_WALL_ISOTHERMAL = 1, /* y faces; no params */
   STRM_BC_CHARACTERISTIC = 2,  /* 5 params: reference rho, u, v, w, p */
   STRM_BC_RECYCLE_INFLOW = 3,  /* x-min; 7 params: reference rho, u, v, w, p, recycling plane i, delta_in */
-  STRM_BC_SHOCK_TOP = 4        /* y-max; 7 params: free stream rho, u, v, w, p, deflection theta
+  STRM_BC_SHOCK_TOP = 4,       /* y-max; 7 params: free stream rho, u, v, w, p, deflection theta
                                   (radians), x where the incident shock reaches the wall */
+  STRM_BC_DF_INFLOW = 5        /* x-min; digital-filter inflow, set with strm_set_inflow_df */
 };
 enum { STRM_FACE_YMIN_YMAX = 0, STRM_FACE_XMIN = 1, STRM_FACE_XMAX = 2, STRM_FACE_YMIN = 3, STRM_FACE_YMAX = 4 };
 enum { STRM_WENO_OFF = 0, STRM_WENO_SENSOR = 1, STRM_WENO_ALL = 2 };
@@ -167,6 +168,32 @@ int strm_sensor(strm_ctx* ctx, const double* w, double* theta, double* div,
 
 /* Number of WENO faces per direction in the last right-hand-side evaluation. Synchronises. */
 int strm_weno_counts(strm_ctx* ctx, long long counts_host[3]);
+
+/* ---- Digital-filter turbulent inflow (Section 3.2: Klein-type digital filter done as a sequence
+ * of one-dimensional convolutions, strong Reynolds analogy, prescribed Reynolds stresses). Once
+ * per time step a new random plane is drawn (SplitMix64 keyed by draw, velocity component, z
+ * and extended-y index; r = sqrt(3)(2u - 1)), filtered along y with b_l = exp(-pi l^2/(2 n^2))
+ * normalised to unit energy, l = -2n..2n, then along z (periodic), and blended into the
+ * fluctuation plane Psi <- Psi exp(-pi dt/(2 tau)) + psi sqrt(1 - exp(-pi dt/tau)). Every ghost
+ * layer of the x-min face takes u_i = U_i(y) + a_ij Psi_j (a: Cholesky factor of the Reynolds
+ * stresses, R13 = R23 = 0), T = T(y) - U u'/cp, p = p_ref, rho = p/(R T). */
+typedef struct {
+  double p_ref;              /* inflow pressure */
+  int ny_filter, nz_filter;  /* filter half-widths n in grid points along y and z (>= 1) */
+  double tau;                /* integral time scale of the time correlation (> 0) */
+  unsigned long long seed;   /* generator seed */
+} strm_df;
+
+/* Device bytes of the inflow buffer for this context and filter (0 if invalid). */
+size_t strm_inflow_df_bytes(const strm_ctx* ctx, const strm_df* df);
+
+/* Make the x-min face a digital-filter inflow. profiles_host[7][ny]: the mean U, V, T and the
+ * Reynolds stresses R11, R12, R22, R33 at the wall-normal nodes (R must be positive
+ * semi-definite). buffer: caller-owned device memory of strm_inflow_df_bytes() bytes, 8-byte
+ * aligned, kept while the face is in use. Draws the first plane (stream-ordered). The x-max face
+ * must not be periodic. STRM_EINVAL on bad arguments. */
+int strm_set_inflow_df(strm_ctx* ctx, const strm_df* df, const double* profiles_host, void* buffer,
+                       size_t bytes);
 
 /* ---- Flow statistics (Section 3: Reynolds averages over the homogeneous directions and in
  * time; Favre averages are ratios of the mass-weighted ones, e.g. u~ = (rho u)/rho). Each

@@ -23,7 +23,12 @@ VISC_LAWS = {"power": 0, "sutherland": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 Y_MAPS = {"uniform": 0, "tanh": 1, "tanh1": 2, "erf": 3, "sinh1": 4}
 FACES = {"xmin": 1, "xmax": 2, "ymin": 3, "ymax": 4}
-BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3, "shock": 4}
+BC_KINDS = {"periodic": 0, "wall": 1, "char": 2, "recycle": 3, "shock": 4, "df": 5}
+
+
+class DF(ctypes.Structure):
+    _fields_ = [("p_ref", ctypes.c_double), ("ny_filter", ctypes.c_int), ("nz_filter", ctypes.c_int),
+                ("tau", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
 
 
 class StrmError(RuntimeError):
@@ -73,6 +78,8 @@ SIGNATURES = {
     "strm_set_time": ([_vp, _d], _i),
     "strm_sensor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "strm_weno_counts": ([_vp, _P(ctypes.c_longlong)], _i),
+    "strm_inflow_df_bytes": ([_vp, _P(DF)], _sz),
+    "strm_set_inflow_df": ([_vp, _P(DF), _P(_d), _vp, _sz], _i),
     "strm_stats_bytes": ([_vp, _i], _sz),
     "strm_stats_bind": ([_vp, _i, _vp, _sz], _i),
     "strm_stats_sample": ([_vp, _vp], _i),
@@ -151,6 +158,8 @@ def face_settings(case):
     ref = list(getattr(case, "ref", None) or (1.0, 0.0, 0.0, 0.0, 1.0))
     out = []
     for face, kind in kinds.items():
+        if kind == "df":
+            continue  # set with the inflow profiles (Solver.set_inflow_df)
         if kind in ("periodic", "wall"):
             out.append((FACES[face], BC_KINDS[kind], None))
         elif kind == "char" and face == "ymax" and getattr(case, "shock", False):
@@ -192,7 +201,11 @@ class Solver:
     State tensors are float64 CUDA tensors of shape [5, nz, ny, nx] (contiguous).
     """
 
-    def __init__(self, case, device=None, stream=None):
+    def __init__(self, case, device=None, stream=None, inflow=None):
+        """`inflow`: the [7, ny] profiles (U, V, T, R11, R12, R22, R33) of a digital-filter
+        inflow face, required when case.bc_xmin == "df"."""
+        if getattr(case, "bc_xmin", None) == "df" and inflow is None:
+            raise ValueError("a digital-filter inflow face needs its profiles (inflow=...)")
         self.case = case
         self.device = torch.device(device if device is not None else "cuda")
         self.g, self.p, self.s = structs(case)
@@ -209,6 +222,23 @@ class Solver:
             _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
         self.ctx = ctx
         apply_faces(L, self.ctx, case)
+        if getattr(case, "bc_xmin", None) == "df":
+            self.set_inflow_df(inflow)
+
+    def set_inflow_df(self, prof):
+        """Make the x-min face a digital-filter inflow with the case's filter parameters."""
+        c = self.case
+        prof = np.ascontiguousarray(prof, dtype=np.float64)
+        if prof.shape != (7, c.ny):
+            raise ValueError("inflow profiles must be [7, ny]")
+        df = DF(c.ref[4], c.df_ny, c.df_nz, c.df_tau, c.df_seed)
+        nbytes = lib().strm_inflow_df_bytes(self.ctx, ctypes.byref(df))
+        if nbytes == 0:
+            raise StrmError("strm_inflow_df_bytes", -1, "invalid inflow parameters")
+        self._df_buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check("strm_set_inflow_df", lib().strm_set_inflow_df(
+            self.ctx, ctypes.byref(df), prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            _ptr(self._df_buf), nbytes))
 
     @property
     def shape(self):

@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/strm.h): context, workspace layout, stage
 // sequencing on the caller's stream, and the CUDA graph replayed by strm_advance_n.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -164,6 +165,9 @@ struct strm_ctx {
   int st_every = 0;
   long long st_samples = 0;
   long long st_steps = 0;
+  // digital-filter inflow (caller-owned buffer)
+  DFParams df = {};
+  std::vector<double> df_host;  // profiles and filter coefficients, kept for the async upload
 };
 
 namespace {
@@ -397,6 +401,9 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   STRM_LAUNCH(STRM_K_PRIMS, launch_prims(d, C, B, w, dt_mode && dt_fixed <= 0.0, st));
   if (dt_mode) STRM_LAUNCH(STRM_K_DT, launch_dt_finalize(d, B, cfl, dt_fixed, st));
   if (C.bc[0] == kBcRecycle) STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_recycle(d, C, B, st));
+  // digital-filter inflow: a new plane once per step, after the step's dt is known
+  if (dt_mode && C.bc[0] == kBcDigitalFilter)
+    STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_df_update(d, x->df, B, false, st));
   STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
   STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, st));
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
@@ -478,6 +485,9 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->C.dx = g->lx / g->nx;
   for (int m = 0; m < 5; ++m) x->C.ref[m] = x->C.shock_ref[m] = 0.0;
   x->C.x_foot = 0.0;
+  x->C.df_p = 0.0;
+  x->B.df_prof = nullptr;
+  x->B.df_psi = nullptr;
   char* ws = (char*)workspace;
   Nodes<double>& N64 = x->B.n64;
   Nodes<float>& N32 = x->B.n32;
@@ -579,6 +589,8 @@ int strm_set_bc(strm_ctx* x, int face, int kind, const double* params, int npara
         C.i_recycle = ir;
         C.delta_in = params[6];
         C.bc[0] = kBcRecycle;
+      } else if (kind == STRM_BC_DF_INFLOW) {
+        return fail(STRM_EINVAL, "digital-filter inflow faces are set with strm_set_inflow_df");
       } else if (kind == STRM_BC_SHOCK_TOP) {
         if (slot != 3) return fail(STRM_EINVAL, "the oblique-shock reference is a y-max face");
         if (!need(7) || !set_ref(C.ref)) return fail(STRM_EINVAL, "shock top takes 7 params: rho u v w p theta x_imp");
@@ -711,6 +723,110 @@ int strm_advance_n_host(strm_ctx* x, double* w_host, double* w, double* r_old, i
   if (rc) return rc;
   STRM_CK(cudaMemcpyAsync(w_host, w, bytes, cudaMemcpyDeviceToHost, x->stream));
   STRM_CK(cudaStreamSynchronize(x->stream));
+  return STRM_OK;
+}
+
+namespace {
+
+struct DFLayout {
+  size_t prof, by, bz, t, psi, count, total;
+};
+
+bool df_layout(const strm_ctx* x, const strm_df* P, DFLayout* L) {
+  if (!x || !P || P->ny_filter < 1 || P->nz_filter < 1 || !(P->tau > 0) || !(P->p_ref > 0)) return false;
+  size_t ny = x->d.ny, plane = (size_t)x->d.nz * x->d.ny, off = 0;
+  L->prof = off;
+  off = align_up(off + sizeof(double) * 7 * ny);
+  L->by = off;
+  off = align_up(off + sizeof(double) * (4 * (size_t)P->ny_filter + 1));
+  L->bz = off;
+  off = align_up(off + sizeof(double) * (4 * (size_t)P->nz_filter + 1));
+  L->t = off;
+  off = align_up(off + sizeof(double) * 3 * plane);
+  L->psi = off;
+  off = align_up(off + sizeof(double) * 3 * plane);
+  L->count = off;
+  off = align_up(off + sizeof(unsigned long long));
+  L->total = off;
+  return true;
+}
+
+// filter coefficients b_l = exp(-pi l^2 / (2 n^2)), l = -2n..2n, scaled to unit sum of squares
+void df_coefs(int n, double* b) {
+  const double pi = std::acos(-1.0);
+  double s = 0.0;
+  for (int l = -2 * n; l <= 2 * n; ++l) {
+    b[l + 2 * n] = std::exp(-pi * l * l / (2.0 * n * n));
+    s += b[l + 2 * n] * b[l + 2 * n];
+  }
+  double r = 1.0 / std::sqrt(s);
+  for (int l = 0; l <= 4 * n; ++l) b[l] *= r;
+}
+
+}  // namespace
+
+size_t strm_inflow_df_bytes(const strm_ctx* x, const strm_df* P) {
+  DFLayout L;
+  return df_layout(x, P, &L) ? L.total : 0;
+}
+
+int strm_set_inflow_df(strm_ctx* x, const strm_df* P, const double* prof, void* buffer, size_t bytes) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  DFLayout L;
+  if (!df_layout(x, P, &L)) return fail(STRM_EINVAL, "bad inflow parameters (filter widths >= 1, tau > 0, p_ref > 0)");
+  if (!prof || !buffer) return fail(STRM_EINVAL, "null profiles or buffer");
+  if (bytes < L.total) return fail(STRM_ENOMEM, "inflow buffer too small: need " + std::to_string(L.total));
+  if ((uintptr_t)buffer & 7) return fail(STRM_EINVAL, "inflow buffer not 8-byte aligned");
+  if (x->C.bc[1] == kBcPeriodic) return fail(STRM_EINVAL, "an inflow face needs a non-periodic x-max face");
+  const int ny = x->d.ny;
+  const int nby = 4 * P->ny_filter + 1, nbz = 4 * P->nz_filter + 1;
+  // host copies: U, V, T and the Cholesky factors a11, a21, a22, a33 per j, then the filters
+  x->df_host.assign(7 * (size_t)ny + nby + nbz, 0.0);
+  double* h = x->df_host.data();
+  for (int j = 0; j < ny; ++j) {
+    double R11 = prof[3 * ny + j], R12 = prof[4 * ny + j], R22 = prof[5 * ny + j], R33 = prof[6 * ny + j];
+    if (!(R11 >= 0) || !(R22 >= 0) || !(R33 >= 0) || !(prof[2 * ny + j] > 0))
+      return fail(STRM_EINVAL, "inflow profiles: T > 0 and non-negative normal stresses required");
+    double a11 = std::sqrt(R11), a21 = a11 > 0 ? R12 / a11 : 0.0;
+    double r22 = R22 - a21 * a21;
+    if (r22 < -1e-12 * (R22 + 1e-300)) return fail(STRM_EINVAL, "inflow Reynolds stresses not positive semi-definite");
+    h[j] = prof[j];
+    h[ny + j] = prof[ny + j];
+    h[2 * ny + j] = prof[2 * ny + j];
+    h[3 * ny + j] = a11;
+    h[4 * ny + j] = a21;
+    h[5 * ny + j] = std::sqrt(std::max(r22, 0.0));
+    h[6 * ny + j] = std::sqrt(R33);
+  }
+  df_coefs(P->ny_filter, h + 7 * ny);
+  df_coefs(P->nz_filter, h + 7 * ny + nby);
+  char* b = (char*)buffer;
+  DFParams& F = x->df;
+  F.ny = P->ny_filter;
+  F.nz = P->nz_filter;
+  F.tau = P->tau;
+  F.seed = P->seed;
+  F.by = (const double*)(b + L.by);
+  F.bz = (const double*)(b + L.bz);
+  F.t = (double*)(b + L.t);
+  F.psi = (double*)(b + L.psi);
+  F.count = (unsigned long long*)(b + L.count);
+  cudaStream_t st = x->stream;
+  STRM_CK(cudaMemcpyAsync(b + L.prof, h, sizeof(double) * 7 * ny, cudaMemcpyHostToDevice, st));
+  STRM_CK(cudaMemcpyAsync(b + L.by, h + 7 * ny, sizeof(double) * nby, cudaMemcpyHostToDevice, st));
+  STRM_CK(cudaMemcpyAsync(b + L.bz, h + 7 * ny + nby, sizeof(double) * nbz, cudaMemcpyHostToDevice, st));
+  STRM_CK(cudaMemsetAsync(F.count, 0, sizeof(unsigned long long), st));
+  x->C.bc[0] = kBcDigitalFilter;
+  x->C.df_p = P->p_ref;
+  x->B.df_prof = (const double*)(b + L.prof);
+  x->B.df_psi = F.psi;
+  launch_df_update(x->d, F, x->B, true, st);
+  x->launches += 2;
+  STRM_CK_LAUNCH();
+  if (x->gexec) {  // the captured graph holds the old constants
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
   return STRM_OK;
 }
 

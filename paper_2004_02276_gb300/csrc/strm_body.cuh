@@ -357,6 +357,28 @@ __device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C,
   return g;
 }
 
+// Digital-filter inflow ghost (every layer of the x-min face): mean profile plus the velocity
+// fluctuations a Psi (Cholesky factor of the Reynolds stresses times the filtered plane), the
+// temperature from the strong Reynolds analogy cp T' + U u' = 0, and the inflow pressure.
+__device__ __forceinline__ PState df_pstate(const Dims& d, const Consts& C, const Bufs& B, int j, int k) {
+  const double* P = B.df_prof;
+  const int ny = d.ny;
+  double U = __ldg(P + j), V = __ldg(P + ny + j), Tm = __ldg(P + 2 * ny + j);
+  double a11 = __ldg(P + 3 * ny + j), a21 = __ldg(P + 4 * ny + j), a22 = __ldg(P + 5 * ny + j),
+         a33 = __ldg(P + 6 * ny + j);
+  long long plane = (long long)d.nz * ny, at = (long long)k * ny + j;
+  double p0 = __ldg(B.df_psi + at), p1 = __ldg(B.df_psi + plane + at), p2 = __ldg(B.df_psi + 2 * plane + at);
+  double up = a11 * p0, vp = fma(a21, p0, a22 * p1), wp = a33 * p2;
+  PState g;
+  g.u = U + up;
+  g.v = V + vp;
+  g.w = wp;
+  g.T = Tm - U * up / C.cp;
+  g.p = C.df_p;
+  g.rho = g.p / (C.r_gas * g.T);
+  return g;
+}
+
 // Ghost node primitives by face kind (both precisions).
 __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C, const Bufs& B,
                                                  long long nthreads, int blk) {
@@ -379,6 +401,8 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
     g = wall_pstate(C, load_pstate(P, gidx(d, i, jm, k)));
   } else if (kind == kBcRecycle) {
     g = recycle_pstate(d, C, B, layer, j, k);
+  } else if (kind == kBcDigitalFilter) {
+    g = df_pstate(d, C, B, j, k);
   } else {  // characteristic
     int ib = face == 0 ? (side == 0 ? 0 : d.nx - 1) : i;
     int jb = face == 1 ? (side == 0 ? 0 : d.ny - 1) : j;

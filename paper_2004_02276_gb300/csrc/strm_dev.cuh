@@ -53,8 +53,8 @@ struct Coefs {
 
 // Face kinds: x faces periodic, recycling inflow (x-min) or characteristic; y faces periodic,
 // isothermal wall or characteristic (y-max optionally with the post-shock reference state
-// downstream of the shock foot); z periodic.
-enum { kBcPeriodic = 0, kBcWall = 1, kBcChar = 2, kBcRecycle = 3 };
+// downstream of the shock foot), digital-filter inflow (x-min); z periodic.
+enum { kBcPeriodic = 0, kBcWall = 1, kBcChar = 2, kBcRecycle = 3, kBcDigitalFilter = 4 };
 
 struct Consts {
   // gas (FP64)
@@ -69,6 +69,7 @@ struct Consts {
   double shock_ref[5], x_foot;
   int i_recycle;
   double delta_in, dx;
+  double df_p;  // pressure of the digital-filter inflow ghosts
   // scheme
   int L, weno_mode, convective, viscous, mixed;
   double vtot;  // total metric volume
@@ -92,6 +93,10 @@ struct Bufs {
   const double* vol;                            // node volume dx (y_eta deta) dz per j
   const double* hy;                             // node height above the wall eta = 0, per j
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j
+  // digital-filter inflow: per j U, V, T and the Cholesky factors a11, a21, a22, a33 of the
+  // Reynolds stresses ([7][ny]), and the time-correlated fluctuation plane [3][nz][ny]
+  const double* df_prof;
+  const double* df_psi;
 };
 
 template <typename R> __device__ __forceinline__ const Nodes<R>& nodes(const Bufs& B);

@@ -27,6 +27,20 @@ void launch_prims(const Dims& d, const Consts& C, const Bufs& B, const double* w
 void launch_dt_finalize(const Dims& d, const Bufs& B, double cfl, double dt_fixed, cudaStream_t s);
 void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_recycle(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// digital-filter inflow: filter half-widths (grid points), integral time, seed, and the device
+// arrays of the caller's inflow buffer (filter coefficients, y-filtered plane, Psi, draw counter)
+struct DFParams {
+  int ny, nz;
+  double tau;
+  unsigned long long seed;
+  const double* by;
+  const double* bz;
+  double* t;
+  double* psi;
+  unsigned long long* count;
+};
+// draw and filter one plane and blend it into Psi (first: Psi = the plane)
+void launch_df_update(const Dims& d, const DFParams& F, const Bufs& B, bool first, cudaStream_t s);
 // one statistics sample of w: mode 0 adds x-z means to acc[24][ny] (scr holds [24][ny][nx]
 // column sums), mode 1 adds z means to acc[24][ny][nx]
 void launch_stats(const Dims& d, const Consts& C, const double* w, double* acc, double* scr, int mode,
