@@ -885,16 +885,38 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
 
 // ------------------------------------------------------------------------------ face kernels
 
-// Warp-aggregated append of face q to a compacted list: one atomic per warp and list.
-__device__ __forceinline__ void warp_append(bool mine, unsigned act, int* list, unsigned* count, int q) {
-  unsigned m = __ballot_sync(act, mine);
-  if (!m) return;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
-  base = __shfl_sync(act, base, leader);
-  if (mine) list[base + __popc(m & ((1u << lane) - 1u))] = q;
+// Block-aggregated append of face q to one of two compacted lists (a when to_a, else b): per-warp
+// counts by ballot, one atomic per list and block, in-block offsets from a prefix over the
+// warps. Every thread of the block calls it (valid = false for threads past the end).
+__device__ __forceinline__ void block_append2(bool valid, bool to_a, int q, int* list_a, unsigned* count_a,
+                                              int* list_b, unsigned* count_b) {
+  __shared__ unsigned s_a[32], s_b[32], s_base[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  unsigned ma = __ballot_sync(0xffffffffu, valid && to_a);
+  unsigned mb = __ballot_sync(0xffffffffu, valid && !to_a);
+  if (lane == 0) {
+    s_a[warp] = __popc(ma);
+    s_b[warp] = __popc(mb);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned ta = 0, tb = 0;
+    for (int w = 0; w < nwarp; ++w) {  // exclusive prefix over the warps
+      unsigned a = s_a[w], b = s_b[w];
+      s_a[w] = ta;
+      s_b[w] = tb;
+      ta += a;
+      tb += b;
+    }
+    s_base[0] = ta ? atomicAdd(count_a, ta) : 0u;
+    s_base[1] = tb ? atomicAdd(count_b, tb) : 0u;
+  }
+  __syncthreads();
+  if (valid) {
+    unsigned below = (1u << lane) - 1u;
+    if (to_a) list_a[s_base[0] + s_a[warp] + __popc(ma & below)] = q;
+    else list_b[s_base[1] + s_b[warp] + __popc(mb & below)] = q;
+  }
 }
 
 // Hybrid switch, sensor mode: split the faces of one direction into a WENO list and a central
@@ -902,13 +924,13 @@ __device__ __forceinline__ void warp_append(bool mine, unsigned act, int* list, 
 template <int L, int DIR, typename R>
 __device__ __forceinline__ void body_classify(const Dims& d, const Consts& C, const Bufs& B, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
-  if (q >= d.nf[DIR]) return;
-  int i, j, k;
-  face_node<DIR>(d, q, i, j, k);
-  bool fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
-  unsigned act = __activemask();
-  warp_append(fl, act, B.wl[DIR], B.wcount + DIR, (int)q);
-  warp_append(!fl, act, B.cl[DIR], B.wcount + 4 + DIR, (int)q);
+  bool valid = q < d.nf[DIR], fl = false;
+  if (valid) {
+    int i, j, k;
+    face_node<DIR>(d, q, i, j, k);
+    fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
+  }
+  block_append2(valid, fl, (int)q, B.wl[DIR], B.wcount + DIR, B.cl[DIR], B.wcount + 4 + DIR);
 }
 
 // Central flux at every face of one direction (WENO off) or at the faces of the central list.

@@ -1,8 +1,8 @@
 // Face kernels of one grid (central energy-consistent flux, characteristic LF-WENO5 at the faces
 // the Ducros sensor flags) and the assembly of the residual with the viscous terms.
 //
-// Per direction: k_classify splits the faces into a WENO list and a central list (warp-aggregated
-// atomics), k_central and k_weno then run over their lists without warp divergence whatever the
+// Per direction: k_classify splits the faces into a WENO list and a central list (one atomic per
+// list and block), k_central and k_weno then run over their lists without warp divergence whatever the
 // flagged fraction (a per-face branch would run both paths in most warps). k_assemble then forms
 // R = -sum_d (f_{s+1} - f_s)/h_d + viscous terms per node and the forcing partial sums. The
 // bodies are in strm_body.cuh.
