@@ -166,6 +166,12 @@ def max_over_ranks(world, v):
     return float(t.item())
 
 
+def job_rate(points, steps, world, ms_max):
+    """Whole-job grid-point RK-stage updates/s: every rank advances its own replica of
+    `points` points by `steps` RK3 steps; the job time is the slowest rank's."""
+    return points * 3 * steps * world / (ms_max / 1e3)
+
+
 def cpu_sample(case):
     """The oracle on one full RK3 step of the workload (host cores): (rate, seconds, state)."""
     from oracle import oracle as O
@@ -212,7 +218,7 @@ def measure(case, args, world, local, flops_per_unit, traffic_per_unit):
         barrier(world)
     launches = solver.launch_count() - n0
     ms_max = max_over_ranks(world, start.elapsed_time(stop))
-    value = case.npts * 3 * args.steps * world / (ms_max / 1e3)
+    value = job_rate(case.npts, args.steps, world, ms_max)
 
     solver.timing(True)
     solver.advance_n(w, r_old, args.steps)
