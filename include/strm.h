@@ -21,9 +21,9 @@
  *   - Concurrency: a context is not thread safe; use one context per host thread/stream.
  *
  * Grid (Sections 3.1-3.3): nx*ny*nz nodes; x and z uniform (x_i = (i + 1/2) lx/nx); y nodes at
- * eta_j = (j + 1/2)/ny mapped by y = (ly/2) tanh(beta (2 eta - 1))/tanh(beta) (both walls), by
- * y = ly (1 - tanh(beta (1 - eta))/tanh(beta)) (one wall at y = 0), or uniformly, so that walls
- * at eta = 0 and 1 fall on interfaces (staggered wall). z is periodic; x and y periodic by default.
+ * eta_j = (j + 1/2)/ny mapped by one of the STRM_MAP_* maps (clustered toward both walls,
+ * toward one wall at y = 0, or uniform), so that walls at eta = 0 and 1 fall on interfaces
+ * (staggered wall). z is periodic; x and y periodic by default.
  * Non-dimensional gas: p = rho R T, E = cv T + |u|^2/2, H = E + p/rho, k = cp mu/Pr.
  */
 #ifndef STRM_H
@@ -124,8 +124,8 @@ int strm_init_grid(strm_ctx** ctx, const strm_grid* g, const strm_phys* p, const
  *     boundary layer and a subsonic outflow prescribes only the far-field pressure.
  *   RECYCLE_INFLOW (x-min): ghost plane -1-q copies interior plane i_recycle-q with heights
  *     stretched by delta_r/delta_in, delta_r where the spanwise-mean u of the recycling plane first
- *     reaches 0.99 u_ref (a rescaled recycling inflow; the paper's digital-filter inflow needs a
- *     Reynolds-stress dataset).
+ *     reaches 0.99 u_ref (a rescaled recycling inflow; the paper's own inflow, the digital-filter
+ *     inflow, is set with strm_set_inflow_df).
  *   SHOCK_TOP (y-max, Section 3.3): characteristic face whose reference is, downstream of the
  *     shock foot x_imp - ly/tan(beta), the weak oblique-shock post-shock state of deflection theta.
  * Returns STRM_EINVAL for a wrong face, kind or parameter count. */
