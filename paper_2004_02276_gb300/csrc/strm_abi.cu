@@ -52,7 +52,7 @@ struct Layout {
   bool mixed;
   size_t off_n64[12], off_n32[11];
   size_t off_fh[3];
-  size_t off_R, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
+  size_t off_R, off_grad, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
 };
 
@@ -104,6 +104,9 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   }
   L.off_R = off;
   off = align_up(off + sizeof(double) * 5 * (size_t)d.N);
+  // FP64: the velocity gradients of the sensor, reused by the viscous terms
+  L.off_grad = off;
+  if (!L.mixed) off = align_up(off + sizeof(double) * 9 * (size_t)d.N);
   for (int dir = 0; dir < 3; ++dir) {
     L.off_wl[dir] = off;
     off = align_up(off + sizeof(int) * (size_t)d.nf[dir]);
@@ -117,7 +120,7 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   L.off_scal = off;
   off = align_up(off + sizeof(double) * kScalCount);
   L.off_metric = off;
-  off = align_up(off + sizeof(double) * 6 * (size_t)d.ny);  // 4 metrics, heights, recycle means
+  off = align_up(off + sizeof(double) * 7 * (size_t)d.ny);  // 4 metrics, heights, c1/hy, recycle means
   L.off_metric32 = off;
   off = align_up(off + sizeof(float) * 3 * (size_t)d.ny);
   L.total = off;
@@ -281,7 +284,7 @@ void build_metrics(strm_ctx* x) {
   const strm_grid& g = x->g;
   int ny = g.ny;
   double deta = 1.0 / ny, dx = g.lx / g.nx, dz = g.lz / g.nz;
-  x->metric_host.assign(5 * (size_t)ny, 0.0);
+  x->metric_host.assign(6 * (size_t)ny, 0.0);
   double vt = 0.0;
   for (int j = 0; j < ny; ++j) {
     double eta = (j + 0.5) * deta, ye, yee, h;
@@ -324,6 +327,7 @@ void build_metrics(strm_ctx* x) {
     x->metric_host[2 * ny + j] = yee / (ye * ye * ye * deta);
     x->metric_host[3 * ny + j] = dx * (ye * deta) * dz;
     x->metric_host[4 * ny + j] = h;  // height above the wall eta = 0
+    x->metric_host[5 * ny + j] = yee / (ye * ye);  // c1y / inv_hy: y_etaeta/y_eta^2
     vt += x->metric_host[3 * ny + j];
   }
   x->metric_host32.resize(3 * (size_t)ny);
@@ -521,7 +525,9 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->B.m64.c1y = met + 2 * g->ny;
   x->B.vol = met + 3 * g->ny;
   x->B.hy = met + 4 * g->ny;
-  x->B.ubar = met + 5 * g->ny;
+  x->B.c1h = met + 5 * g->ny;
+  x->B.ubar = met + 6 * g->ny;
+  x->B.grad = L.mixed ? nullptr : (double*)(ws + L.off_grad);
   x->B.m32.inv_hy = met32;
   x->B.m32.c2y = met32 + g->ny;
   x->B.m32.c1y = met32 + 2 * g->ny;
@@ -530,7 +536,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 5 * g->ny,
+    e = cudaMemcpyAsync(met, x->metric_host.data(), sizeof(double) * 6 * g->ny,
                         cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(met32, x->metric_host32.data(), sizeof(float) * 3 * g->ny,

@@ -479,10 +479,21 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
   node_ijk(d, q, i, j, k);
   const Nodes<R>& P = nodes<R>(B);
   R div;
-  R th = theta_node<L, R>(d, C, B, i, j, k, div);
-  long long n = gidx(d, i, j, k);
-  P.theta[n] = th;
-  P.div[n] = div;
+  if constexpr (std::is_same<R, double>::value) {
+    // FP64: the velocity gradients are kept for the viscous terms
+    double g9[9];
+    double th = theta_node<L, double>(d, C, B, i, j, k, div, g9);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) B.grad[c * d.N + q] = g9[c];
+    long long n = gidx(d, i, j, k);
+    P.theta[n] = th;
+    P.div[n] = div;
+  } else {
+    R th = theta_node<L, R>(d, C, B, i, j, k, div);
+    long long n = gidx(d, i, j, k);
+    P.theta[n] = th;
+    P.div[n] = div;
+  }
 }
 
 // ---------------------------------------------------------------------------------- RK, forcing
@@ -988,7 +999,7 @@ __device__ __forceinline__ void body_weno(const Dims& d, const Consts& C, const 
 // d2/dy2 = (f_etaeta - (y_etaeta/y_eta) f_eta)/y_eta^2; d_i(div) from the ghost-filled div.
 template <int L, typename R>
 __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, const Dims& d, long long n,
-                                             int j, R* V) {
+                                             long long q, int j, R* V) {
   const Nodes<R>& P = nodes<R>(B);
   const Coefs<R>& K = coefs<R>(C);
   const Metric<R>& M = metric<R>(B);
@@ -996,28 +1007,54 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
   const R hy = __ldg(M.inv_hy + j), c2 = __ldg(M.c2y + j), c1 = __ldg(M.c1y + j);
   const R* __restrict__ fld[4] = {P.u, P.v, P.w, P.T};
   R du[3][3], lap[3], dT[3], lapT = R(0);
+  if constexpr (std::is_same<R, double>::value) {
+    // FP64: first derivatives of the velocity from the sensor; second derivatives here, with
+    // the eta-derivative of the stretched-y term taken back from d_y u (f_eta / y_eta^2 term
+    // = (y_etaeta / y_eta^2) d_y u)
+    const double c1h = __ldg(B.c1h + j);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    R s1, s2, d0, d1v, d2v, l0;
-    dsum12<L>(fld[a], n, 1, K.a, K.b, s1, s2);
-    d0 = s1 * K.inv_dx;
-    l0 = s2 * K.inv_dx2;
-    dsum12<L>(fld[a], n, sy, K.a, K.b, s1, s2);
-    d1v = s1 * hy;
-    l0 += s2 * c2 - s1 * c1;
-    dsum12<L>(fld[a], n, sz, K.a, K.b, s1, s2);
-    d2v = s1 * K.inv_dz;
-    l0 += s2 * K.inv_dz2;
-    if (a < 3) {
-      du[a][0] = d0;
-      du[a][1] = d1v;
-      du[a][2] = d2v;
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) du[a][b] = __ldg(B.grad + (3 * a + b) * d.N + q);
+      double l0 = dsum2<L>(fld[a], n, 1, K.b) * K.inv_dx2;
+      l0 += dsum2<L>(fld[a], n, sy, K.b) * c2 - du[a][1] * c1h;
+      l0 += dsum2<L>(fld[a], n, sz, K.b) * K.inv_dz2;
       lap[a] = l0;
-    } else {
-      dT[0] = d0;
-      dT[1] = d1v;
-      dT[2] = d2v;
-      lapT = l0;
+    }
+    R s1, s2;
+    dsum12<L>(fld[3], n, 1, K.a, K.b, s1, s2);
+    dT[0] = s1 * K.inv_dx;
+    lapT = s2 * K.inv_dx2;
+    dsum12<L>(fld[3], n, sy, K.a, K.b, s1, s2);
+    dT[1] = s1 * hy;
+    lapT += s2 * c2 - s1 * c1;
+    dsum12<L>(fld[3], n, sz, K.a, K.b, s1, s2);
+    dT[2] = s1 * K.inv_dz;
+    lapT += s2 * K.inv_dz2;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      R s1, s2, d0, d1v, d2v, l0;
+      dsum12<L>(fld[a], n, 1, K.a, K.b, s1, s2);
+      d0 = s1 * K.inv_dx;
+      l0 = s2 * K.inv_dx2;
+      dsum12<L>(fld[a], n, sy, K.a, K.b, s1, s2);
+      d1v = s1 * hy;
+      l0 += s2 * c2 - s1 * c1;
+      dsum12<L>(fld[a], n, sz, K.a, K.b, s1, s2);
+      d2v = s1 * K.inv_dz;
+      l0 += s2 * K.inv_dz2;
+      if (a < 3) {
+        du[a][0] = d0;
+        du[a][1] = d1v;
+        du[a][2] = d2v;
+        lap[a] = l0;
+      } else {
+        dT[0] = d0;
+        dT[1] = d1v;
+        dT[2] = d2v;
+        lapT = l0;
+      }
     }
   }
   R dmu[3], ddiv[3];
@@ -1101,7 +1138,7 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
     }
     if (C.viscous) {
       R V[5];
-      viscous_node<L, R>(C, B, d, gidx(d, i, j, k), j, V);
+      viscous_node<L, R>(C, B, d, gidx(d, i, j, k), q, j, V);
 #pragma unroll
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }

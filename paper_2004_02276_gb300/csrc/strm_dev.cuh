@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace strm {
@@ -92,6 +93,9 @@ struct Bufs {
   Metric<float> m32;
   const double* vol;                            // node volume dx (y_eta deta) dz per j
   const double* hy;                             // node height above the wall eta = 0, per j
+  const double* c1h;                            // y_etaeta / y_eta^2 per j (FP64)
+  double* grad;                                 // FP64: velocity gradients d_b u_a at the
+                                                //   interior nodes, [3a + b][N], from the sensor
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j
   // digital-filter inflow: per j U, V, T and the Cholesky factors a11, a21, a22, a33 of the
   // Reynolds stresses ([7][ny]), and the time-correlated fluctuation plane [3][nz][ny]
@@ -142,6 +146,15 @@ __device__ __forceinline__ R viscosity(const Coefs<R>& K, int law, R T) {
   return K.mu_ref * rpow(tr, K.visc_exp);
 }
 
+// sum_l b_l (f_{+l} + f_{-l} - 2 f_0) along a line (second-derivative numerator of order 2L)
+template <int L, typename R>
+__device__ __forceinline__ R dsum2(const R* __restrict__ f, long long n, long long st, const R* b) {
+  R f0 = __ldg(f + n), s2 = R(0);
+#pragma unroll
+  for (int l = 1; l <= L; ++l) s2 += b[l] * ((__ldg(f + n + l * st) + __ldg(f + n - l * st)) - R(2) * f0);
+  return s2;
+}
+
 // sum_l a_l (f_{+l} - f_{-l}) along a line (first-derivative numerator of order 2L)
 template <int L, typename R>
 __device__ __forceinline__ R dsum(const R* __restrict__ f, long long n, long long st, const R* a) {
@@ -171,7 +184,7 @@ __device__ __forceinline__ void dsum12(const R* __restrict__ f, long long n, lon
 // |curl u|^2 + (u0/L0)^2), 0), first derivatives of order 2L in precision R; div is returned too.
 template <int L, typename R>
 __device__ __forceinline__ R theta_node(const Dims& d, const Consts& C, const Bufs& B, int i, int j,
-                                        int k, R& div) {
+                                        int k, R& div, R* g9 = nullptr) {
   const Nodes<R>& P = nodes<R>(B);
   const Coefs<R>& K = coefs<R>(C);
   long long n = gidx(d, i, j, k);
@@ -187,6 +200,11 @@ __device__ __forceinline__ R theta_node(const Dims& d, const Consts& C, const Bu
   R wy = dsum<L>(P.w, n, sy, K.a) * hy;
   R wz = dsum<L>(P.w, n, sz, K.a) * K.inv_dz;
   div = ux + vy + wz;
+  if (g9) {  // d_b u_a, a = u, v, w
+    g9[0] = ux; g9[1] = uy; g9[2] = uz;
+    g9[3] = vx; g9[4] = vy; g9[5] = vz;
+    g9[6] = wx; g9[7] = wy; g9[8] = wz;
+  }
   R o1 = wy - vz, o2 = uz - wx, o3 = vx - uy;
   R den = sqrt(div * div + (o1 * o1 + o2 * o2 + o3 * o3) + K.sens_eps);
   R th = -div / den;
