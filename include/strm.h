@@ -153,7 +153,9 @@ int strm_advance_n_host(strm_ctx* ctx, double* w_host, double* w, double* r_old,
  * Returns STRM_ENONFINITE if any total is NaN or Inf. */
 int strm_conserved_totals(strm_ctx* ctx, const double* w, double out_host[5]);
 
-/* Simulated time accumulated by strm_rk_step/strm_advance_n and the last dt. Synchronises. */
+/* Simulated time accumulated by strm_rk_step/strm_advance_n and the last dt. Synchronises.
+ * Returns STRM_ENONFINITE (outputs still written) when either is NaN or Inf: the CFL maximum
+ * propagates a non-finite state into dt, so this is the cheap health check after a run. */
 int strm_get_time(strm_ctx* ctx, double* t_host, double* dt_host);
 
 /* Set the simulated time (and reset the last dt to 0). Stream-ordered. */

@@ -909,6 +909,9 @@ int strm_get_time(strm_ctx* x, double* t_host, double* dt_host) {
   STRM_CK(cudaStreamSynchronize(x->stream));
   if (t_host) *t_host = v[0];
   if (dt_host) *dt_host = v[1];
+  // a non-finite state makes the CFL maximum, hence dt and the time, non-finite
+  if (!std::isfinite(v[0]) || !std::isfinite(v[1]))
+    return fail(STRM_ENONFINITE, "non-finite time step: the state is not finite");
   return STRM_OK;
 }
 

@@ -164,6 +164,12 @@ def test_nonfinite_state_is_reported():
     with pytest.raises(binding.StrmError) as e:
         s.totals(gpu(w0))
     assert e.value.code == -3
+    # a CFL step on the bad state: dt and the time become NaN and get_time reports it
+    w = gpu(w0)
+    s.advance_n(w, torch.zeros_like(w), 2, cfl=0.8)
+    with pytest.raises(binding.StrmError) as e:
+        s.time()
+    assert e.value.code == -3
     s.close()
 
 
