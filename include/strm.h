@@ -274,6 +274,20 @@ int strm_ensemble_create(strm_ensemble** ens, int n, const strm_grid* grids, con
                          const strm_scheme* schemes, const int* bc_y, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/* Boundary kind of a face of instance e (as strm_set_bc on a single context: characteristic,
+ * recycling inflow, shock top, ...), so that channel and boundary-layer instances advance
+ * together. Takes effect at the next strm_ensemble_advance (the step graph is re-captured). */
+int strm_ensemble_set_bc(strm_ensemble* ens, int e, int face, int kind, const double* params,
+                         int nparams);
+
+/* Device bytes of the inflow buffer of instance e (0 if invalid). */
+size_t strm_ensemble_inflow_df_bytes(const strm_ensemble* ens, int e, const strm_df* df);
+
+/* Digital-filter inflow of instance e (as strm_set_inflow_df; the caller-owned buffer serves that
+ * instance). */
+int strm_ensemble_set_inflow_df(strm_ensemble* ens, int e, const strm_df* df,
+                                const double* profiles_host, void* buffer, size_t bytes);
+
 /* nsteps RK3 steps of every instance (dt > 0 fixed for all, else each instance takes its own CFL
  * step with number cfl). w and r_old are host arrays of n device pointers (layout as for a
  * single grid, sized by each instance's grid). */

@@ -92,6 +92,9 @@ SIGNATURES = {
     "strm_conserved_totals_static": ([_P(Grid), _vp, _P(_d), _vp], _i),
     "strm_ensemble_workspace_bytes": ([_i, _P(Grid), _P(Scheme)], _sz),
     "strm_ensemble_create": ([_P(_vp), _i, _P(Grid), _P(Phys), _P(Scheme), _P(_i), _vp, _sz, _vp], _i),
+    "strm_ensemble_set_bc": ([_vp, _i, _i, _i, _vp, _i], _i),
+    "strm_ensemble_inflow_df_bytes": ([_vp, _i, _P(DF)], _sz),
+    "strm_ensemble_set_inflow_df": ([_vp, _i, _P(DF), _P(_d), _vp, _sz], _i),
     "strm_ensemble_advance": ([_vp, _P(_vp), _P(_vp), _i, _d, _d], _i),
     "strm_ensemble_tune": ([_vp, _P(_vp), _P(_vp), _P(_i)], _i),
     "strm_ensemble_totals": ([_vp, _P(_vp), _P(_d)], _i),
@@ -367,11 +370,13 @@ class Solver:
 class Ensemble:
     """Many independent grids advanced together by the batched kernels of the library.
 
-    ``cases`` is a list of workload descriptions sharing L and precision. State tensors are
-    lists of float64 CUDA tensors, one [5, nz, ny, nx] tensor per instance.
+    ``cases`` is a list of workload descriptions sharing L and precision: channels and
+    boundary layers alike (every face kind of a single context). ``inflows`` maps the index of
+    an instance with a digital-filter inflow to its [7, ny] profiles. State tensors are lists of
+    float64 CUDA tensors, one [5, nz, ny, nx] tensor per instance.
     """
 
-    def __init__(self, cases, device=None, stream=None):
+    def __init__(self, cases, device=None, stream=None, inflows=None):
         self.cases = list(cases)
         n = len(self.cases)
         self.device = torch.device(device if device is not None else "cuda")
@@ -391,6 +396,26 @@ class Ensemble:
             ctypes.byref(ens), n, self.grids, self.phys, self.schemes, self.bc,
             _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream)))
         self.ens = ens
+        self._df_bufs = {}
+        inflows = inflows or {}
+        for e, c in enumerate(self.cases):
+            for face, kind, params in face_settings(c):
+                arr = (ctypes.c_double * len(params))(*params) if params else None
+                _check("strm_ensemble_set_bc", L.strm_ensemble_set_bc(
+                    self.ens, e, face, kind, arr, len(params) if params else 0))
+            if getattr(c, "bc_xmin", None) == "df":
+                if e not in inflows:
+                    raise ValueError(f"instance {e} has a digital-filter inflow but no profiles")
+                prof = np.ascontiguousarray(inflows[e], dtype=np.float64)
+                df = DF(c.ref[4], c.df_ny, c.df_nz, c.df_tau, c.df_seed)
+                nb = L.strm_ensemble_inflow_df_bytes(self.ens, e, ctypes.byref(df))
+                if nb == 0:
+                    raise StrmError("strm_ensemble_inflow_df_bytes", -1, "invalid inflow parameters")
+                buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+                self._df_bufs[e] = buf
+                _check("strm_ensemble_set_inflow_df", L.strm_ensemble_set_inflow_df(
+                    self.ens, e, ctypes.byref(df), prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    _ptr(buf), nb))
 
     def empty(self):
         return [torch.empty((5, c.nz, c.ny, c.nx), dtype=torch.float64, device=self.device)

@@ -994,6 +994,12 @@ void strm::ctx_parts(strm_ctx* x, Dims* d, Consts* C, Bufs* B, int* sms) {
   *sms = x->weno_grid / 8;
 }
 
+bool strm::ctx_df(strm_ctx* x, DFParams* F) {
+  if (x->C.bc[0] != kBcDigitalFilter) return false;
+  *F = x->df;
+  return true;
+}
+
 extern "C" {
 
 void strm_destroy(strm_ctx* x) {

@@ -197,6 +197,7 @@ struct strm_ensemble {
   int L = 3;
   bool mixed = false;
   bool any_recycle = false;
+  bool dirty = false;  // an instance's constants changed since the table upload
   cudaStream_t stream = nullptr;
   int sms = 0;
   std::vector<strm_ctx*> ctx;
@@ -238,6 +239,12 @@ void enqueue_rhs_t(const strm_ensemble* E, bool dt_mode, double cfl, double dt_f
     kb_recycle_mean<<<E->total_blocks[kKindRow], 256, 0, st>>>(X);
     kb_recycle_scale<<<E->n, 32, 0, st>>>(X);
   }
+  // digital-filter inflows: a new plane per step for each instance that has one
+  if (dt_mode)
+    for (int e = 0; e < E->n; ++e) {
+      DFParams F;
+      if (ctx_df(E->ctx[e], &F)) launch_df_update(E->inst_host[e].d, F, E->inst_host[e].B, false, st);
+    }
   kb_ghost_prims<<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
   kb_sensor<L, R><<<E->total_blocks[kKindNode], 256, 0, st>>>(X);
   kb_ghost_scalars<R><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
@@ -279,7 +286,7 @@ int enqueue_step(const strm_ensemble* E, double dt, double cfl, cudaStream_t st)
 
 // Point the instance table at the caller's state buffers (re-uploaded only when they change).
 int bind_states(strm_ensemble* E, double* const* w, double* const* r_old) {
-  bool same = E->g_w.size() == (size_t)E->n;
+  bool same = !E->dirty && E->g_w.size() == (size_t)E->n;
   for (int e = 0; e < E->n && same; ++e) same = E->g_w[e] == w[e] && E->g_r[e] == r_old[e];
   if (same) return STRM_OK;
   for (int e = 0; e < E->n; ++e) {
@@ -293,11 +300,32 @@ int bind_states(strm_ensemble* E, double* const* w, double* const* r_old) {
   STRME_CK(cudaStreamSynchronize(E->stream));
   E->g_w.assign(w, w + E->n);
   E->g_r.assign(r_old, r_old + E->n);
+  E->dirty = false;
   if (E->gexec) {
     cudaGraphExecDestroy(E->gexec);
     E->gexec = nullptr;
   }
   return STRM_OK;
+}
+
+// Refresh the host copy of instance e's constants and buffers after a boundary change; the
+// device table is re-uploaded before the next launch and the step graph re-captured.
+void refresh_instance(strm_ensemble* E, int e) {
+  Inst& I = E->inst_host[e];
+  double* w = I.w;
+  double* r = I.r_old;
+  int sms;
+  ctx_parts(E->ctx[e], &I.d, &I.C, &I.B, &sms);
+  I.w = w;
+  I.r_old = r;
+  E->any_recycle = false;
+  for (const Inst& J : E->inst_host)
+    if (J.C.bc[0] == kBcRecycle) E->any_recycle = true;
+  E->dirty = true;
+  if (E->gexec) {
+    cudaGraphExecDestroy(E->gexec);
+    E->gexec = nullptr;
+  }
 }
 
 size_t table_bytes(int n) { return align256(sizeof(Inst) * (size_t)n) + align256(sizeof(int) * kKinds * (n + 1)); }
@@ -387,11 +415,37 @@ int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, con
   return STRM_OK;
 }
 
+int strm_ensemble_set_bc(strm_ensemble* E, int e, int face, int kind, const double* params, int nparams) {
+  if (!E || e < 0 || e >= E->n) return record_error(STRM_EINVAL, "null ensemble or instance out of range");
+  int rc = strm_set_bc(E->ctx[e], face, kind, params, nparams);
+  if (rc) return rc;
+  refresh_instance(E, e);
+  return STRM_OK;
+}
+
+size_t strm_ensemble_inflow_df_bytes(const strm_ensemble* E, int e, const strm_df* df) {
+  if (!E || e < 0 || e >= E->n) return 0;
+  return strm_inflow_df_bytes(E->ctx[e], df);
+}
+
+int strm_ensemble_set_inflow_df(strm_ensemble* E, int e, const strm_df* df, const double* profiles_host,
+                                void* buffer, size_t bytes) {
+  if (!E || e < 0 || e >= E->n) return record_error(STRM_EINVAL, "null ensemble or instance out of range");
+  int rc = strm_set_inflow_df(E->ctx[e], df, profiles_host, buffer, bytes);
+  if (rc) return rc;
+  refresh_instance(E, e);
+  return STRM_OK;
+}
+
 int strm_ensemble_advance(strm_ensemble* E, double* const* w, double* const* r_old, int nsteps, double dt,
                           double cfl) {
   if (!E || !w || !r_old) return record_error(STRM_EINVAL, "null ensemble or state table");
   if (nsteps < 0) return record_error(STRM_EINVAL, "nsteps < 0");
   if (!(dt > 0.0) && !(cfl > 0.0)) return record_error(STRM_EINVAL, "need dt > 0 or cfl > 0");
+  for (const Inst& I : E->inst_host)
+    if ((I.C.bc[0] == kBcPeriodic) != (I.C.bc[1] == kBcPeriodic) ||
+        (I.C.bc[2] == kBcPeriodic) != (I.C.bc[3] == kBcPeriodic))
+      return record_error(STRM_EINVAL, "an instance has a periodic face opposite a non-periodic one");
   int rc = bind_states(E, w, r_old);
   if (rc) return rc;
   if (nsteps == 0) return STRM_OK;

@@ -41,6 +41,8 @@ struct DFParams {
 };
 // draw and filter one plane and blend it into Psi (first: Psi = the plane)
 void launch_df_update(const Dims& d, const DFParams& F, const Bufs& B, bool first, cudaStream_t s);
+// the digital-filter inflow of a context, if its x-min face has one
+bool ctx_df(strm_ctx* x, DFParams* F);
 // one statistics sample of w: mode 0 adds x-z means to acc[24][ny] (scr holds [24][ny][nx]
 // column sums), mode 1 adds z means to acc[24][ny][nx]
 void launch_stats(const Dims& d, const Consts& C, const double* w, double* acc, double* scr, int mode,

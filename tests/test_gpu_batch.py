@@ -96,3 +96,45 @@ def test_ensemble_workload_draws():
     assert len(cases) == 64
     assert all(32 <= c.nx <= 192 and 32 <= c.ny <= 128 and 32 <= c.nz <= 128 for c in cases)
     assert all(0.3 <= c.mach <= 3.0 and 2000 <= c.reynolds <= 8000 for c in cases)
+
+
+def bl_bag(precision):
+    """Channel and boundary-layer instances together: recycling inflow, oblique shock, digital-
+    filter inflow, characteristic faces on every side."""
+    return [
+        inputs.Case(nx=40, ny=24, nz=18, mach=0.5, reynolds=2500.0, precision=precision),
+        inputs.bl_case("bl-48x40x12", 48, 40, 12, 7.0, 6.0, 1.5, precision=precision),
+        inputs.bl_case("sbli-64x40x12", 64, 40, 12, 12.0, 6.0, 1.5, shock=True, noise=0.003,
+                       precision=precision),
+        inputs.bl_case("bl-df-36x30x10", 36, 30, 10, 5.0, 6.0, 1.5, bc_xmin="df", df_ny=2, df_nz=2,
+                       df_tau=0.3, df_seed=3, precision=precision),
+        inputs.bl_case("open-40x24x10", 40, 24, 10, 6.0, 6.0, 1.5, bc_xmin="char", bc_ymin="char",
+                       weno_mode="all", precision=precision),
+    ]
+
+
+def initial(c):
+    return inputs.channel_state(c, seed=c.nx) if c.kind == "channel" else inputs.bl_state(c, seed=c.nx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_with_boundary_layer_instances(precision):
+    cases = bl_bag(precision)
+    inflows = {e: inputs.df_profiles(c) for e, c in enumerate(cases) if c.bc_xmin == "df"}
+    ref, tref = [], []
+    for e, c in enumerate(cases):
+        s = binding.Solver(c, inflow=inflows.get(e))
+        w = torch.from_numpy(initial(c)).cuda()
+        s.advance_n(w, torch.zeros_like(w), 4, cfl=0.8)
+        ref.append(w.cpu().numpy())
+        tref.append(s.time()[0])
+        s.close()
+    E = binding.Ensemble(cases, inflows=inflows)
+    ws = [torch.from_numpy(initial(c)).cuda() for c in cases]
+    rs = [torch.zeros_like(w) for w in ws]
+    E.advance(ws, rs, 4, cfl=0.8)
+    errs = [rel_max(ws[e].cpu().numpy(), ref[e]) for e in range(len(cases))]
+    print(precision, "boundary-layer ensemble vs independent contexts:", max(errs))
+    assert max(errs) <= TOL[precision], errs
+    np.testing.assert_allclose(E.times(), tref, rtol=1e-13)
+    E.close()
