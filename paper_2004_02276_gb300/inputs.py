@@ -291,3 +291,25 @@ def ensemble_cases(seed: int = 0, n: int = 64, precision: str = "fp64") -> list:
         cases.append(Case(name=f"ensemble-{e}", nx=nx, ny=ny, nz=nz, mach=mach, reynolds=re,
                           precision=precision, seed=seed * 1000 + e))
     return cases
+
+
+def ensemble_bl_cases(seed: int = 0, n: int = 32, precision: str = "fp64") -> list:
+    """Boundary-layer instances for a mixed ensemble: grid dimensions from {64..192} x {32..128}
+    x {32..96} on a box of 3 x 12 x 3 delta_in per 64 x 128 x 64 nodes (the aspect of the
+    1024x256x256 workload), free-stream Mach number from U[1.5, 3.0], and, in turn, a recycling
+    inflow, a recycling inflow under the 8-degree shock, and a digital-filter inflow."""
+    r = uniform(seed + 7, (n, 4))
+    cases = []
+    for e in range(n):
+        nx = 64 + int(r[e, 0] * 129)
+        ny = 32 + int(r[e, 1] * 97)
+        nz = 32 + int(r[e, 2] * 65)
+        mach = 1.5 + 1.5 * r[e, 3]
+        kind = e % 3
+        kw = dict(mach=mach, precision=precision, seed=seed * 1000 + 500 + e, noise=0.01)
+        if kind == 1:
+            kw.update(shock=True)
+        if kind == 2:
+            kw.update(bc_xmin="df", df_ny=3, df_nz=3, df_tau=0.5, df_seed=seed * 1000 + e)
+        cases.append(bl_case(f"ensemble-bl-{e}", nx, ny, nz, 3.0 * nx / 64, 12.0, 3.0 * nz / 64, **kw))
+    return cases
