@@ -213,3 +213,35 @@ def test_c2_full_size_rhs_and_step_match_oracle():
     s.close()
     assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
     assert abs(t1[1] - t0[1]) <= 1e-13 * t0[1]
+
+
+@pytest.mark.parametrize("weno_mode", ["off", "sensor", "all"])
+def test_free_stream_preserved(weno_mode):
+    """A uniform state on the stretched periodic grid (the metric terms must cancel) gives a zero
+    right-hand side to round-off, whatever the switch, as the oracle's pin requires."""
+    case = inputs.Case(nx=20, ny=24, nz=12, y_wall=False, forcing=False, weno_mode=weno_mode, beta=2.0)
+    cv = case.r_gas / (case.gamma - 1.0)
+    rho, u, v, w, T = 1.2, 0.7, -0.2, 0.3, 1.1
+    st = np.empty((5, case.nz, case.ny, case.nx))
+    st[0], st[1], st[2], st[3] = rho, rho * u, rho * v, rho * w
+    st[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    s = binding.Solver(case)
+    r = s.compute_rhs(gpu(st)).cpu().numpy()
+    s.close()
+    assert np.abs(r).max() < 1e-12
+
+
+def test_free_stream_preserved_with_open_faces():
+    """Characteristic faces on all four x/y sides around a uniform free stream: R = 0."""
+    case = inputs.bl_case("open-free", 20, 16, 8, 4.0, 6.0, 1.0, bc_xmin="char", bc_ymin="char",
+                          weno_mode="all")
+    cv = case.r_gas / (case.gamma - 1.0)
+    rho, u, v, w, p = case.ref
+    T = p / (rho * case.r_gas)
+    st = np.empty((5, case.nz, case.ny, case.nx))
+    st[0], st[1], st[2], st[3] = rho, rho * u, rho * v, rho * w
+    st[4] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    s = binding.Solver(case)
+    r = s.compute_rhs(gpu(st)).cpu().numpy()
+    s.close()
+    assert np.abs(r).max() < 1e-12
