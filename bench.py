@@ -288,7 +288,7 @@ def run_ours(args, world, rank, local):
         "clocks": m64["clocks"],
         "hbm_step": hbm_step(m64["value"]),
     }
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:  # the oracle baseline: N = 1 only
         rate, sec, w_ref, cores = cpu_sample(case)
         # the same first step on the GPU, for the error at which the figure holds
         wg = torch.from_numpy(w0).cuda()
