@@ -221,12 +221,13 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
   for (int l = 0; l < 4; ++l) K.a[l] = K.b[l] = R(0);
   // central coefficients of order 2L: first derivative a_l, second derivative b_l with
   // f'' ~ sum_l b_l (f_{+l} + f_{-l} - 2 f_0)/h^2 (Section 2.1)
+  // b_0 = -2 sum_l b_l is the centre weight of the same stencil written as sum_l b_l f_l
   if (s.L == 3) {
     K.a[1] = R(3.0 / 4.0); K.a[2] = R(-3.0 / 20.0); K.a[3] = R(1.0 / 60.0);
-    K.b[1] = R(3.0 / 2.0); K.b[2] = R(-3.0 / 20.0); K.b[3] = R(1.0 / 90.0);
+    K.b[0] = R(-49.0 / 18.0); K.b[1] = R(3.0 / 2.0); K.b[2] = R(-3.0 / 20.0); K.b[3] = R(1.0 / 90.0);
   } else {
     K.a[1] = R(2.0 / 3.0); K.a[2] = R(-1.0 / 12.0);
-    K.b[1] = R(4.0 / 3.0); K.b[2] = R(-1.0 / 12.0);
+    K.b[0] = R(-5.0 / 2.0); K.b[1] = R(4.0 / 3.0); K.b[2] = R(-1.0 / 12.0);
   }
   double dx = g.lx / g.nx, dz = g.lz / g.nz;
   K.inv_dx = R(1.0 / dx);

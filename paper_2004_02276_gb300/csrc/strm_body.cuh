@@ -1016,19 +1016,19 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) du[a][b] = __ldg(B.grad + (3 * a + b) * d.N + q);
-      double l0 = dsum2<L>(fld[a], n, 1, K.b) * K.inv_dx2;
-      l0 += dsum2<L>(fld[a], n, sy, K.b) * c2 - du[a][1] * c1h;
-      l0 += dsum2<L>(fld[a], n, sz, K.b) * K.inv_dz2;
+      double l0 = dsum2_c<L>(fld[a], n, 1, K.b) * K.inv_dx2;
+      l0 += dsum2_c<L>(fld[a], n, sy, K.b) * c2 - du[a][1] * c1h;
+      l0 += dsum2_c<L>(fld[a], n, sz, K.b) * K.inv_dz2;
       lap[a] = l0;
     }
     R s1, s2;
-    dsum12<L>(fld[3], n, 1, K.a, K.b, s1, s2);
+    dsum12_c<L>(fld[3], n, 1, K.a, K.b, s1, s2);
     dT[0] = s1 * K.inv_dx;
     lapT = s2 * K.inv_dx2;
-    dsum12<L>(fld[3], n, sy, K.a, K.b, s1, s2);
+    dsum12_c<L>(fld[3], n, sy, K.a, K.b, s1, s2);
     dT[1] = s1 * hy;
     lapT += s2 * c2 - s1 * c1;
-    dsum12<L>(fld[3], n, sz, K.a, K.b, s1, s2);
+    dsum12_c<L>(fld[3], n, sz, K.a, K.b, s1, s2);
     dT[2] = s1 * K.inv_dz;
     lapT += s2 * K.inv_dz2;
   } else {
