@@ -230,6 +230,10 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
     K.b[0] = R(-5.0 / 2.0); K.b[1] = R(4.0 / 3.0); K.b[2] = R(-1.0 / 12.0);
   }
   double dx = g.lx / g.nx, dz = g.lz / g.nz;
+  for (int l = 0; l < 4; ++l) {
+    K.ax[l] = R((double)K.a[l] / dx);
+    K.az[l] = R((double)K.a[l] / dz);
+  }
   K.inv_dx = R(1.0 / dx);
   K.inv_dz = R(1.0 / dz);
   K.inv_dx2 = R((1.0 / dx) * (1.0 / dx));

@@ -1022,27 +1022,27 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
       lap[a] = l0;
     }
     R s1, s2;
-    dsum12_c<L>(fld[3], n, 1, K.a, K.b, s1, s2);
-    dT[0] = s1 * K.inv_dx;
+    dsum12_c<L>(fld[3], n, 1, K.ax, K.b, s1, s2);
+    dT[0] = s1;
     lapT = s2 * K.inv_dx2;
     dsum12_c<L>(fld[3], n, sy, K.a, K.b, s1, s2);
     dT[1] = s1 * hy;
     lapT += s2 * c2 - s1 * c1;
-    dsum12_c<L>(fld[3], n, sz, K.a, K.b, s1, s2);
-    dT[2] = s1 * K.inv_dz;
+    dsum12_c<L>(fld[3], n, sz, K.az, K.b, s1, s2);
+    dT[2] = s1;
     lapT += s2 * K.inv_dz2;
   } else {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       R s1, s2, d0, d1v, d2v, l0;
-      dsum12<L>(fld[a], n, 1, K.a, K.b, s1, s2);
-      d0 = s1 * K.inv_dx;
+      dsum12<L>(fld[a], n, 1, K.ax, K.b, s1, s2);
+      d0 = s1;
       l0 = s2 * K.inv_dx2;
       dsum12<L>(fld[a], n, sy, K.a, K.b, s1, s2);
       d1v = s1 * hy;
       l0 += s2 * c2 - s1 * c1;
-      dsum12<L>(fld[a], n, sz, K.a, K.b, s1, s2);
-      d2v = s1 * K.inv_dz;
+      dsum12<L>(fld[a], n, sz, K.az, K.b, s1, s2);
+      d2v = s1;
       l0 += s2 * K.inv_dz2;
       if (a < 3) {
         du[a][0] = d0;
@@ -1058,12 +1058,12 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
     }
   }
   R dmu[3], ddiv[3];
-  dmu[0] = dsum<L>(P.mu, n, 1, K.a) * K.inv_dx;
+  dmu[0] = dsum<L>(P.mu, n, 1, K.ax);
   dmu[1] = dsum<L>(P.mu, n, sy, K.a) * hy;
-  dmu[2] = dsum<L>(P.mu, n, sz, K.a) * K.inv_dz;
-  ddiv[0] = dsum<L>(P.div, n, 1, K.a) * K.inv_dx;
+  dmu[2] = dsum<L>(P.mu, n, sz, K.az);
+  ddiv[0] = dsum<L>(P.div, n, 1, K.ax);
   ddiv[1] = dsum<L>(P.div, n, sy, K.a) * hy;
-  ddiv[2] = dsum<L>(P.div, n, sz, K.a) * K.inv_dz;
+  ddiv[2] = dsum<L>(P.div, n, sz, K.az);
   const R mu = __ldg(P.mu + n);
   const R div = du[0][0] + du[1][1] + du[2][2];
   const R tdiv = R(2.0 / 3.0) * div;

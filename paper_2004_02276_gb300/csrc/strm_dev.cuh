@@ -47,6 +47,7 @@ struct Metric {
 template <typename R>
 struct Coefs {
   R a[4], b[4];                      // central first/second-derivative coefficients, 1..L
+  R ax[4], az[4];                    // a_l / dx and a_l / dz (first derivatives along x and z)
   R inv_dx, inv_dz, inv_dx2, inv_dz2;
   R cp_pr, sens_eps, theta_thr, weno_eps;
   R gamma, gm1, r_gas, cp, t_wall, mu_ref, inv_tref, visc_exp, suth_s;
@@ -216,15 +217,15 @@ __device__ __forceinline__ R theta_node(const Dims& d, const Consts& C, const Bu
   long long n = gidx(d, i, j, k);
   long long sy = d.px, sz = d.plane;
   R hy = metric<R>(B).inv_hy[j];
-  R ux = dsum<L>(P.u, n, 1, K.a) * K.inv_dx;
+  R ux = dsum<L>(P.u, n, 1, K.ax);
   R uy = dsum<L>(P.u, n, sy, K.a) * hy;
-  R uz = dsum<L>(P.u, n, sz, K.a) * K.inv_dz;
-  R vx = dsum<L>(P.v, n, 1, K.a) * K.inv_dx;
+  R uz = dsum<L>(P.u, n, sz, K.az);
+  R vx = dsum<L>(P.v, n, 1, K.ax);
   R vy = dsum<L>(P.v, n, sy, K.a) * hy;
-  R vz = dsum<L>(P.v, n, sz, K.a) * K.inv_dz;
-  R wx = dsum<L>(P.w, n, 1, K.a) * K.inv_dx;
+  R vz = dsum<L>(P.v, n, sz, K.az);
+  R wx = dsum<L>(P.w, n, 1, K.ax);
   R wy = dsum<L>(P.w, n, sy, K.a) * hy;
-  R wz = dsum<L>(P.w, n, sz, K.a) * K.inv_dz;
+  R wz = dsum<L>(P.w, n, sz, K.az);
   div = ux + vy + wz;
   if (g9) {  // d_b u_a, a = u, v, w
     g9[0] = ux; g9[1] = uy; g9[2] = uz;
