@@ -45,12 +45,12 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Node fields held in FP64 (all of them in FP64 precision; those the FP64 characteristic
 // projection reads in mixed precision) and in FP32 (mixed precision only).
-const int kN64All = 12, kN64Mixed = 8, kN32Mixed = 11;
+const int kN64All = 18, kN64Mixed = 8, kN32Mixed = 11;  // FP64: 12 fields and the 6 wave speeds u_d -+ c
 
 struct Layout {
   Dims d;
   bool mixed;
-  size_t off_n64[12], off_n32[11];
+  size_t off_n64[kN64All], off_n32[kN32Mixed];
   size_t off_fh[3];
   size_t off_R, off_grad, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
@@ -509,9 +509,10 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
                               &N32.H,   &N32.c, &N32.mu, &N32.theta, &N32.div};
     for (int f = 0; f < kN32Mixed; ++f) *f32[f] = (float*)(ws + L.off_n32[f]);
   } else {
-    double** f64[kN64All] = {&N64.rho, &N64.u, &N64.v,  &N64.w,     &N64.p,   &N64.T,
-                             &N64.H,   &N64.c, &N64.mu, &N64.theta, &N64.div, &N64.srho};
-    for (int f = 0; f < kN64All; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
+    double** f64[12] = {&N64.rho, &N64.u, &N64.v,  &N64.w,     &N64.p,   &N64.T,
+                        &N64.H,   &N64.c, &N64.mu, &N64.theta, &N64.div, &N64.srho};
+    for (int f = 0; f < 12; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
+    for (int f = 0; f < 6; ++f) x->B.lam[f] = (double*)(ws + L.off_n64[12 + f]);
   }
   for (int dir = 0; dir < 3; ++dir) {
     x->B.fh64[dir] = L.mixed ? nullptr : (double*)(ws + L.off_fh[dir]);

@@ -46,6 +46,12 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
     P.p[n] = p;
     P.H[n] = E + p * ir;
     P.c[n] = c;
+    B.lam[0][n] = u - c;
+    B.lam[1][n] = u + c;
+    B.lam[2][n] = v - c;
+    B.lam[3][n] = v + c;
+    B.lam[4][n] = ww - c;
+    B.lam[5][n] = ww + c;
     P.mu[n] = viscosity(C.k64, C.visc_law, T);
     P.srho[n] = rho * rs;
     if (want_cfl)
@@ -200,7 +206,14 @@ __device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, lon
   P.H[dst] = H;
   P.srho[dst] = sqrt(g.rho);
   if (!C.mixed) {
-    P.c[dst] = sqrt(C.gamma * g.p / g.rho);
+    double c = sqrt(C.gamma * g.p / g.rho);
+    P.c[dst] = c;
+    B.lam[0][dst] = g.u - c;
+    B.lam[1][dst] = g.u + c;
+    B.lam[2][dst] = g.v - c;
+    B.lam[3][dst] = g.v + c;
+    B.lam[4][dst] = g.w - c;
+    B.lam[5][dst] = g.w + c;
     P.mu[dst] = viscosity(C.k64, C.visc_law, g.T);
   } else {
     const Nodes<float>& F = B.n32;
@@ -235,7 +248,12 @@ __device__ __forceinline__ void copy_node(const Nodes<R>& P, long long dst, long
 __device__ __forceinline__ void copy_ghost(const Consts& C, const Bufs& B, long long dst, long long src) {
   copy_node(B.n64, dst, src, !C.mixed);
   B.n64.srho[dst] = B.n64.srho[src];
-  if (C.mixed) copy_node(B.n32, dst, src, true);
+  if (C.mixed) {
+    copy_node(B.n32, dst, src, true);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) B.lam[f][dst] = B.lam[f][src];
+  }
 }
 
 // Isothermal no-slip staggered wall: the ghost mirrors an interior node across the wall
@@ -708,13 +726,14 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 
   // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
   long long m0 = 0, m1 = 0, m4 = 0;
+  const double* __restrict__ lm = B.lam[2 * DIR];      // u_n - c at the nodes
+  const double* __restrict__ lp = B.lam[2 * DIR + 1];  // u_n + c
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    double un = __ldg(un_p + nn), cs = __ldg(P.c + nn);
-    m0 = max_bits(m0, un - cs);
-    m1 = max_bits(m1, un);
-    m4 = max_bits(m4, un + cs);
+    m0 = max_bits(m0, __ldg(lm + nn));
+    m1 = max_bits(m1, __ldg(un_p + nn));
+    m4 = max_bits(m4, __ldg(lp + nn));
   }
   const double lam0 = __longlong_as_double(m0), lam1 = __longlong_as_double(m1),
                lam4 = __longlong_as_double(m4);

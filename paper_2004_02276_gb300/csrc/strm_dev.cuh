@@ -95,6 +95,8 @@ struct Bufs {
   const double* vol;                            // node volume dx (y_eta deta) dz per j
   const double* hy;                             // node height above the wall eta = 0, per j
   const double* c1h;                            // y_etaeta / y_eta^2 per j (FP64)
+  double* lam[6];                               // FP64: u - c, u + c, v - c, v + c, w - c, w + c
+                                                //   at the nodes (ghosted), for the LF speeds
   double* grad;                                 // FP64: velocity gradients d_b u_a at the
                                                 //   interior nodes, [3a + b][N], from the sensor
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j
