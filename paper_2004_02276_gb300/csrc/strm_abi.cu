@@ -233,6 +233,7 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
   for (int l = 0; l < 4; ++l) {
     K.ax[l] = R((double)K.a[l] / dx);
     K.az[l] = R((double)K.a[l] / dz);
+    K.aq[l] = R(0.25 * (double)K.a[l]);
   }
   K.inv_dx = R(1.0 / dx);
   K.inv_dz = R(1.0 / dz);

@@ -581,37 +581,31 @@ __device__ __forceinline__ void face_node(const Dims& d, long long q, int& i, in
 // ------------------------------------------------------------------------------ central flux
 
 // Energy-consistent split flux at the face between nodes n and n+st (Eqs. avg_operator,
-// encflux): f_phi = 2 sum_l a_l sum_{m<l} (rho, u_n, phi)~_{n-m,l}. With
-// qq = (rho_a + rho_b)(u_a + u_b)/4 this is sum_l a_l sum_m qq (phi_a + phi_b); the pressure
-// enters the normal momentum as sum_l a_l sum_m (p_a + p_b). R is the arithmetic precision.
+// encflux): f_phi = 2 sum_l a_l sum_{m<l} (rho, u_n, phi)~_{n-m,l}. With the pair weight
+// q = a_l (rho_a + rho_b)(u_a + u_b)/4 this is sum_{l,m} q (phi_a + phi_b) (the 1/4 is carried in
+// the coefficients a_l/4, and f_rho = 2 sum q); the pressure enters the normal momentum as
+// sum_l a_l sum_m (p_a + p_b). R is the arithmetic precision.
 template <int L, int DIR, typename R>
 __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, long long n, long long st,
                                              R* f) {
   const Nodes<R>& P = nodes<R>(B);
   const R* a = coefs<R>(C).a;
+  const R* aq = coefs<R>(C).aq;  // a_l / 4
   const R* __restrict__ ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
   R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0), ap = R(0);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0), sp = R(0);
 #pragma unroll
     for (int m = 0; m < l; ++m) {
       long long ia = n - m * st, ib = n + (l - m) * st;
-      R qq = R(0.25) * (__ldg(P.rho + ia) + __ldg(P.rho + ib)) * (__ldg(ud + ia) + __ldg(ud + ib));
-      s0 += qq;
-      s1 += qq * (__ldg(P.u + ia) + __ldg(P.u + ib));
-      s2 += qq * (__ldg(P.v + ia) + __ldg(P.v + ib));
-      s3 += qq * (__ldg(P.w + ia) + __ldg(P.w + ib));
-      s4 += qq * (__ldg(P.H + ia) + __ldg(P.H + ib));
-      sp += __ldg(P.p + ia) + __ldg(P.p + ib);
+      R q = (aq[l] * (__ldg(P.rho + ia) + __ldg(P.rho + ib))) * (__ldg(ud + ia) + __ldg(ud + ib));
+      a0 += q;
+      a1 = fma(q, __ldg(P.u + ia) + __ldg(P.u + ib), a1);
+      a2 = fma(q, __ldg(P.v + ia) + __ldg(P.v + ib), a2);
+      a3 = fma(q, __ldg(P.w + ia) + __ldg(P.w + ib), a3);
+      a4 = fma(q, __ldg(P.H + ia) + __ldg(P.H + ib), a4);
+      ap = fma(a[l], __ldg(P.p + ia) + __ldg(P.p + ib), ap);
     }
-    R al = a[l];
-    a0 += al * s0;
-    a1 += al * s1;
-    a2 += al * s2;
-    a3 += al * s3;
-    a4 += al * s4;
-    ap += al * sp;
   }
   f[0] = R(2) * a0;
   f[1] = a1;

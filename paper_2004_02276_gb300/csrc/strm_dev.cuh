@@ -48,6 +48,7 @@ template <typename R>
 struct Coefs {
   R a[4], b[4];                      // central first/second-derivative coefficients, 1..L
   R ax[4], az[4];                    // a_l / dx and a_l / dz (first derivatives along x and z)
+  R aq[4];                           // a_l / 4 (pair weights of the split central flux)
   R inv_dx, inv_dz, inv_dx2, inv_dz2;
   R cp_pr, sens_eps, theta_thr, weno_eps;
   R gamma, gm1, r_gas, cp, t_wall, mu_ref, inv_tref, visc_exp, suth_s;
@@ -271,6 +272,17 @@ __device__ __forceinline__ bool face_decision(const Dims& d, const Consts& C, co
                                               int k, int dir) {
   if (C.weno_mode == 2) return true;
   if (C.weno_mode == 0) return false;
+  if constexpr (std::is_same<R, double>::value) {
+    // theta >= 0: the window maximum and the comparison on the IEEE bit patterns (integer pipe)
+    const double* th = B.n64.theta;
+    long long n = gidx(d, i, j, k), st = dir_stride(d, dir), m = 0;
+#pragma unroll
+    for (int q = -L + 1; q <= L; ++q) {
+      long long b = __double_as_longlong(__ldg(th + n + q * st));
+      m = b > m ? b : m;
+    }
+    return m > __double_as_longlong(C.k64.theta_thr);
+  }
   R tmax = face_theta_max<L>(nodes<R>(B).theta, gidx(d, i, j, k), dir_stride(d, dir));
   const R thr = coefs<R>(C).theta_thr;
   if (sizeof(R) == sizeof(double) || fabs(tmax - thr) > R(0.002) * thr) return tmax > thr;
