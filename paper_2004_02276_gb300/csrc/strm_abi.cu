@@ -45,14 +45,14 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Node fields held in FP64 (all of them in FP64 precision; those the FP64 characteristic
 // projection reads in mixed precision) and in FP32 (mixed precision only).
-const int kN64All = 18, kN64Mixed = 8, kN32Mixed = 11;  // FP64: 12 fields and the 6 wave speeds u_d -+ c
+const int kN64All = 18, kN64Mixed = 9, kN32Mixed = 11;  // FP64: 12 fields and the 6 wave speeds u_d -+ c
 
 struct Layout {
   Dims d;
   bool mixed;
   size_t off_n64[kN64All], off_n32[kN32Mixed];
   size_t off_fh[3];
-  size_t off_R, off_grad, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
+  size_t off_R, off_grad, off_band, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
 };
 
@@ -107,6 +107,9 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   // FP64: the velocity gradients of the sensor, reused by the viscous terms
   L.off_grad = off;
   if (!L.mixed) off = align_up(off + sizeof(double) * 9 * (size_t)d.N);
+  // mixed: the list of nodes whose FP32 theta is near the switch threshold
+  L.off_band = off;
+  if (L.mixed) off = align_up(off + sizeof(int) * (size_t)d.N);
   for (int dir = 0; dir < 3; ++dir) {
     L.off_wl[dir] = off;
     off = align_up(off + sizeof(int) * (size_t)d.nf[dir]);
@@ -416,6 +419,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
     STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_df_update(d, x->df, B, false, st));
   STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
   STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, st));
+  if (C.mixed && C.weno_mode == 1) STRM_LAUNCH(STRM_K_SENSOR, launch_band_theta(d, C, B, st));
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
   if (C.convective) {
     for (int dir = 0; dir < 3; ++dir)
@@ -504,7 +508,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   N64 = Nodes<double>{};
   N32 = Nodes<float>{};
   if (L.mixed) {
-    double** f64[kN64Mixed] = {&N64.rho, &N64.u, &N64.v, &N64.w, &N64.p, &N64.T, &N64.H, &N64.srho};
+    double** f64[kN64Mixed] = {&N64.rho, &N64.u, &N64.v, &N64.w, &N64.p, &N64.T, &N64.H, &N64.srho, &N64.theta};
     for (int f = 0; f < kN64Mixed; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
     float** f32[kN32Mixed] = {&N32.rho, &N32.u, &N32.v, &N32.w, &N32.p, &N32.T,
                               &N32.H,   &N32.c, &N32.mu, &N32.theta, &N32.div};
@@ -535,6 +539,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->B.c1h = met + 5 * g->ny;
   x->B.ubar = met + 6 * g->ny;
   x->B.grad = L.mixed ? nullptr : (double*)(ws + L.off_grad);
+  x->B.band = L.mixed ? (int*)(ws + L.off_band) : nullptr;
   x->B.m32.inv_hy = met32;
   x->B.m32.c2y = met32 + g->ny;
   x->B.m32.c1y = met32 + 2 * g->ny;
@@ -934,10 +939,13 @@ int strm_set_time(strm_ctx* x, double t) {
 int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsigned char* fx,
                 unsigned char* fy, unsigned char* fz) {
   if (!x || !w) return fail(STRM_EINVAL, "null context or state");
+  STRM_CK(cudaMemsetAsync(x->B.wcount, 0, 8 * sizeof(unsigned), x->stream));
   launch_prims(x->d, x->C, x->B, w, false, x->stream);
   if (x->C.bc[0] == kBcRecycle) launch_recycle(x->d, x->C, x->B, x->stream);
   launch_ghost_prims(x->d, x->C, x->B, x->stream);
   launch_sensor(x->d, x->C, x->B, x->stream);
+  if (x->C.mixed && x->C.weno_mode == 1) launch_band_theta(x->d, x->C, x->B, x->stream);
+  launch_ghost_scalars(x->d, x->C, x->B, x->stream);
   launch_export_sensor(x->d, x->C, x->B, theta, div, x->stream);
   unsigned char* fl[3] = {fx, fy, fz};
   for (int dir = 0; dir < 3; ++dir)

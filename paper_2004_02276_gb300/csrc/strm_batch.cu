@@ -111,6 +111,16 @@ __global__ void __launch_bounds__(256) kb_sensor(BatchIndex X) {
   body_sensor<L, R>(I.d, I.C, I.B, blk);
 }
 
+template <int L>
+__global__ void __launch_bounds__(128) kb_band_theta(BatchIndex X) {
+  long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long ts = (long long)gridDim.x * blockDim.x;
+  for (int e = 0; e < X.n; ++e) {
+    const Inst& I = X.inst[e];
+    if (I.C.weno_mode == 1) body_band_theta<L>(I.d, I.C, I.B, t0, ts);
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) kb_ghost_scalars(BatchIndex X) {
   int blk;
@@ -247,6 +257,7 @@ void enqueue_rhs_t(const strm_ensemble* E, bool dt_mode, double cfl, double dt_f
     }
   kb_ghost_prims<<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
   kb_sensor<L, R><<<E->total_blocks[kKindNode], 256, 0, st>>>(X);
+  if (MIXED) kb_band_theta<L><<<(unsigned)(E->sms * 8), 128, 0, st>>>(X);
   kb_ghost_scalars<R><<<E->total_blocks[kKindGhost], 256, 0, st>>>(X);
   kb_classify<L, 0, R><<<E->total_blocks[kKindFace + 0], 256, 0, st>>>(X);
   kb_classify<L, 1, R><<<E->total_blocks[kKindFace + 1], 256, 0, st>>>(X);

@@ -456,6 +456,7 @@ __device__ __forceinline__ void body_ghost_scalars(const Dims& d, const Consts& 
   int sk = theta_source(k, d.nz, kBcPeriodic, kBcPeriodic);
   long long dst = gidx(d, i, j, k), src = gidx(d, si, sj, sk);
   P.theta[dst] = P.theta[src];
+  if (!std::is_same<R, double>::value) B.n64.theta[dst] = B.n64.theta[src];  // mixed: switch field
   P.div[dst] = P.div[src];
 }
 
@@ -489,9 +490,51 @@ __device__ __forceinline__ void body_recycle_scale(const Dims& d, const Consts& 
 
 // Ducros sensor (Eq. sensor) at the interior nodes; the node divergence is kept for the
 // viscous terms.
+// Block-aggregated append of q to one compacted list (every thread of the block calls it).
+__device__ __forceinline__ void block_append1(bool mine, int q, int* list, unsigned* count) {
+  __shared__ unsigned s_w[32], s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  unsigned m = __ballot_sync(0xffffffffu, mine);
+  if (lane == 0) s_w[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < nwarp; ++w) {
+      unsigned c = s_w[w];
+      s_w[w] = t;
+      t += c;
+    }
+    s_base = t ? atomicAdd(count, t) : 0u;
+  }
+  __syncthreads();
+  if (mine) list[s_base + s_w[warp] + __popc(m & ((1u << lane) - 1u))] = q;
+}
+
 template <int L, typename R>
 __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, const Bufs& B, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
+  if constexpr (!std::is_same<R, double>::value) {
+    // mixed precision: FP32 theta; the switch decides on an FP64 theta field, which holds the
+    // FP32 value, except at the nodes whose FP32 theta falls within 0.2 % of the threshold
+    // (far wider than its FP32 error): those are listed here and get the FP64 theta from the
+    // FP64 velocities (body_band_theta), so the decisions are the ones FP64 takes on this state
+    bool valid = q < d.N, band = false;
+    if (valid) {
+      int i, j, k;
+      node_ijk(d, q, i, j, k);
+      const Nodes<R>& P = nodes<R>(B);
+      R div;
+      R th = theta_node<L, R>(d, C, B, i, j, k, div);
+      long long n = gidx(d, i, j, k);
+      P.theta[n] = th;
+      P.div[n] = div;
+      B.n64.theta[n] = (double)th;
+      const R thr = coefs<R>(C).theta_thr;
+      band = C.weno_mode == 1 && fabs(th - thr) <= R(0.002) * thr;
+    }
+    block_append1(band, (int)q, B.band, B.wcount + 3);
+    return;
+  }
   if (q >= d.N) return;
   int i, j, k;
   node_ijk(d, q, i, j, k);
@@ -511,6 +554,20 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
     long long n = gidx(d, i, j, k);
     P.theta[n] = th;
     P.div[n] = div;
+  }
+}
+
+// Mixed precision: the FP64 theta at the listed near-threshold nodes (grid-stride loop).
+template <int L>
+__device__ __forceinline__ void body_band_theta(const Dims& d, const Consts& C, const Bufs& B, long long t0,
+                                                long long tstride) {
+  long long cnt = B.wcount[3];
+  for (long long t = t0; t < cnt; t += tstride) {
+    long long q = B.band[t];
+    int i, j, k;
+    node_ijk(d, q, i, j, k);
+    double dv;
+    B.n64.theta[gidx(d, i, j, k)] = theta_node<L, double>(d, C, B, i, j, k, dv);
   }
 }
 

@@ -96,6 +96,8 @@ struct Bufs {
   const double* vol;                            // node volume dx (y_eta deta) dz per j
   const double* hy;                             // node height above the wall eta = 0, per j
   const double* c1h;                            // y_etaeta / y_eta^2 per j (FP64)
+  int* band;                                    // mixed: interior nodes whose FP32 theta is near
+                                                //   the threshold (count in wcount[3])
   double* lam[6];                               // FP64: u - c, u + c, v - c, v + c, w - c, w + c
                                                 //   at the nodes (ghosted), for the LF speeds
   double* grad;                                 // FP64: velocity gradients d_b u_a at the
@@ -241,15 +243,6 @@ __device__ __forceinline__ R theta_node(const Dims& d, const Consts& C, const Bu
   return th > R(0) ? th : R(0);
 }
 
-// WENO switch at the face between nodes n and n+st: max theta over nodes n-L+1 .. n+L.
-template <int L, typename R>
-__device__ __forceinline__ R face_theta_max(const R* __restrict__ theta, long long n, long long st) {
-  R tmax = R(0);
-#pragma unroll
-  for (int q = -L + 1; q <= L; ++q) tmax = fmax(tmax, __ldg(theta + n + q * st));
-  return tmax;
-}
-
 // Interior node whose theta a ghost node carries along a direction with face kinds lo/hi:
 // periodic copy, even mirror across a wall, copy of the boundary node at other faces.
 __device__ __forceinline__ int theta_source(int idx, int n, int lo, int hi) {
@@ -262,40 +255,24 @@ __device__ __forceinline__ int theta_source(int idx, int n, int lo, int hi) {
   return hi == kBcWall ? 2 * n - 1 - idx : n - 1;
 }
 
-// Hybrid switch decision for the face whose left node is (i,j,k) along dir. FP64 precision
-// compares the FP64 window maximum. Mixed precision compares the FP32 maximum, except when it
-// falls within 0.2% of the threshold (far wider than the FP32 error of theta): then theta is
-// recomputed in FP64 over the window (from the FP64 velocities), so that the decision is the
-// one the FP64 path takes for the same state.
+// Hybrid switch decision for the face whose left node is (i,j,k) along dir: the largest theta
+// over the window exceeds the threshold. The decision reads the FP64 theta field in both
+// precisions (in mixed precision it holds FP64 theta at every node whose FP32 value is near
+// the threshold). theta >= 0, so the maximum and the comparison are taken on the IEEE bit
+// patterns on the integer pipe.
 template <int L, typename R>
 __device__ __forceinline__ bool face_decision(const Dims& d, const Consts& C, const Bufs& B, int i, int j,
                                               int k, int dir) {
   if (C.weno_mode == 2) return true;
   if (C.weno_mode == 0) return false;
-  if constexpr (std::is_same<R, double>::value) {
-    // theta >= 0: the window maximum and the comparison on the IEEE bit patterns (integer pipe)
-    const double* th = B.n64.theta;
-    long long n = gidx(d, i, j, k), st = dir_stride(d, dir), m = 0;
+  const double* th = B.n64.theta;
+  long long n = gidx(d, i, j, k), st = dir_stride(d, dir), m = 0;
 #pragma unroll
-    for (int q = -L + 1; q <= L; ++q) {
-      long long b = __double_as_longlong(__ldg(th + n + q * st));
-      m = b > m ? b : m;
-    }
-    return m > __double_as_longlong(C.k64.theta_thr);
-  }
-  R tmax = face_theta_max<L>(nodes<R>(B).theta, gidx(d, i, j, k), dir_stride(d, dir));
-  const R thr = coefs<R>(C).theta_thr;
-  if (sizeof(R) == sizeof(double) || fabs(tmax - thr) > R(0.002) * thr) return tmax > thr;
-  double t64 = 0.0;
   for (int q = -L + 1; q <= L; ++q) {
-    int ii = i + (dir == 0 ? q : 0), jj = j + (dir == 1 ? q : 0), kk = k + (dir == 2 ? q : 0);
-    ii = theta_source(ii, d.nx, C.bc[0], C.bc[1]);
-    jj = theta_source(jj, d.ny, C.bc[2], C.bc[3]);
-    kk = theta_source(kk, d.nz, kBcPeriodic, kBcPeriodic);
-    double dv;
-    t64 = fmax(t64, theta_node<L, double>(d, C, B, ii, jj, kk, dv));
+    long long b = __double_as_longlong(__ldg(th + n + q * st));
+    m = b > m ? b : m;
   }
-  return t64 > C.k64.theta_thr;
+  return m > __double_as_longlong(C.k64.theta_thr);
 }
 
 // Block-wide sum (deterministic order) of a per-thread value; result valid in thread 0.

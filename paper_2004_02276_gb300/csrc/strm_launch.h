@@ -48,6 +48,8 @@ bool ctx_df(strm_ctx* x, DFParams* F);
 void launch_stats(const Dims& d, const Consts& C, const double* w, double* acc, double* scr, int mode,
                   cudaStream_t s);
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// mixed precision: FP64 theta at the nodes the sensor listed as near the switch threshold
+void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);

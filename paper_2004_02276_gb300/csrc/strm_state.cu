@@ -1,6 +1,8 @@
 // Node-wise kernels of one grid: primitives (+ CFL partial maxima), ghost fills of the
 // primitives and of the sensor fields, the Ducros sensor, RK stage update, forcing, totals and
 // flag export. The bodies are in strm_body.cuh.
+#include <algorithm>
+
 #include "strm_body.cuh"
 #include "strm_launch.h"
 
@@ -37,6 +39,12 @@ __global__ void k_recycle_scale(Dims d, Consts C, Bufs B) { body_recycle_scale(d
 template <typename R>
 __global__ void __launch_bounds__(256) k_ghost_scalars(Dims d, Consts C, Bufs B, long long nthreads) {
   body_ghost_scalars<R>(d, C, B, nthreads, blockIdx.x);
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) k_band_theta(Dims d, Consts C, Bufs B) {
+  body_band_theta<L>(d, C, B, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                     (long long)gridDim.x * blockDim.x);
 }
 
 template <int L, typename R>
@@ -155,6 +163,12 @@ void launch_ghost_prims(const Dims& d, const Consts& C, const Bufs& B, cudaStrea
 void launch_recycle(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
   k_recycle_mean<<<d.ny, 256, 0, s>>>(d, C, B);
   k_recycle_scale<<<1, 1, 0, s>>>(d, C, B);
+}
+
+void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
+  unsigned nb = (unsigned)std::min<long long>(blocks_for(d.N, 128), 1216);
+  if (C.L == 3) k_band_theta<3><<<nb, 128, 0, s>>>(d, C, B);
+  else k_band_theta<2><<<nb, 128, 0, s>>>(d, C, B);
 }
 
 void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
