@@ -238,6 +238,11 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
     K.az[l] = R((double)K.a[l] / dz);
     K.aq[l] = R(0.25 * (double)K.a[l]);
   }
+  for (int r = 0; r < 4; ++r) {
+    double t = 0.0;
+    for (int l = r + 1; l <= s.L; ++l) t += (double)K.a[l];
+    K.ap[r] = R(t);
+  }
   K.inv_dx = R(1.0 / dx);
   K.inv_dz = R(1.0 / dz);
   K.inv_dx2 = R((1.0 / dx) * (1.0 / dx));

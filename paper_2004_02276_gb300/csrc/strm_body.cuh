@@ -641,15 +641,18 @@ __device__ __forceinline__ void face_node(const Dims& d, long long q, int& i, in
 // encflux): f_phi = 2 sum_l a_l sum_{m<l} (rho, u_n, phi)~_{n-m,l}. With the pair weight
 // q = a_l (rho_a + rho_b)(u_a + u_b)/4 this is sum_{l,m} q (phi_a + phi_b) (the 1/4 is carried in
 // the coefficients a_l/4, and f_rho = 2 sum q); the pressure enters the normal momentum as
-// sum_l a_l sum_m (p_a + p_b). R is the arithmetic precision.
+// sum_l a_l sum_m (p_a + p_b) = sum_r ap_r (p_{n-r} + p_{n+1+r}), ap_r = a_{r+1} + .. + a_L,
+// r = 0..L-1, since the pressure sum is linear. R is the arithmetic precision.
 template <int L, int DIR, typename R>
 __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, long long n, long long st,
                                              R* f) {
   const Nodes<R>& P = nodes<R>(B);
-  const R* a = coefs<R>(C).a;
   const R* aq = coefs<R>(C).aq;  // a_l / 4
+  const R* apc = coefs<R>(C).ap;  // a_{r+1} + .. + a_L
   const R* __restrict__ ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
   R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0), ap = R(0);
+#pragma unroll
+  for (int r = 0; r < L; ++r) ap = fma(apc[r], __ldg(P.p + n - r * st) + __ldg(P.p + n + (r + 1) * st), ap);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
 #pragma unroll
@@ -661,7 +664,6 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
       a2 = fma(q, __ldg(P.v + ia) + __ldg(P.v + ib), a2);
       a3 = fma(q, __ldg(P.w + ia) + __ldg(P.w + ib), a3);
       a4 = fma(q, __ldg(P.H + ia) + __ldg(P.H + ib), a4);
-      ap = fma(a[l], __ldg(P.p + ia) + __ldg(P.p + ib), ap);
     }
   }
   f[0] = R(2) * a0;

@@ -49,6 +49,7 @@ struct Coefs {
   R a[4], b[4];                      // central first/second-derivative coefficients, 1..L
   R ax[4], az[4];                    // a_l / dx and a_l / dz (first derivatives along x and z)
   R aq[4];                           // a_l / 4 (pair weights of the split central flux)
+  R ap[4];                           // a_{r+1} + .. + a_L, r = 0..L-1 (its pressure part)
   R inv_dx, inv_dz, inv_dx2, inv_dz2;
   R cp_pr, sens_eps, theta_thr, weno_eps;
   R gamma, gm1, r_gas, cp, t_wall, mu_ref, inv_tref, visc_exp, suth_s;
