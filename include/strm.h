@@ -306,7 +306,23 @@ int strm_ensemble_totals(strm_ensemble* ens, double* const* w, double* out_host)
 /* Simulated time of every instance, t_host[e]. Synchronises. */
 int strm_ensemble_times(strm_ensemble* ens, double* t_host);
 
+/* The error words of all instances OR-ed together (bounds-checking build; see
+ * strm_debug_flags). Synchronises. */
+int strm_ensemble_debug_flags(strm_ensemble* ens, unsigned* flags_host);
+
 void strm_ensemble_destroy(strm_ensemble* ens);
+
+/* ---- Bounds checking. A library built with -DSTRM_DEBUG (paper_2004_02276_gb300/build.py,
+ * debug=True: libstrm_debug.so) checks in every kernel the extreme nodes of each stencil, the
+ * source node of each ghost and each face-list entry before using them; a violation ORs a code
+ * into the context's error word (1 ghost fill, 2 node stencil, 4 face stencil or face index,
+ * 8 list entry, 16 inflow plane) and the access is skipped instead of faulting. */
+
+/* 1 if this library is the bounds-checking build, else 0. */
+int strm_debug_build(void);
+
+/* The context's error word (always 0 in the release build). Synchronises. */
+int strm_debug_flags(strm_ctx* ctx, unsigned* flags_host);
 
 /* Largest grid (nx*ny*nz) strm_conserved_totals_static accepts. */
 #define STRM_STATIC_MAX_NODES 67108864

@@ -14,7 +14,8 @@ import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libstrm.so")
+# STRM_LIBRARY=debug selects the bounds-checking build (libstrm_debug.so)
+LIB_PATH = os.path.join(HERE, "libstrm_debug.so" if os.environ.get("STRM_LIBRARY") == "debug" else "libstrm.so")
 
 STRM_OK = 0
 _STATUS = {-1: "EINVAL", -2: "ECUDA", -3: "ENONFINITE", -4: "ENOMEM", -5: "ETIMEOUT"}
@@ -80,6 +81,8 @@ SIGNATURES = {
     "strm_weno_counts": ([_vp, _P(ctypes.c_longlong)], _i),
     "strm_inflow_df_bytes": ([_vp, _P(DF)], _sz),
     "strm_set_inflow_df": ([_vp, _P(DF), _P(_d), _vp, _sz], _i),
+    "strm_debug_build": ([], _i),
+    "strm_debug_flags": ([_vp, _P(ctypes.c_uint)], _i),
     "strm_stats_bytes": ([_vp, _i], _sz),
     "strm_stats_bind": ([_vp, _i, _vp, _sz], _i),
     "strm_stats_sample": ([_vp, _vp], _i),
@@ -93,6 +96,7 @@ SIGNATURES = {
     "strm_ensemble_workspace_bytes": ([_i, _P(Grid), _P(Scheme)], _sz),
     "strm_ensemble_create": ([_P(_vp), _i, _P(Grid), _P(Phys), _P(Scheme), _P(_i), _vp, _sz, _vp], _i),
     "strm_ensemble_set_bc": ([_vp, _i, _i, _i, _vp, _i], _i),
+    "strm_ensemble_debug_flags": ([_vp, _P(ctypes.c_uint)], _i),
     "strm_ensemble_inflow_df_bytes": ([_vp, _i, _P(DF)], _sz),
     "strm_ensemble_set_inflow_df": ([_vp, _i, _P(DF), _P(_d), _vp, _sz], _i),
     "strm_ensemble_advance": ([_vp, _P(_vp), _P(_vp), _i, _d, _d], _i),
@@ -338,6 +342,13 @@ class Solver:
             self.ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ns)))
         return out, ns.value
 
+    def debug_flags(self):
+        """The bounds-checking build's error word (0: no violation; always 0 in the release
+        build)."""
+        out = ctypes.c_uint()
+        _check("strm_debug_flags", lib().strm_debug_flags(self.ctx, ctypes.byref(out)))
+        return out.value
+
     def timing(self, enable=True):
         _check("strm_timing", lib().strm_timing(self.ctx, int(bool(enable))))
 
@@ -433,6 +444,11 @@ class Ensemble:
     def advance(self, ws, rs, nsteps, dt=0.0, cfl=0.8):
         _check("strm_ensemble_advance", lib().strm_ensemble_advance(
             self.ens, self._ptrs(ws), self._ptrs(rs), nsteps, dt, cfl))
+
+    def debug_flags(self):
+        out = ctypes.c_uint()
+        _check("strm_ensemble_debug_flags", lib().strm_ensemble_debug_flags(self.ens, ctypes.byref(out)))
+        return out.value
 
     def tune(self, ws, rs):
         """Run the autotuner; returns (WENO block, WENO blocks per SM, central blocks per SM)."""

@@ -52,7 +52,7 @@ struct Layout {
   bool mixed;
   size_t off_n64[kN64All], off_n32[kN32Mixed];
   size_t off_fh[3];
-  size_t off_R, off_grad, off_band, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
+  size_t off_R, off_grad, off_band, off_dbg, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
 };
 
@@ -118,6 +118,8 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   }
   L.off_wcount = off;
   off = align_up(off + 8 * sizeof(unsigned));
+  L.off_dbg = off;  // error word of the bounds-checking (debug) build
+  off = align_up(off + sizeof(unsigned));
   L.off_red = off;
   off = align_up(off + sizeof(double) * (5 * (size_t)reduce_blocks(d) + 64));
   L.off_scal = off;
@@ -545,6 +547,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   x->B.ubar = met + 6 * g->ny;
   x->B.grad = L.mixed ? nullptr : (double*)(ws + L.off_grad);
   x->B.band = L.mixed ? (int*)(ws + L.off_band) : nullptr;
+  x->d.dbg = (unsigned*)(ws + L.off_dbg);
   x->B.m32.inv_hy = met32;
   x->B.m32.c2y = met32 + g->ny;
   x->B.m32.c1y = met32 + 2 * g->ny;
@@ -560,6 +563,7 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
                         cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->B.scal, 0, sizeof(double) * kScalCount, x->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->B.wcount, 0, 8 * sizeof(unsigned), x->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->d.dbg, 0, sizeof(unsigned), x->stream);
   if (e != cudaSuccess) {
     delete x;
     return fail(STRM_ECUDA, std::string("init: ") + cudaGetErrorString(e));
@@ -904,6 +908,15 @@ int strm_stats_read(strm_ctx* x, double* out_host, long long* nsamples_host) {
   double inv = x->st_samples > 0 ? 1.0 / (double)x->st_samples : 0.0;
   for (size_t q = 0; q < n; ++q) out_host[q] *= inv;
   if (nsamples_host) *nsamples_host = x->st_samples;
+  return STRM_OK;
+}
+
+int strm_debug_build(void) { return kDebug ? 1 : 0; }
+
+int strm_debug_flags(strm_ctx* x, unsigned* flags_host) {
+  if (!x || !flags_host) return fail(STRM_EINVAL, "null context or output");
+  STRM_CK(cudaMemcpyAsync(flags_host, x->d.dbg, sizeof(unsigned), cudaMemcpyDeviceToHost, x->stream));
+  STRM_CK(cudaStreamSynchronize(x->stream));
   return STRM_OK;
 }
 

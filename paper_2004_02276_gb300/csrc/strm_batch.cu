@@ -434,6 +434,19 @@ int strm_ensemble_set_bc(strm_ensemble* E, int e, int face, int kind, const doub
   return STRM_OK;
 }
 
+int strm_ensemble_debug_flags(strm_ensemble* E, unsigned* flags_host) {
+  if (!E || !flags_host) return record_error(STRM_EINVAL, "null ensemble or output");
+  unsigned acc = 0;
+  for (strm_ctx* c : E->ctx) {
+    unsigned f = 0;
+    int rc = strm_debug_flags(c, &f);
+    if (rc) return rc;
+    acc |= f;
+  }
+  *flags_host = acc;
+  return STRM_OK;
+}
+
 size_t strm_ensemble_inflow_df_bytes(const strm_ensemble* E, int e, const strm_df* df) {
   if (!E || e < 0 || e >= E->n) return 0;
   return strm_inflow_df_bytes(E->ctx[e], df);

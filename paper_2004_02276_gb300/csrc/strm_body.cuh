@@ -404,14 +404,22 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
   if (q >= nthreads) return;
   int face, side, layer, i, j, k;
   if (!ghost_target(d, q, face, side, layer, i, j, k)) return;
+  if (!stencil_ok(d, i, j, k, 0, 0, 0, kDbgGhost)) return;
   const Nodes<double>& P = B.n64;
   long long dst = gidx(d, i, j, k);
   int kind = face == 2 ? kBcPeriodic : C.bc[2 * face + side];
   if (kind == kBcPeriodic) {
     int si = face == 0 ? wrapi(i, d.nx) : i, sj = face == 1 ? wrapi(j, d.ny) : j;
     int sk = face == 2 ? wrapi(k, d.nz) : k;
+    if (!stencil_ok(d, si, sj, sk, 0, 0, 0, kDbgGhost)) return;
     copy_ghost(C, B, dst, gidx(d, si, sj, sk));
     return;
+  }
+  if constexpr (kDebug) {  // the interior source node of the face kinds below
+    int si = face == 0 ? (side == 0 ? 0 : d.nx - 1) : i, sj = face == 1 ? (side == 0 ? 0 : d.ny - 1) : j;
+    if (kind == kBcRecycle) si = C.i_recycle - layer;
+    if (!stencil_ok(d, si, sj, k, 0, 0, 0, kDbgGhost) || si < 0 || si >= d.nx) return;
+    if (kind == kBcDigitalFilter && !index_ok(d, (long long)k * d.ny + j, (long long)d.nz * d.ny, kDbgInflow)) return;
   }
   PState g;
   if (kind == kBcWall) {
@@ -454,6 +462,7 @@ __device__ __forceinline__ void body_ghost_scalars(const Dims& d, const Consts& 
   int si = theta_source(i, d.nx, C.bc[0], C.bc[1]);
   int sj = theta_source(j, d.ny, C.bc[2], C.bc[3]);
   int sk = theta_source(k, d.nz, kBcPeriodic, kBcPeriodic);
+  if (!stencil_ok(d, i, j, k, 0, 0, 0, kDbgGhost) || !stencil_ok(d, si, sj, sk, 0, 0, 0, kDbgGhost)) return;
   long long dst = gidx(d, i, j, k), src = gidx(d, si, sj, sk);
   P.theta[dst] = P.theta[src];
   if (!std::is_same<R, double>::value) B.n64.theta[dst] = B.n64.theta[src];  // mixed: switch field
@@ -524,6 +533,9 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
       node_ijk(d, q, i, j, k);
       const Nodes<R>& P = nodes<R>(B);
       R div;
+      if (!stencil_ok(d, i, j, k, 0, L, L, kDbgNode) || !stencil_ok(d, i, j, k, 1, L, L, kDbgNode) ||
+          !stencil_ok(d, i, j, k, 2, L, L, kDbgNode))
+        i = j = k = 0;  // (debug builds) keep the block's barrier: compute at a safe node
       R th = theta_node<L, R>(d, C, B, i, j, k, div);
       long long n = gidx(d, i, j, k);
       P.theta[n] = th;
@@ -538,6 +550,9 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
   if (q >= d.N) return;
   int i, j, k;
   node_ijk(d, q, i, j, k);
+  if (!stencil_ok(d, i, j, k, 0, L, L, kDbgNode) || !stencil_ok(d, i, j, k, 1, L, L, kDbgNode) ||
+      !stencil_ok(d, i, j, k, 2, L, L, kDbgNode))
+    return;
   const Nodes<R>& P = nodes<R>(B);
   R div;
   if constexpr (std::is_same<R, double>::value) {
@@ -564,6 +579,7 @@ __device__ __forceinline__ void body_band_theta(const Dims& d, const Consts& C, 
   long long cnt = B.wcount[3];
   for (long long t = t0; t < cnt; t += tstride) {
     long long q = B.band[t];
+    if (!index_ok(d, q, d.N, kDbgList)) continue;
     int i, j, k;
     node_ijk(d, q, i, j, k);
     double dv;
@@ -1011,7 +1027,7 @@ __device__ __forceinline__ void body_classify(const Dims& d, const Consts& C, co
   if (valid) {
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
-    fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
+    if (stencil_ok(d, i, j, k, DIR, L - 1, L, kDbgFace)) fl = face_decision<L, R>(d, C, B, i, j, k, DIR);
   }
   block_append2(valid, fl, (int)q, B.wl[DIR], B.wcount + DIR, B.cl[DIR], B.wcount + 4 + DIR);
 }
@@ -1026,8 +1042,10 @@ __device__ __forceinline__ void body_central(const Dims& d, const Consts& C, con
   R* out = face_flux<R>(B, DIR);
   for (long long t = t0; t < cnt; t += tstride) {
     long long q = use_list ? (long long)B.cl[DIR][t] : t;
+    if (!index_ok(d, q, nf, kDbgList)) continue;
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
+    if (!stencil_ok(d, i, j, k, DIR, L - 1, L, kDbgFace)) continue;
     R f[5];
     central_flux<L, DIR, R>(C, B, gidx(d, i, j, k), st, f);
 #pragma unroll
@@ -1046,8 +1064,10 @@ __device__ __forceinline__ void body_weno(const Dims& d, const Consts& C, const 
   long long st = dir_stride(d, DIR);
   for (long long t = t0; t < cnt; t += tstride) {
     long long q = all ? t : (long long)B.wl[DIR][t];
+    if (!index_ok(d, q, nf, kDbgList)) continue;
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
+    if (!stencil_ok(d, i, j, k, DIR, 2, 3, kDbgFace)) continue;
     if (MIXED) {
       float f[5];
       weno_flux_mixed<DIR>(C, B, gidx(d, i, j, k), st, f);
@@ -1170,7 +1190,20 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
                                               double* __restrict__ Rout, int blk, double* sh) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   double fpart = 0.0;
-  if (q < d.N) {
+  bool live = q < d.N;
+  if constexpr (kDebug) {  // stencils of the viscous terms and the faces read (debug builds)
+    if (live) {
+      int i = (int)(q % d.nx), j = (int)((q / d.nx) % d.ny), k = (int)(q / ((long long)d.nx * d.ny));
+      long long qx = ((long long)k * d.ny + j) * (d.nx + 1) + i;
+      long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
+      long long qz = ((long long)k * d.ny + j) * d.nx + i;
+      live = stencil_ok(d, i, j, k, 0, L, L, kDbgNode) && stencil_ok(d, i, j, k, 1, L, L, kDbgNode) &&
+             stencil_ok(d, i, j, k, 2, L, L, kDbgNode) && index_ok(d, qx + 1, d.nf[0], kDbgFace) &&
+             index_ok(d, qy + d.nx, d.nf[1], kDbgFace) &&
+             index_ok(d, qz + (long long)d.nx * d.ny, d.nf[2], kDbgFace);
+    }
+  }
+  if (live) {
     int i = (int)(q % d.nx);
     long long r = q / d.nx;
     int j = (int)(r % d.ny);

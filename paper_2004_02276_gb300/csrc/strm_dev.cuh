@@ -29,6 +29,7 @@ struct Dims {
   long long ng;       // px * py * pz
   long long N;        // nx * ny * nz
   long long nf[3];    // faces per direction
+  unsigned* dbg;      // debug builds: the context's error word (see kDebug)
 };
 
 // Ghosted node fields of one precision.
@@ -128,6 +129,47 @@ enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalRecycle
 
 __device__ __forceinline__ long long gidx(const Dims& d, int i, int j, int k) {
   return ((long long)(k + G) * d.py + (j + G)) * d.px + (i + GX);
+}
+
+// Debug builds (-DSTRM_DEBUG, the bounds-checking build): the kernels check the extreme nodes of
+// every stencil, the ghost sources and the list entries they are about to use, OR a code into
+// the context's error word when one lies outside its array, and skip that access instead of
+// faulting (codes: kDbg*). Release builds compile the checks away.
+#ifdef STRM_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+enum : unsigned { kDbgGhost = 1u, kDbgNode = 2u, kDbgFace = 4u, kDbgList = 8u, kDbgInflow = 16u };
+
+__device__ __forceinline__ bool node_in_box(const Dims& d, int i, int j, int k) {
+  return i >= -G && i < d.nx + G && j >= -G && j < d.ny + G && k >= -G && k < d.nz + G;
+}
+
+// true when the nodes from -lo to +hi along dir around (i, j, k) are all in the ghosted box
+// (always true in release builds); records `code` otherwise
+__device__ __forceinline__ bool stencil_ok(const Dims& d, int i, int j, int k, int dir, int lo, int hi,
+                                           unsigned code) {
+  if constexpr (!kDebug) {
+    return true;
+  } else {
+    int a0 = i - (dir == 0 ? lo : 0), a1 = j - (dir == 1 ? lo : 0), a2 = k - (dir == 2 ? lo : 0);
+    int b0 = i + (dir == 0 ? hi : 0), b1 = j + (dir == 1 ? hi : 0), b2 = k + (dir == 2 ? hi : 0);
+    bool ok = node_in_box(d, a0, a1, a2) && node_in_box(d, b0, b1, b2);
+    if (!ok && d.dbg) atomicOr(d.dbg, code);
+    return ok;
+  }
+}
+
+// the same for a single index against an extent
+__device__ __forceinline__ bool index_ok(const Dims& d, long long q, long long n, unsigned code) {
+  if constexpr (!kDebug) {
+    return true;
+  } else {
+    bool ok = q >= 0 && q < n;
+    if (!ok && d.dbg) atomicOr(d.dbg, code);
+    return ok;
+  }
 }
 
 __device__ __forceinline__ long long dir_stride(const Dims& d, int dir) {
