@@ -150,6 +150,12 @@ def bl_case(name, nx, ny, nz, lx, ly, lz, shock=False, **kw) -> Case:
 
 
 C3 = bl_case("bl-1024x256x256", 1024, 256, 256, 26.25, 12.0, 5.0)
+# The paper's own boundary-layer settings (Section 3.2) on the C3 grid: fourth-order stencils,
+# Sutherland's law (T_inf = 288.15 K), hyperbolic-sine clustering (beta = 4, first node at
+# y = 0.0034 delta_in) and the digital-filter inflow (profiles: df_profiles).
+PAPER_BL = bl_case("paper-bl-1024x256x256", 1024, 256, 256, 26.25, 12.0, 5.0, L=2,
+                   visc_law="sutherland", y_map="sinh1", beta=4.0, bc_xmin="df", df_ny=4, df_nz=4,
+                   df_tau=0.5, df_seed=1)
 C4 = bl_case("sbli-2048x384x256", 2048, 384, 256, 50.0, 12.0, 5.33, shock=True, noise=0.001)
 
 

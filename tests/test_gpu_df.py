@@ -34,6 +34,11 @@ DF_BL = inputs.bl_case("bl-df-48x40x16", 48, 40, 16, 7.0, 6.0, 1.5, bc_xmin="df"
                        df_tau=0.5, df_seed=12345)
 DF_ODD = inputs.bl_case("bl-df-37x29x9", 37, 29, 9, 5.0, 6.0, 1.0, bc_xmin="df", df_ny=2, df_nz=4,
                         df_tau=0.2, df_seed=7, y_map="sinh1", beta=3.0)
+# the paper's own boundary-layer settings together (Section 3.2): fourth-order stencils,
+# Sutherland's law, hyperbolic-sine clustering and the digital-filter inflow
+DF_PAPER = inputs.bl_case("bl-paper-48x40x12", 48, 40, 12, 7.0, 6.0, 1.5, bc_xmin="df", df_ny=3,
+                          df_nz=3, df_tau=0.5, df_seed=11, L=2, visc_law="sutherland",
+                          y_map="sinh1", beta=4.0)
 
 
 def oracle_cfg(case):
@@ -41,7 +46,7 @@ def oracle_cfg(case):
     return O.make_cfg(case, df=df), df
 
 
-@pytest.mark.parametrize("case", [DF_BL, DF_ODD], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [DF_BL, DF_ODD, DF_PAPER], ids=lambda c: c.name)
 def test_rhs_and_flags_match_oracle(case):
     w0 = inputs.bl_state(case, seed=2)
     cfg, _ = oracle_cfg(case)
@@ -57,7 +62,7 @@ def test_rhs_and_flags_match_oracle(case):
     assert err.max() <= TOL, err
 
 
-@pytest.mark.parametrize("case", [DF_BL, DF_ODD], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [DF_BL, DF_ODD, DF_PAPER], ids=lambda c: c.name)
 def test_ten_steps_match_oracle(case):
     w0 = inputs.bl_state(case, seed=3)
     cfg, df = oracle_cfg(case)
