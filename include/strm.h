@@ -324,6 +324,23 @@ int strm_debug_build(void);
 /* The context's error word (always 0 in the release build). Synchronises. */
 int strm_debug_flags(strm_ctx* ctx, unsigned* flags_host);
 
+/* ---- Precision conversions of the mixed-precision kernels. On this GPU the FP64 <-> FP32
+ * conversion instructions issue on the FP64 pipe; the mixed-precision kernels convert with
+ * integer operations on the IEEE-754 bit patterns instead. These two calls apply the same
+ * conversions elementwise to device arrays, so that they can be checked against IEEE-754
+ * conversion:
+ *   FP64 -> FP32: round to nearest, ties away from zero (IEEE ties-to-even differs only for
+ *   values exactly halfway between two floats); magnitudes that round below 2^-126 give a
+ *   signed zero; magnitudes that round to 2^128 or above, infinities and NaNs give a signed
+ *   infinity.
+ *   FP32 -> FP64: exact for normal floats; subnormals give a signed zero; infinities and NaNs
+ *   stay infinities and NaNs.
+ * x and y are device arrays of n elements (n = 0: nothing is done); the work is enqueued on
+ * `stream` (NULL: the legacy default stream) and the call does not synchronise. n < 0, or a
+ * null pointer with n > 0: STRM_EINVAL. */
+int strm_convert_f64_f32(const double* x, float* y, long long n, void* stream);
+int strm_convert_f32_f64(const float* x, double* y, long long n, void* stream);
+
 /* Largest grid (nx*ny*nz) strm_conserved_totals_static accepts. */
 #define STRM_STATIC_MAX_NODES 67108864
 

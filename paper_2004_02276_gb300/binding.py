@@ -93,6 +93,8 @@ SIGNATURES = {
     "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
     "strm_launch_count": ([_vp, _P(ctypes.c_longlong)], _i),
     "strm_conserved_totals_static": ([_P(Grid), _vp, _P(_d), _vp], _i),
+    "strm_convert_f64_f32": ([_vp, _vp, ctypes.c_longlong, _vp], _i),
+    "strm_convert_f32_f64": ([_vp, _vp, ctypes.c_longlong, _vp], _i),
     "strm_ensemble_workspace_bytes": ([_i, _P(Grid), _P(Scheme)], _sz),
     "strm_ensemble_create": ([_P(_vp), _i, _P(Grid), _P(Phys), _P(Scheme), _P(_i), _vp, _sz, _vp], _i),
     "strm_ensemble_set_bc": ([_vp, _i, _i, _i, _vp, _i], _i),
@@ -200,6 +202,21 @@ def conserved_totals_static(case, w, stream=None):
            lib().strm_conserved_totals_static(ctypes.byref(g), _ptr(w), out,
                                               ctypes.c_void_p(st.cuda_stream)))
     return list(out)
+
+
+def convert(x):
+    """The FP64 <-> FP32 conversions of the mixed-precision kernels, elementwise on a contiguous
+    CUDA tensor (float64 -> float32 or float32 -> float64), on the current stream."""
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in (torch.float64, torch.float32)):
+        raise ValueError("need a contiguous float64 or float32 CUDA tensor")
+    st = ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    if x.dtype == torch.float64:
+        y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        _check("strm_convert_f64_f32", lib().strm_convert_f64_f32(_ptr(x), _ptr(y), x.numel(), st))
+    else:
+        y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        _check("strm_convert_f32_f64", lib().strm_convert_f32_f64(_ptr(x), _ptr(y), x.numel(), st))
+    return y
 
 
 class Solver:

@@ -911,6 +911,20 @@ int strm_stats_read(strm_ctx* x, double* out_host, long long* nsamples_host) {
   return STRM_OK;
 }
 
+int strm_convert_f64_f32(const double* x, float* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(STRM_EINVAL, "bad conversion arguments");
+  launch_d2f(x, y, n, (cudaStream_t)stream);
+  STRM_CK(cudaGetLastError());
+  return STRM_OK;
+}
+
+int strm_convert_f32_f64(const float* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(STRM_EINVAL, "bad conversion arguments");
+  launch_f2d(x, y, n, (cudaStream_t)stream);
+  STRM_CK(cudaGetLastError());
+  return STRM_OK;
+}
+
 int strm_debug_build(void) { return kDebug ? 1 : 0; }
 
 int strm_debug_flags(strm_ctx* x, unsigned* flags_host) {

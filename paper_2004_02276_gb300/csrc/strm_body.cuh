@@ -77,7 +77,7 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     const Nodes<double>& P = B.n64;
     const Nodes<float>& F = B.n32;
     double rho = w[q];
-    double rs = rsqrt(rho);
+    double rs = rsqrt_nr(rho);
     double ir = rs * rs;
     double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
     double E = w[4 * d.N + q] * ir;
@@ -93,19 +93,19 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     P.p[n] = p;
     P.H[n] = H;
     P.srho[n] = rho * rs;
-    float rf = (float)rho, pf = (float)p, Tf = (float)T;
+    float rf = d2f(rho), pf = d2f(p), Tf = d2f(T);
     float cf = sqrtf(C.k32.gamma * pf / rf);
     F.rho[n] = rf;
-    F.u[n] = (float)u;
-    F.v[n] = (float)v;
-    F.w[n] = (float)ww;
+    F.u[n] = d2f(u);
+    F.v[n] = d2f(v);
+    F.w[n] = d2f(ww);
     F.p[n] = pf;
     F.T[n] = Tf;
-    F.H[n] = (float)H;
+    F.H[n] = d2f(H);
     F.c[n] = cf;
     F.mu[n] = viscosity(C.k32, C.visc_law, Tf);
     if (want_cfl) {
-      double c = (double)cf;
+      double c = f2d(cf);
       spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
     }
   }
@@ -217,14 +217,14 @@ __device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, lon
     P.mu[dst] = viscosity(C.k64, C.visc_law, g.T);
   } else {
     const Nodes<float>& F = B.n32;
-    float rf = (float)g.rho, pf = (float)g.p, Tf = (float)g.T;
+    float rf = d2f(g.rho), pf = d2f(g.p), Tf = d2f(g.T);
     F.rho[dst] = rf;
-    F.u[dst] = (float)g.u;
-    F.v[dst] = (float)g.v;
-    F.w[dst] = (float)g.w;
+    F.u[dst] = d2f(g.u);
+    F.v[dst] = d2f(g.v);
+    F.w[dst] = d2f(g.w);
     F.p[dst] = pf;
     F.T[dst] = Tf;
-    F.H[dst] = (float)H;
+    F.H[dst] = d2f(H);
     F.c[dst] = sqrtf(C.k32.gamma * pf / rf);
     F.mu[dst] = viscosity(C.k32, C.visc_law, Tf);
   }
@@ -540,7 +540,7 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
       long long n = gidx(d, i, j, k);
       P.theta[n] = th;
       P.div[n] = div;
-      B.n64.theta[n] = (double)th;
+      B.n64.theta[n] = f2d(th);
       const R thr = coefs<R>(C).theta_thr;
       band = C.weno_mode == 1 && fabs(th - thr) <= R(0.002) * thr;
     }
@@ -732,28 +732,37 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
 // by s_k. The acoustic difference row is formed as c B (no division by c per node) and the 1/c
 // enters the sums A +- B as an FMA.
 //
-// FP64 is the binding pipe on this path, so the maxima of the non-negative LF speeds are taken
-// on their IEEE bit patterns (monotone in the value for non-negative doubles) on the integer
-// pipe.
-__device__ __forceinline__ long long max_bits(long long m, double x) {
-  long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;  // |x|, sign bit cleared
-  return b > m ? b : m;
-}
+// FP64 is the binding pipe on this path, so the maxima of the LF speeds |x| are taken on their
+// IEEE bit patterns (with the sign bit cleared, monotone in |x|) on the integer pipe, as
+// (high word, low word) pairs.
+struct AbsMax {
+  unsigned hi = 0u, lo = 0u;
+  __device__ __forceinline__ void add(double x) {
+    unsigned l, h;
+    split64(x, l, h);
+    h &= 0x7fffffffu;
+    const bool gt = h > hi || (h == hi && l > lo);
+    hi = gt ? h : hi;
+    lo = gt ? l : lo;
+  }
+  __device__ __forceinline__ double value() const { return join64(lo, hi); }
+};
 
 // Reciprocals of five positive doubles with one division (prefix-product method): each value
-// is first brought to [1, 2) by replacing its exponent field (integer operations), the five
-// mantissas are inverted together, and each reciprocal gets its exponent back by an integer
-// subtraction on its exponent field. Valid for positive normal inputs below 2^1022 (the
-// reciprocals stay normal); a NaN input yields a finite value here, so callers
+// is first brought to [1, 2) by replacing its exponent field (integer operations on the high
+// word), the five mantissas are inverted together, and each reciprocal gets its exponent back
+// by an integer subtraction on its exponent field. Valid for positive normal inputs below
+// 2^1022 (the reciprocals stay normal); a NaN input yields a finite value here, so callers
 // multiply by a numerator that carries the NaN.
 __device__ __forceinline__ void recip5(const double* y, double* r) {
   double m[5];
-  long long e[5];
+  int e[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    long long b = __double_as_longlong(y[k]);
-    e[k] = ((b >> 52) & 0x7ff) - 1023;
-    m[k] = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    unsigned lo, hi;
+    split64(y[k], lo, hi);
+    e[k] = (int)((hi >> 20) & 0x7ffu) - 1023;
+    m[k] = join64(lo, (hi & 0x000fffffu) | 0x3ff00000u);
   }
   double p1 = m[0] * m[1], p2 = p1 * m[2], p3 = p2 * m[3], p4 = p3 * m[4];
   double inv = 1.0 / p4;
@@ -766,7 +775,11 @@ __device__ __forceinline__ void recip5(const double* y, double* r) {
   double i1 = inv * m[0], i0 = inv * m[1];
   const double im[5] = {i0, i1, i2, i3, i4};
 #pragma unroll
-  for (int k = 0; k < 5; ++k) r[k] = __longlong_as_double(__double_as_longlong(im[k]) - (e[k] << 52));
+  for (int k = 0; k < 5; ++k) {
+    unsigned lo, hi;
+    split64(im[k], lo, hi);
+    r[k] = join64(lo, hi - ((unsigned)e[k] << 20));
+  }
 }
 
 template <int DIR>
@@ -794,18 +807,17 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
   double un_a = ua[DIR];
 
   // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
-  long long m0 = 0, m1 = 0, m4 = 0;
+  AbsMax m0, m1, m4;
   const double* __restrict__ lm = B.lam[2 * DIR];      // u_n - c at the nodes
   const double* __restrict__ lp = B.lam[2 * DIR + 1];  // u_n + c
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    m0 = max_bits(m0, __ldg(lm + nn));
-    m1 = max_bits(m1, __ldg(un_p + nn));
-    m4 = max_bits(m4, __ldg(lp + nn));
+    m0.add(__ldg(lm + nn));
+    m1.add(__ldg(un_p + nn));
+    m4.add(__ldg(lp + nn));
   }
-  const double lam0 = __longlong_as_double(m0), lam1 = __longlong_as_double(m1),
-               lam4 = __longlong_as_double(m4);
+  const double lam0 = m0.value(), lam1 = m1.value(), lam4 = m4.value();
 
   // scaled split characteristic values s_k (L F +- lam_k L w)/2 at the stencil nodes
   double gp[5][6], gm[5][6];
@@ -890,6 +902,9 @@ __device__ __forceinline__ float weno5_f(float f0, float f1, float f2, float f3,
 // done in FP64: Roe state, eigen-scalars and, per stencil node, the acoustic-row scalars
 // A and B of w and of the Euler flux (where cancellation happens). The LF split, WENO5 and the
 // projection back to conserved variables run in FP32; the result is an FP32 face flux.
+// The FP64 pipe bounds this kernel, so its FP64 -> FP32 roundings run on the integer pipe (d2f)
+// and the Roe state's reciprocal and inverse sound speed come from FP32 estimates refined by a
+// Newton step in FP64 (rcp_nr, rsqrt_nr; relative error below 2^-43).
 template <int DIR>
 __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, long long n, long long st,
                                                 float* f) {
@@ -901,7 +916,7 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
   const float* __restrict__ velf[3] = {F.u, F.v, F.w};
   // FP64 Roe average of nodes n and n + st and the eigen-scalars
   double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
-  double inv = 1.0 / (sl + sr);
+  double inv = rcp_nr(sl + sr);
   double wl = sl * inv, wr = sr * inv;
   double ua[3];
 #pragma unroll
@@ -909,11 +924,11 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
   double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
   double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
   double c2a = C.gm1 * (Ha - 0.5 * q2);
-  double ic = rsqrt(c2a);
-  double ca = c2a * ic;
+  double ic = rsqrt_nr(c2a);
   double b1 = C.gm1 * ic * ic;
   double b2 = 0.5 * q2 * b1;
   double un_a = ua[DIR];
+  const float uaf[3] = {d2f(ua[0]), d2f(ua[1]), d2f(ua[2])};
   // FP32 local LF speeds
   float lam0 = 0.f, lam1 = 0.f, lam4 = 0.f;
 #pragma unroll
@@ -924,7 +939,6 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     lam1 = fmaxf(lam1, fabsf(un));
     lam4 = fmaxf(lam4, fabsf(un + cs));
   }
-  const float uat1 = (float)ua[T1], uat2 = (float)ua[T2];
   float gp[5][6], gm[5][6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -934,16 +948,16 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
     double un = uu[DIR];
     double run = rho * un;
-    double udot = ua[0] * uu[0] + ua[1] * uu[1] + ua[2] * uu[2];
-    double K = b2 + b1 * (H - udot);
+    double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
+    double K = fma(b1, hu, b2);
     double b1p = b1 * p;
-    double Aw = rho * K - b1p;
-    double Af = run * K - b1p * un_a;
+    double Aw = fma(rho, K, -b1p);
+    double Af = fma(run, K, -b1p * un_a);
     double du = un_a - un;
     double cBw = rho * du, cBf = fma(run, du, -p);
-    float Sw = (float)fma(ic, cBw, Aw), Sf = (float)fma(ic, cBf, Af), Dw = (float)fma(-ic, cBw, Aw),
-          Df = (float)fma(-ic, cBf, Af);
-    float Awf = (float)Aw, Aff = (float)Af;
+    float Sw = d2f(fma(ic, cBw, Aw)), Sf = d2f(fma(ic, cBf, Af)), Dw = d2f(fma(-ic, cBw, Aw)),
+          Df = d2f(fma(-ic, cBf, Af));
+    float Awf = d2f(Aw), Aff = d2f(Af);
     float rhof = __ldg(F.rho + nn), unf = __ldg(velf[DIR] + nn);
     float runf = rhof * unf;
     gp[0][q] = fmaf(lam0, Sw, Sf);
@@ -953,7 +967,7 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     float r1 = fmaf(lam1, rhof, runf), r2 = fmaf(-lam1, rhof, runf);
     gp[1][q] = r1 - fmaf(lam1, Awf, Aff);
     gm[1][q] = r2 - fmaf(-lam1, Awf, Aff);
-    float d1 = __ldg(velf[T1] + nn) - uat1, d2 = __ldg(velf[T2] + nn) - uat2;
+    float d1 = __ldg(velf[T1] + nn) - uaf[T1], d2 = __ldg(velf[T2] + nn) - uaf[T2];
     gp[2][q] = d1 * r1;
     gm[2][q] = d1 * r2;
     gp[3][q] = d2 * r1;
@@ -969,8 +983,8 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
               weno5_f(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4);
     g[k] = (acoustic ? 0.25f : 0.5f) * v;
   }
-  const float uaf[3] = {(float)ua[0], (float)ua[1], (float)ua[2]};
-  const float caf = (float)ca, Haf = (float)Ha, q2f = (float)q2, unaf = (float)un_a;
+  const float icf = d2f(ic), c2f = d2f(c2a);
+  const float caf = c2f * icf, Haf = d2f(Ha), q2f = d2f(q2), unaf = uaf[DIR];
   float gs = g[0] + g[1] + g[4];
   f[0] = gs;
 #pragma unroll
@@ -1235,9 +1249,9 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
           // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
           // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
           // FP64 round-off as in the FP64 path
-          mass64 = -(((double)__ldg(fx + qx + 1) - (double)__ldg(fx + qx)) * C.k64.inv_dx +
-                     ((double)yhi - (double)ylo) * __ldg(B.m64.inv_hy + j) +
-                     ((double)__ldg(fz + qz + sxy) - (double)__ldg(fz + qz)) * C.k64.inv_dz);
+          mass64 = -((to_f64(__ldg(fx + qx + 1)) - to_f64(__ldg(fx + qx))) * C.k64.inv_dx +
+                     (to_f64(yhi) - to_f64(ylo)) * __ldg(B.m64.inv_hy + j) +
+                     (to_f64(__ldg(fz + qz + sxy)) - to_f64(__ldg(fz + qz))) * C.k64.inv_dz);
         }
       }
     }
@@ -1248,9 +1262,9 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }
 #pragma unroll
-    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = (double)res[m];
+    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
     if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
-    fpart = (double)res[1] * __ldg(B.vol + j);
+    fpart = to_f64(res[1]) * __ldg(B.vol + j);
   }
   if (C.forcing) {
     double s = block_sum(fpart, sh);

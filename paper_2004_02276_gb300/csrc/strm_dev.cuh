@@ -187,6 +187,70 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 __device__ __forceinline__ double rpow(double x, double e) { return exp(e * log(x)); }
 __device__ __forceinline__ float rpow(float x, float e) { return powf(x, e); }
 
+// ---------------------------------------------------------------- FP64 bit patterns
+// The two 32-bit halves of an FP64 value and back, as opaque register moves. Integer work on
+// FP64 bit patterns goes through these: written as 64-bit integer operations on the bit
+// pattern, a sign-bit mask is recognised by the compiler as |x| and issued on the FP64 pipe.
+__device__ __forceinline__ void split64(double x, unsigned& lo, unsigned& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+__device__ __forceinline__ double join64(unsigned lo, unsigned hi) {
+  double x;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(x) : "r"(lo), "r"(hi));
+  return x;
+}
+
+// ---------------------------------------------------------------- FP64 <-> FP32 conversions
+// On this GPU the conversions between FP64 and FP32 issue on the FP64 pipe, which runs at 1/64
+// of the FP32 rate. The mixed-precision kernels convert several values per stencil node, so
+// they convert with 32-bit integer operations on the IEEE-754 bit patterns instead.
+//
+// binary64 -> binary32: round to nearest, ties away from zero (IEEE's ties-to-even differs only
+// for values exactly halfway between two floats); magnitudes that round below the smallest
+// normal float (2^-126) give a signed zero, those that round to 2^128 or above, infinities and
+// NaNs give a signed infinity.
+__device__ __forceinline__ float d2f(double x) {
+  unsigned lo, hi;
+  split64(x, lo, hi);
+  const unsigned sign = hi & 0x80000000u;
+  // magnitude plus half of the 29 dropped mantissa bits (the carry moves into the high word and,
+  // past the mantissa, into the exponent as it should), rebiased from 1023 to 127 (896 << 20)
+  const unsigned lo2 = lo + 0x10000000u;
+  const int h = (int)((hi & 0x7fffffffu) + (lo2 < lo ? 1u : 0u) - (896u << 20));  // < 0 below 2^-127
+  unsigned m = __funnelshift_r(lo2, (unsigned)h, 29);  // low 32 bits of (h:lo2) >> 29
+  m = h >= (255 << 20) ? 0x7f800000u : m;
+  m = h < (1 << 20) ? 0u : m;
+  return __uint_as_float(m | sign);
+}
+
+// binary32 -> binary64, exact for normal floats; subnormals give a signed zero, infinities and
+// NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u, m = b & 0x7fffffffu;
+  unsigned hi = (m >> 3) + (m >= 0x7f800000u ? (1792u << 20) : (896u << 20));
+  unsigned lo = m << 29;
+  if (m < 0x00800000u) hi = lo = 0u;
+  return join64(lo, hi | sign);
+}
+
+__device__ __forceinline__ double to_f64(float x) { return f2d(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
+// 1/x and 1/sqrt(x) for positive normal x in the FP32 range, for the mixed-precision path: an
+// FP32 estimate refined by one Newton-Raphson step in FP64. With an estimate of relative error
+// d the step leaves d^2 (1/x) and about 1.5 d^2 (1/sqrt x): below 2^-43, far below the FP32
+// rounding that every mixed-precision result gets.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double y = f2d(__frcp_rn(d2f(x)));
+  return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const double y = f2d(rsqrtf(d2f(x)));
+  const double r = fma(-x * y, y, 1.0);  // 1 - x y^2
+  return fma(0.5 * y, r, y);
+}
+
 // Viscosity law (Section 2): power law mu_ref (T/t_ref)^exp, or Sutherland.
 template <typename R>
 __device__ __forceinline__ R viscosity(const Coefs<R>& K, int law, R T) {

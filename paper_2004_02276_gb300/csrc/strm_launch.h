@@ -61,6 +61,9 @@ void launch_apply_forcing(const Dims& d, const Bufs& B, double* rhs, cudaStream_
 void launch_totals(const Dims& d, const Bufs& B, const double* w, cudaStream_t s);
 void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsigned char* out,
                   cudaStream_t s);
+// elementwise d2f / f2d over n elements
+void launch_d2f(const double* x, float* y, long long n, cudaStream_t s);
+void launch_f2d(const float* x, double* y, long long n, cudaStream_t s);
 void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double* theta, double* div,
                           cudaStream_t s);
 

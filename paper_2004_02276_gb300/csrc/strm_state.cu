@@ -133,6 +133,19 @@ __global__ void __launch_bounds__(256) k_export_interior(Dims d, const R* __rest
   dst[q] = (double)src[gidx(d, i, j, k)];
 }
 
+// elementwise FP64 <-> FP32 with the integer-pipe conversions of the mixed-precision kernels
+__global__ void __launch_bounds__(256) k_convert_d2f(const double* __restrict__ x, float* __restrict__ y,
+                                                     long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    y[q] = d2f(x[q]);
+}
+
+__global__ void __launch_bounds__(256) k_convert_f2d(const float* __restrict__ x, double* __restrict__ y,
+                                                     long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    y[q] = f2d(x[q]);
+}
+
 // ---------------------------------------------------------------------------------- launchers
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -231,6 +244,14 @@ void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double*
     if (theta) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.theta, theta);
     if (div) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.div, div);
   }
+}
+
+void launch_d2f(const double* x, float* y, long long n, cudaStream_t s) {
+  if (n > 0) k_convert_d2f<<<(unsigned)std::min<long long>(blocks_for(n, 256), 4096), 256, 0, s>>>(x, y, n);
+}
+
+void launch_f2d(const float* x, double* y, long long n, cudaStream_t s) {
+  if (n > 0) k_convert_f2d<<<(unsigned)std::min<long long>(blocks_for(n, 256), 4096), 256, 0, s>>>(x, y, n);
 }
 
 }  // namespace strm

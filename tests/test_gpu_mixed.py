@@ -88,6 +88,14 @@ def test_mixed_sensor_switch():
     assert max(err[0], err[1], err[4]) <= 2e-4, err
     assert max(err[2], err[3]) <= 2e-2, err
     print("mixed sensor-mode relative L2 error after 100 steps:", err)
+    # the domain totals (metric-weighted sums) see only what crosses the walls and the forcing:
+    # mass and bulk momentum are held exactly, total energy differs by the wall heat flux and
+    # forcing work of the two runs, transverse momentum stays at rounding level of |rho u|
+    cfg = O.make_cfg(case)
+    tm, to_ = np.array(O.totals(cfg, wm)), np.array(O.totals(cfg, wo))
+    terr = np.abs(tm - to_) / np.array([to_[0], to_[1], to_[1], to_[1], to_[4]])
+    print("mixed sensor-mode conserved-total error after 100 steps:", terr)
+    assert terr.max() <= 1e-5, terr
 
 
 def test_mixed_conserves_mass_and_bulk_flow():
