@@ -692,29 +692,31 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
 
 // ------------------------------------------------------------------------------ WENO5
 
-// Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2} = (f0..f4), written in first differences
-// a..d of the stencil: value = f2 + num/(6 den) with the candidates
-//   6 p_0 = 6 f2 + 5b - 2a,  6 p_1 = 6 f2 + b + 2c,  6 p_2 = 6 f2 + 4c - d,
-// smoothness indicators scaled by 4 (4 beta = 13/3 t^2 + t'^2, so eps4 = 4 eps keeps the
-// weights), and the weights d_k/(eps+beta_k)^2 multiplied through by 10 (eps+beta_0..2)^2
-// products. The caller folds the 1/6 into its own scaling.
+// Jiang-Shu WENO5 at i+1/2 from f_{i-2..i+2} = (f0..f4), written in first differences a..d of
+// the stencil. Each smoothness indicator is a quadratic form in two differences; completing the
+// square gives
+//   12 beta_0 = 16 [(a - 11b/8)^2 + (39/64) b^2],   12 beta_1 = 16 [(b - 5c/8)^2 + (39/64) c^2],
+//   12 beta_2 = 16 [(d - 11c/8)^2 + (39/64) c^2],
+// so q_k = (3/4) beta_k + eps3 (eps3 = (3/4) eps keeps the weights) takes ten operations, the
+// (39/64) c^2 term being shared by q_1 and q_2. The weights d_k/(eps+beta_k)^2 are multiplied
+// through by 10 (3/4)^2 q_0^2 q_1^2 q_2^2: (w0, 6 v1, 3 v2). With the candidates
+//   p_0 = f2 + (5b - 2a)/6,  p_1 = f2 + (b + 2c)/6,  p_2 = f2 + (4c - d)/6,
+// the result is f2 - num/(3 den), num = w0 e0 + v1 e1 + v2 e2 with e0 = a - 5b/2 = -3 (p_0 - f2),
+// e1 = -3b - 6c = -18 (p_1 - f2), e2 = 3d/2 - 6c = -9 (p_2 - f2), and den = w0 + 6 v1 + 3 v2.
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
-                                         double eps4, double& num, double& den) {
+                                         double eps3, double& num, double& den) {
   double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
-  double t0 = b - a, t1 = fma(3.0, b, -a);
-  double t2 = c - b, t3 = b + c;
-  double t4 = d - c, t5 = fma(-3.0, c, d);
-  // q_k = 4 beta_k + eps4
-  double q0 = fma(t1, t1, fma((13.0 / 3.0) * t0, t0, eps4));
-  double q1 = fma(t3, t3, fma((13.0 / 3.0) * t2, t2, eps4));
-  double q2 = fma(t5, t5, fma((13.0 / 3.0) * t4, t4, eps4));
+  double u0 = fma(-1.375, b, a), u1 = fma(-0.625, c, b), u2 = fma(-1.375, c, d);
+  double kb = 0.609375 * b, kc = 0.609375 * c;
+  double q0 = fma(u0, u0, fma(kb, b, eps3));
+  double qc = fma(kc, c, eps3);
+  double q1 = fma(u1, u1, qc), q2 = fma(u2, u2, qc);
   double Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
-  // weights d_k / Q_k times Q0 Q1 Q2: (w0, 6 v1, 3 v2); the 6 and 3 ride on the candidates
   double w0 = Q1 * Q2, v1 = Q0 * Q2, v2 = Q0 * Q1;
-  double c12 = 12.0 * c;
-  double e0 = fma(2.0, t1, -b);  // 5b - 2a: 6 (candidate 0 - f2)
-  double e1 = fma(6.0, b, c12);  // 6 (b + 2c): 36 (candidate 1 - f2)
-  double e2 = fma(-3.0, d, c12); // 3 (4c - d): 18 (candidate 2 - f2)
+  double c6 = 6.0 * c;
+  double e0 = fma(-2.5, b, a);
+  double e1 = fma(-3.0, b, -c6);
+  double e2 = fma(1.5, d, -c6);
   num = fma(v2, e2, fma(v1, e1, w0 * e0));
   den = fma(3.0, v2, fma(6.0, v1, w0));
 }
@@ -857,10 +859,10 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const bool acoustic = (k == 0 || k == 4);
-    const double eps4 = (acoustic ? 64.0 : 16.0) * C.k64.weno_eps;  // 4 s_k^2 eps
+    const double eps3 = (acoustic ? 12.0 : 3.0) * C.k64.weno_eps;  // (3/4) s_k^2 eps
     double np_, dp_, nm_, dm_;
-    weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps4, np_, dp_);
-    weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps4, nm_, dm_);
+    weno5_nd(gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4], eps3, np_, dp_);
+    weno5_nd(gm[k][5], gm[k][4], gm[k][3], gm[k][2], gm[k][1], eps3, nm_, dm_);
     num[k] = fma(np_, dm_, nm_ * dp_);
     den[k] = dp_ * dm_;
   }
@@ -869,7 +871,7 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const double s = (k == 0 || k == 4) ? 0.25 : 0.5;
-    g[k] = fma(s * (1.0 / 6.0), num[k] * rden[k], s * (gp[k][2] + gm[k][3]));
+    g[k] = fma(s * (-1.0 / 3.0), num[k] * rden[k], s * (gp[k][2] + gm[k][3]));
   }
   // back to conserved variables with the right eigenvectors
   double s04 = g[0] + g[4], cd40 = ca * (g[4] - g[0]);
