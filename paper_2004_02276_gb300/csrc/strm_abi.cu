@@ -245,6 +245,11 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
     for (int l = r + 1; l <= s.L; ++l) t += (double)K.a[l];
     K.ap[r] = R(t);
   }
+  for (int l = 0; l < 4; ++l) {
+    K.bx[l] = R((double)K.b[l] / (dx * dx));
+    K.bz[l] = R((double)K.b[l] / (dz * dz));
+  }
+  K.bxz0 = R((double)K.b[0] / (dx * dx) + (double)K.b[0] / (dz * dz));
   K.inv_dx = R(1.0 / dx);
   K.inv_dz = R(1.0 / dz);
   K.inv_dx2 = R((1.0 / dx) * (1.0 / dx));

@@ -1120,25 +1120,19 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
     // the eta-derivative of the stretched-y term taken back from d_y u (f_eta / y_eta^2 term
     // = (y_etaeta / y_eta^2) d_y u)
     const double c1h = __ldg(B.c1h + j);
+    const double cc = fma(K.b[0], c2, K.bxz0);  // centre weight of the three second differences
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) du[a][b] = __ldg(B.grad + (3 * a + b) * d.N + q);
-      double l0 = dsum2_c<L>(fld[a], n, 1, K.b) * K.inv_dx2;
-      l0 += dsum2_c<L>(fld[a], n, sy, K.b) * c2 - du[a][1] * c1h;
-      l0 += dsum2_c<L>(fld[a], n, sz, K.b) * K.inv_dz2;
-      lap[a] = l0;
+      lap[a] = fma(-du[a][1], c1h, lap_c<L>(fld[a], n, sy, sz, K, cc, c2));
     }
-    R s1, s2;
-    dsum12_c<L>(fld[3], n, 1, K.ax, K.b, s1, s2);
-    dT[0] = s1;
-    lapT = s2 * K.inv_dx2;
-    dsum12_c<L>(fld[3], n, sy, K.a, K.b, s1, s2);
-    dT[1] = s1 * hy;
-    lapT += s2 * c2 - s1 * c1;
-    dsum12_c<L>(fld[3], n, sz, K.az, K.b, s1, s2);
-    dT[2] = s1;
-    lapT += s2 * K.inv_dz2;
+    double g3[3];
+    const double l3 = lap_c<L>(fld[3], n, sy, sz, K, cc, c2, g3);
+    dT[0] = g3[0];
+    dT[1] = g3[1] * hy;
+    dT[2] = g3[2];
+    lapT = fma(-g3[1], c1, l3);
   } else {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {

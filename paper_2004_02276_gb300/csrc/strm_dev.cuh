@@ -49,6 +49,8 @@ template <typename R>
 struct Coefs {
   R a[4], b[4];                      // central first/second-derivative coefficients, 1..L
   R ax[4], az[4];                    // a_l / dx and a_l / dz (first derivatives along x and z)
+  R bx[4], bz[4];                    // b_l / dx^2 and b_l / dz^2, l = 0..L (second derivatives)
+  R bxz0;                            // bx[0] + bz[0]
   R aq[4];                           // a_l / 4 (pair weights of the split central flux)
   R ap[4];                           // a_{r+1} + .. + a_L, r = 0..L-1 (its pressure part)
   R inv_dx, inv_dz, inv_dx2, inv_dz2;
@@ -268,30 +270,39 @@ __device__ __forceinline__ R dsum2(const R* __restrict__ f, long long n, long lo
   return s2;
 }
 
-// FP64 forms of the two sums above with the centre weight b_0 = -2 sum_l b_l applied once,
-// s2 = b_0 f_0 + sum_l b_l (f_{+l} + f_{-l}): two operations per l instead of three. In FP64 the
-// cancellation of the large centre term costs ~1e-16 |f_0| / h^2, far below the truncation
-// error; FP32 keeps the difference form.
+// FP64 Laplacian numerator at node n on the stretched grid, without the y first-derivative term:
+//   cc f_0 + sum_l [bx_l (f_{+l x} + f_{-l x}) + bz_l (f_{+l z} + f_{-l z})]
+//          + c2 sum_l b_l (f_{+l y} + f_{-l y}),
+// cc = bx_0 + bz_0 + c2 b_0 (b_0 = -2 sum_l b_l, the centre weight of the stencil written as
+// sum_l b_l f_l): the three second differences share one centre term, applied once, and 1/dx^2,
+// 1/dz^2 ride on the x and z weights; two operations per l and direction instead of three. In
+// FP64 the cancellation of the large centre term costs ~1e-16 |f_0| / h^2, far below the
+// truncation error; FP32 keeps the difference form. With grad, also the first-derivative sums
+// along x, y, z (x and z already divided by dx and dz, y not yet by y_eta deta).
 template <int L>
-__device__ __forceinline__ double dsum2_c(const double* __restrict__ f, long long n, long long st,
-                                          const double* b) {
-  double s2 = b[0] * __ldg(f + n);
-#pragma unroll
-  for (int l = 1; l <= L; ++l) s2 = fma(b[l], __ldg(f + n + l * st) + __ldg(f + n - l * st), s2);
-  return s2;
-}
-
-template <int L>
-__device__ __forceinline__ void dsum12_c(const double* __restrict__ f, long long n, long long st,
-                                         const double* a, const double* b, double& s1, double& s2) {
-  s1 = 0.0;
-  s2 = b[0] * __ldg(f + n);
+__device__ __forceinline__ double lap_c(const double* __restrict__ f, long long n, long long sy, long long sz,
+                                        const Coefs<double>& K, double cc, double c2, double* grad = nullptr) {
+  double s = cc * __ldg(f + n), t = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    double fp = __ldg(f + n + l * st), fm = __ldg(f + n - l * st);
-    s1 = fma(a[l], fp - fm, s1);
-    s2 = fma(b[l], fp + fm, s2);
+    const double xp = __ldg(f + n + l), xm = __ldg(f + n - l);
+    const double yp = __ldg(f + n + l * sy), ym = __ldg(f + n - l * sy);
+    const double zp = __ldg(f + n + l * sz), zm = __ldg(f + n - l * sz);
+    s = fma(K.bx[l], xp + xm, s);
+    s = fma(K.bz[l], zp + zm, s);
+    t = fma(K.b[l], yp + ym, t);
+    if (grad) {
+      gx = fma(K.ax[l], xp - xm, gx);
+      gy = fma(K.a[l], yp - ym, gy);
+      gz = fma(K.az[l], zp - zm, gz);
+    }
   }
+  if (grad) {
+    grad[0] = gx;
+    grad[1] = gy;
+    grad[2] = gz;
+  }
+  return fma(c2, t, s);
 }
 
 // sum_l a_l (f_{+l} - f_{-l}) along a line (first-derivative numerator of order 2L)
