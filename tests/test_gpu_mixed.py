@@ -96,6 +96,11 @@ def test_mixed_sensor_switch():
     terr = np.abs(tm - to_) / np.array([to_[0], to_[1], to_[1], to_[1], to_[4]])
     print("mixed sensor-mode conserved-total error after 100 steps:", terr)
     assert terr.max() <= 1e-5, terr
+    # mean-velocity and Reynolds-stress profiles (x-z averages), relative to each profile's peak
+    pm, po = profiles(wm), profiles(wo)
+    perr = np.abs(pm - po).max(axis=1) / np.maximum(np.abs(po).max(axis=1), 1e-12)
+    print("mixed sensor-mode profile error after 100 steps (U, u'u', v'v', w'w', u'v'):", perr)
+    assert perr[0] <= 1e-5 and perr[1:].max() <= 5e-3, perr
 
 
 def test_mixed_conserves_mass_and_bulk_flow():
