@@ -312,6 +312,25 @@ int strm_ensemble_debug_flags(strm_ensemble* ens, unsigned* flags_host);
 
 void strm_ensemble_destroy(strm_ensemble* ens);
 
+/* ---- Overlap (Section 4: the paper overlaps the convective fluxes with the halo exchange).
+ * mode is a set of bits; every later right-hand side of this context then runs
+ *   STRM_OVERLAP_GHOST: the ghost-layer fill on a side stream while the Ducros sensor runs over
+ *     the nodes at least L from every face of the box (their stencils read no ghost node); the
+ *     sensor's boundary shell follows the join;
+ *   STRM_OVERLAP_FACES: the x, y and z face stages (classification, central and WENO fluxes),
+ *     which write separate flux arrays and lists, as three concurrent branches joined before
+ *     the assembly.
+ * Only the order of independent kernels changes: results are bit-identical to mode 0 (the
+ * sequential order, the default). The two side streams and their events are created on the
+ * first non-zero mode (with the context's device current) and released by strm_destroy; the
+ * captured step graph of strm_advance_n is rebuilt on its next call. In timing mode
+ * (strm_timing) all work stays on the context's stream. Concurrency pays on small grids, whose
+ * kernels do not fill the GPU; on grids of millions of points each kernel fills it alone.
+ * Null context or unknown bits: STRM_EINVAL; stream or event creation failure: STRM_ECUDA. */
+#define STRM_OVERLAP_GHOST 1
+#define STRM_OVERLAP_FACES 2
+int strm_set_overlap(strm_ctx* ctx, int mode);
+
 /* ---- Bounds checking. A library built with -DSTRM_DEBUG (paper_2004_02276_gb300/build.py,
  * debug=True: libstrm_debug.so) checks in every kernel the extreme nodes of each stencil, the
  * source node of each ghost and each face-list entry before using them; a violation ORs a code

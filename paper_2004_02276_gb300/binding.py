@@ -81,6 +81,7 @@ SIGNATURES = {
     "strm_weno_counts": ([_vp, _P(ctypes.c_longlong)], _i),
     "strm_inflow_df_bytes": ([_vp, _P(DF)], _sz),
     "strm_set_inflow_df": ([_vp, _P(DF), _P(_d), _vp, _sz], _i),
+    "strm_set_overlap": ([_vp, _i], _i),
     "strm_debug_build": ([], _i),
     "strm_debug_flags": ([_vp, _P(ctypes.c_uint)], _i),
     "strm_stats_bytes": ([_vp, _i], _sz),
@@ -305,6 +306,13 @@ class Solver:
         out = (ctypes.c_double * 5)()
         _check("strm_conserved_totals", lib().strm_conserved_totals(self.ctx, _ptr(self._state(w)), out))
         return list(out)
+
+    def set_overlap(self, mode=3):
+        """Concurrency inside a right-hand side (bit-identical results): bit 1 the ghost fill
+        beside the inner part of the sensor, bit 2 the x/y/z face stages as concurrent branches;
+        True means both, False or 0 the sequential order."""
+        mode = 3 if mode is True else int(mode)
+        _check("strm_set_overlap", lib().strm_set_overlap(self.ctx, mode))
 
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()

@@ -176,6 +176,10 @@ struct strm_ctx {
   // digital-filter inflow (caller-owned buffer)
   DFParams df = {};
   std::vector<double> df_host;  // profiles and filter coefficients, kept for the async upload
+  // overlap (strm_set_overlap): two side streams and the fork/join events of one right-hand side
+  int overlap = 0;  // STRM_OVERLAP_* bits
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -429,11 +433,39 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   // digital-filter inflow: a new plane once per step, after the step's dt is known
   if (dt_mode && C.bc[0] == kBcDigitalFilter)
     STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_df_update(d, x->df, B, false, st));
-  STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
-  STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, st));
+  // With overlap (not in timing mode, whose per-kernel events assume one stream): the ghost
+  // fill runs on a side stream while the sensor covers the nodes whose stencils read no ghost;
+  // the sensor's boundary shell follows the join. Later the x, y and z face stages, which
+  // write separate flux arrays and lists, run as three concurrent branches.
+  const int ovl = x->timing ? 0 : x->overlap;
+  if ((ovl & STRM_OVERLAP_GHOST) && sensor_inner_nodes(d, C.L) > 0) {
+    STRM_CK(cudaEventRecord(x->ev[0], st));
+    STRM_CK(cudaStreamWaitEvent(x->side[0], x->ev[0], 0));
+    STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, x->side[0]));
+    STRM_CK(cudaEventRecord(x->ev[1], x->side[0]));
+    STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, 1, st));
+    STRM_CK(cudaStreamWaitEvent(st, x->ev[1], 0));
+    STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, 2, st));
+  } else {
+    STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
+    STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, 0, st));
+  }
   if (C.mixed && C.weno_mode == 1) STRM_LAUNCH(STRM_K_SENSOR, launch_band_theta(d, C, B, st));
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
-  if (C.convective) {
+  if (C.convective && (ovl & STRM_OVERLAP_FACES)) {
+    STRM_CK(cudaEventRecord(x->ev[2], st));
+    for (int b = 0; b < 2; ++b) STRM_CK(cudaStreamWaitEvent(x->side[b], x->ev[2], 0));
+    for (int dir = 0; dir < 3; ++dir) {
+      cudaStream_t sd = dir == 0 ? st : x->side[dir - 1];
+      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, sd));
+      if (C.weno_mode != STRM_WENO_OFF)
+        STRM_LAUNCH(STRM_K_WENO_X + dir, launch_weno_dir(d, C, B, dir, x->weno_grid, sd));
+    }
+    for (int b = 0; b < 2; ++b) {
+      STRM_CK(cudaEventRecord(x->ev[3 + b], x->side[b]));
+      STRM_CK(cudaStreamWaitEvent(st, x->ev[3 + b], 0));
+    }
+  } else if (C.convective) {
     for (int dir = 0; dir < 3; ++dir)
       STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, st));
     if (C.weno_mode != STRM_WENO_OFF) {
@@ -930,6 +962,21 @@ int strm_convert_f32_f64(const float* x, double* y, long long n, void* stream) {
   return STRM_OK;
 }
 
+int strm_set_overlap(strm_ctx* x, int mode) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  if (mode & ~(STRM_OVERLAP_GHOST | STRM_OVERLAP_FACES)) return fail(STRM_EINVAL, "unknown overlap bits");
+  if (mode && !x->side[0]) {
+    for (int b = 0; b < 2; ++b) STRM_CK(cudaStreamCreateWithFlags(&x->side[b], cudaStreamNonBlocking));
+    for (int e = 0; e < 5; ++e) STRM_CK(cudaEventCreateWithFlags(&x->ev[e], cudaEventDisableTiming));
+  }
+  x->overlap = mode;
+  if (x->gexec) {  // the captured graph has the other launch structure
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
+  return STRM_OK;
+}
+
 int strm_debug_build(void) { return kDebug ? 1 : 0; }
 
 int strm_debug_flags(strm_ctx* x, unsigned* flags_host) {
@@ -980,7 +1027,7 @@ int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsign
   launch_prims(x->d, x->C, x->B, w, false, x->stream);
   if (x->C.bc[0] == kBcRecycle) launch_recycle(x->d, x->C, x->B, x->stream);
   launch_ghost_prims(x->d, x->C, x->B, x->stream);
-  launch_sensor(x->d, x->C, x->B, x->stream);
+  launch_sensor(x->d, x->C, x->B, 0, x->stream);
   if (x->C.mixed && x->C.weno_mode == 1) launch_band_theta(x->d, x->C, x->B, x->stream);
   launch_ghost_scalars(x->d, x->C, x->B, x->stream);
   launch_export_sensor(x->d, x->C, x->B, theta, div, x->stream);
@@ -1059,6 +1106,10 @@ void strm_destroy(strm_ctx* x) {
   for (cudaEvent_t e : x->events) cudaEventDestroy(e);
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
   if (x->cap) cudaStreamDestroy(x->cap);
+  for (cudaStream_t sd : x->side)
+    if (sd) cudaStreamDestroy(sd);
+  for (cudaEvent_t e : x->ev)
+    if (e) cudaEventDestroy(e);
   delete x;
 }
 

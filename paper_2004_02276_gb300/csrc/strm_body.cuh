@@ -519,15 +519,64 @@ __device__ __forceinline__ void block_append1(bool mine, int q, int* list, unsig
   if (mine) list[s_base + s_w[warp] + __popc(m & ((1u << lane) - 1u))] = q;
 }
 
+// Node of sensor thread t for a part of the grid: region 0 all interior nodes; region 1 the
+// nodes at least L from every face of the box (the inner box), whose stencils read no ghost
+// node, so they can run while the ghost layers are being filled; region 2 the others (the
+// shell), enumerated as the L planes at each z end, then the L rows at each y end of the
+// remaining planes, then the L nodes at each x end of the remaining rows. Region 1 and 2 are
+// used only when the inner box is not empty.
+__device__ __forceinline__ bool sensor_node(const Dims& d, int region, int L, long long t, long long& q) {
+  const long long nx = d.nx, ny = d.ny, nz = d.nz;
+  const long long bx = nx - 2 * L, by = ny - 2 * L, bz = nz - 2 * L;
+  long long i, j, k;
+  if (region == 0) {
+    q = t;
+    return t < d.N;
+  }
+  if (region == 1) {
+    if (t >= bx * by * bz) return false;
+    i = t % bx;
+    const long long r = t / bx;
+    j = r % by;
+    k = r / by;
+    q = ((k + L) * ny + (j + L)) * nx + (i + L);
+    return true;
+  }
+  const long long zn = 2 * L * nx * ny, yn = bz * 2 * L * nx, xn = bz * by * 2 * L;
+  if (t < zn) {  // z-end planes
+    const long long p = t / (nx * ny), r = t % (nx * ny);
+    k = p < L ? p : nz - 2 * L + p;
+    j = r / nx;
+    i = r % nx;
+  } else if (t < zn + yn) {  // y-end rows of the inner planes
+    const long long u = t - zn, row = u / nx;
+    i = u % nx;
+    k = L + row / (2 * L);
+    const long long jr = row % (2 * L);
+    j = jr < L ? jr : ny - 2 * L + jr;
+  } else if (t < zn + yn + xn) {  // x-end nodes of the inner rows
+    const long long u = t - zn - yn, ir = u % (2 * L), row = u / (2 * L);
+    i = ir < L ? ir : nx - 2 * L + ir;
+    j = L + row % by;
+    k = L + row / by;
+  } else {
+    return false;
+  }
+  q = (k * ny + j) * nx + i;
+  return true;
+}
+
 template <int L, typename R>
-__device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, const Bufs& B, int blk) {
-  long long q = (long long)blk * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, const Bufs& B, int blk,
+                                            int region = 0) {
+  long long q;
+  const bool mine = sensor_node(d, region, L, (long long)blk * blockDim.x + threadIdx.x, q);
   if constexpr (!std::is_same<R, double>::value) {
     // mixed precision: FP32 theta; the switch decides on an FP64 theta field, which holds the
     // FP32 value, except at the nodes whose FP32 theta falls within 0.2 % of the threshold
     // (far wider than its FP32 error): those are listed here and get the FP64 theta from the
     // FP64 velocities (body_band_theta), so the decisions are the ones FP64 takes on this state
-    bool valid = q < d.N, band = false;
+    bool valid = mine, band = false;
     if (valid) {
       int i, j, k;
       node_ijk(d, q, i, j, k);
@@ -547,7 +596,7 @@ __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, cons
     block_append1(band, (int)q, B.band, B.wcount + 3);
     return;
   }
-  if (q >= d.N) return;
+  if (!mine) return;
   int i, j, k;
   node_ijk(d, q, i, j, k);
   if (!stencil_ok(d, i, j, k, 0, L, L, kDbgNode) || !stencil_ok(d, i, j, k, 1, L, L, kDbgNode) ||

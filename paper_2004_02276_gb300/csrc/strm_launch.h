@@ -47,7 +47,10 @@ bool ctx_df(strm_ctx* x, DFParams* F);
 // column sums), mode 1 adds z means to acc[24][ny][nx]
 void launch_stats(const Dims& d, const Consts& C, const double* w, double* acc, double* scr, int mode,
                   cudaStream_t s);
-void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// Ducros sensor over region 0 (all interior nodes), 1 (the nodes whose stencils read no ghost:
+// sensor_inner_nodes of them) or 2 (the others)
+long long sensor_inner_nodes(const Dims& d, int L);
+void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, int region, cudaStream_t s);
 // mixed precision: FP64 theta at the nodes the sensor listed as near the switch threshold
 void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);

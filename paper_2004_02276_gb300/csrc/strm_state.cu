@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(128) k_band_theta(Dims d, Consts C, Bufs B) {
 }
 
 template <int L, typename R>
-__global__ void __launch_bounds__(256) k_sensor(Dims d, Consts C, Bufs B) {
-  body_sensor<L, R>(d, C, B, blockIdx.x);
+__global__ void __launch_bounds__(256) k_sensor(Dims d, Consts C, Bufs B, int region) {
+  body_sensor<L, R>(d, C, B, blockIdx.x, region);
 }
 
 __global__ void k_force_finalize(Bufs B, int nparts, double inv_vtot) {
@@ -184,14 +184,22 @@ void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream
   else k_band_theta<2><<<nb, 128, 0, s>>>(d, C, B);
 }
 
-void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s) {
-  unsigned nb = blocks_for(d.N, 256);
+long long sensor_inner_nodes(const Dims& d, int L) {
+  const long long bx = d.nx - 2 * L, by = d.ny - 2 * L, bz = d.nz - 2 * L;
+  return (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0;
+}
+
+void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, int region, cudaStream_t s) {
+  const long long inner = sensor_inner_nodes(d, C.L);
+  const long long n = region == 0 ? d.N : (region == 1 ? inner : d.N - inner);
+  if (n <= 0) return;
+  unsigned nb = blocks_for(n, 256);
   if (C.mixed) {
-    if (C.L == 3) k_sensor<3, float><<<nb, 256, 0, s>>>(d, C, B);
-    else k_sensor<2, float><<<nb, 256, 0, s>>>(d, C, B);
+    if (C.L == 3) k_sensor<3, float><<<nb, 256, 0, s>>>(d, C, B, region);
+    else k_sensor<2, float><<<nb, 256, 0, s>>>(d, C, B, region);
   } else {
-    if (C.L == 3) k_sensor<3, double><<<nb, 256, 0, s>>>(d, C, B);
-    else k_sensor<2, double><<<nb, 256, 0, s>>>(d, C, B);
+    if (C.L == 3) k_sensor<3, double><<<nb, 256, 0, s>>>(d, C, B, region);
+    else k_sensor<2, double><<<nb, 256, 0, s>>>(d, C, B, region);
   }
 }
 
