@@ -2,7 +2,7 @@
 extreme nodes of each stencil, each ghost source and each list entry before using them and
 records a violation in the context's error word instead of faulting. Run on every code path
 (FP64 and mixed channels, the paper's L = 2 settings, boundary layers with each face kind,
-the digital-filter inflow, statistics and the batched ensemble), it must record nothing and
+the digital-filter inflow, statistics, the overlap modes and the batched ensemble), it must record nothing and
 give the oracle's right-hand sides."""
 import json
 import os
@@ -32,12 +32,17 @@ cases = {{
     "bl-sinh-mixed": bl("bls", 48, 40, 12, 7.0, 6.0, 1.5, y_map="sinh1", beta=4.0, precision="mixed"),
     "open-char": bl("open", 40, 24, 10, 6.0, 6.0, 1.5, bc_xmin="char", bc_ymin="char", weno_mode="all"),
     "bl-df": bl("bldf", 36, 30, 10, 5.0, 6.0, 1.5, bc_xmin="df", df_ny=2, df_nz=2, df_tau=0.3, df_seed=3),
+    # overlap: the sensor's inner-box and shell regions, concurrent face branches
+    "channel-fp64-overlap": inputs.C1,
+    "sbli-mixed-overlap": bl("sblim", 64, 40, 12, 12.0, 6.0, 1.5, shock=True, noise=0.003, precision="mixed"),
 }}
 out = {{}}
 for name, c in cases.items():
     prof = inputs.df_profiles(c) if c.bc_xmin == "df" else None
     w0 = inputs.channel_state(c, 0) if c.kind == "channel" else inputs.bl_state(c, 0)
     s = binding.Solver(c, inflow=prof)
+    if name.endswith("-overlap"):
+        s.set_overlap(3)
     w = torch.from_numpy(w0).cuda()
     r = s.compute_rhs(w).cpu().numpy()
     cfg = O.make_cfg(c, df=O.DFState(c, prof) if prof is not None else None)
