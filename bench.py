@@ -322,19 +322,22 @@ def run_ours(args, world, rank, local):
         }}
     if not args.no_batched:
         out.setdefault("variants", {})["batched"] = run_batched(args, world, local, m64["value"])
+        if not args.no_mixed:
+            out["variants"]["batched_mixed"] = run_batched(args, world, local, mm["value"], "mixed")
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def run_batched(args, world, local, large_grid_value):
+def run_batched(args, world, local, large_grid_value, precision="fp64"):
     """The batched workload: 64 independent channels of uneven size, Mach and Reynolds number
     (44.7 M points in all), advanced by the ensemble kernels, one graph replay per step, launch
-    shapes from the autotuner (run before the warm-up, outside the timed region)."""
+    shapes from the autotuner (run before the warm-up, outside the timed region). The per-point
+    rate is compared with the large grid's rate in the same precision."""
     import torch
 
     from paper_2004_02276_gb300 import binding
 
-    cases = inputs.ensemble_cases(seed=0)
+    cases = inputs.ensemble_cases(seed=0, precision=precision)
     npts = sum(c.npts for c in cases)
     E = binding.Ensemble(cases, device=f"cuda:{local}")
     ws = [torch.from_numpy(inputs.channel_state(c)).cuda() for c in cases]
@@ -356,7 +359,7 @@ def run_batched(args, world, local, large_grid_value):
     tot = E.totals(ws)
     E.close()
     return {"value": value, "ms_per_step": ms / args.steps, "instances": len(cases),
-            "points": npts, "dtype": "f64",
+            "points": npts, "dtype": "f64" if precision == "fp64" else "f32 flux / f64 state",
             "per_point_vs_large_grid": value / large_grid_value,
             "tuned": {"weno_block": choice[0], "weno_blocks_per_sm": choice[1],
                       "central_blocks_per_sm": choice[2]},

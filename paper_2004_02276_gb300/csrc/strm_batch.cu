@@ -147,8 +147,12 @@ __global__ void __launch_bounds__(256) kb_central(BatchIndex X) {
   }
 }
 
+// At most 128 threads per block, with the register budget of 3 (FP64) or 4 (mixed) resident
+// blocks per SM: the instance fields read from the table in global memory live in registers,
+// where the single-context kernel reads them from its constant parameter bank, and without the
+// bound the compiler took 210 (FP64) and 138 (mixed) registers.
 template <int DIR, bool MIXED>
-__global__ void __launch_bounds__(256) kb_weno(BatchIndex X) {
+__global__ void __launch_bounds__(128, MIXED ? 4 : 3) kb_weno(BatchIndex X) {
   long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long ts = (long long)gridDim.x * blockDim.x;
   for (int e = 0; e < X.n; ++e) {
@@ -523,7 +527,7 @@ int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old,
   // WENO launch shape first (the dominant kernel), then the central list grid
   Tuning bestT = E->tune;
   float best = 1e30f;
-  const int blocks[3] = {64, 128, 256}, per_sm[3] = {4, 8, 16};
+  const int blocks[3] = {32, 64, 128}, per_sm[3] = {4, 8, 16};  // kb_weno takes <= 128 threads
   for (int bi = 0; bi < 3 && rc == STRM_OK; ++bi)
     for (int gi = 0; gi < 3 && rc == STRM_OK; ++gi) {
       E->tune.weno_block = blocks[bi];
