@@ -161,8 +161,10 @@ __global__ void __launch_bounds__(128, MIXED ? 4 : 3) kb_weno(BatchIndex X) {
   }
 }
 
+// Register budget of 3 (mixed) or 2 (FP64) resident blocks, for the same reason as kb_weno
+// (unbounded, the mixed instance took 114 registers against 62 in the single-context kernel).
 template <int L, typename R>
-__global__ void __launch_bounds__(256) kb_assemble(BatchIndex X) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) kb_assemble(BatchIndex X) {
   __shared__ double sh[32];
   int blk;
   const Inst& I = block_inst(X, kKindNode, blk);
