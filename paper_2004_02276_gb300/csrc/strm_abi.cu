@@ -420,7 +420,7 @@ struct LaunchScope {
 // One right-hand-side evaluation into R (stream order). With dt_mode, stage-0 work also sets the
 // step: dt_fixed > 0 is taken as is, otherwise the CFL step from the primitive pass.
 int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cfl, double dt_fixed,
-                cudaStream_t st) {
+                cudaStream_t st, const RkFuse& rk = RkFuse{nullptr, nullptr, 0.0, 0.0}) {
   const Dims& d = x->d;
   const Consts& C = x->C;
   const Bufs& B = x->B;
@@ -479,7 +479,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
       }
     }
   }
-  STRM_LAUNCH(STRM_K_ASSEMBLE, launch_assemble(d, C, B, R, st));
+  STRM_LAUNCH(STRM_K_ASSEMBLE, launch_assemble(d, C, B, R, rk, st));
   if (C.forcing) STRM_LAUNCH(STRM_K_FORCE, launch_force_finalize(d, C, B, st));
   STRM_CK_LAUNCH();
   return STRM_OK;
@@ -487,6 +487,11 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
 
 int enqueue_step(strm_ctx* x, double* w, double* r_old, double dt, double cfl, cudaStream_t st) {
   for (int stage = 0; stage < 3; ++stage) {
+    if (!x->C.forcing) {  // no forcing to reduce first: the assembly applies the stage update
+      int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st, RkFuse{w, r_old, kAlpha[stage], kBeta[stage]});
+      if (rc) return rc;
+      continue;
+    }
     int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st);
     if (rc) return rc;
     STRM_LAUNCH(STRM_K_RK_UPDATE,

@@ -1246,7 +1246,8 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
 // plus the viscous terms, in precision R; stored in FP64 with the forcing partial sums.
 template <int L, typename R>
 __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, const Bufs& B,
-                                              double* __restrict__ Rout, int blk, double* sh) {
+                                              double* __restrict__ Rout, int blk, double* sh,
+                                              const RkFuse& rk = RkFuse{nullptr, nullptr, 0.0, 0.0}) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   double fpart = 0.0;
   bool live = q < d.N;
@@ -1306,9 +1307,25 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
 #pragma unroll
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }
+    if (rk.w) {
+      // the RK stage update of this node (body_rk_update without the forcing terms): the
+      // residual stays in registers instead of a round trip through memory
+      const double dt = B.scal[kScalDt];
+      const double ad = rk.alpha * dt, bd = rk.beta * dt;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
-    if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
+      for (int m = 0; m < 5; ++m) {
+        const long long e = m * d.N + q;
+        const double rr = (m == 0 && sizeof(R) != sizeof(double)) ? mass64 : to_f64(res[m]);
+        double wn = rk.w[e] + bd * rr;
+        if (rk.alpha != 0.0) wn += ad * rk.r_old[e];
+        rk.w[e] = wn;
+        rk.r_old[e] = rr;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
+      if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
+    }
     fpart = to_f64(res[1]) * __ldg(B.vol + j);
   }
   if (C.forcing) {

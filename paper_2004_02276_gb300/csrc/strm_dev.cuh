@@ -126,6 +126,14 @@ template <typename R> __device__ __forceinline__ const Coefs<R>& coefs(const Con
 template <> __device__ __forceinline__ const Coefs<double>& coefs<double>(const Consts& C) { return C.k64; }
 template <> __device__ __forceinline__ const Coefs<float>& coefs<float>(const Consts& C) { return C.k32; }
 
+// RK stage update fused into the assembly (flows without forcing): w <- w + dt (alpha R_old +
+// beta R), R_old <- R, with dt from the device scalars; w == nullptr: no fusion.
+struct RkFuse {
+  double* w;
+  double* r_old;
+  double alpha, beta;
+};
+
 // device scalars
 enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalRecycle = 4, kScalCount = 16 };
 

@@ -29,9 +29,10 @@ __global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
 }
 
 template <int L, typename R>
-__global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, double* __restrict__ Rout) {
+__global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, double* __restrict__ Rout,
+                                                  RkFuse rk) {
   __shared__ double sh[32];
-  body_assemble<L, R>(d, C, B, Rout, blockIdx.x, sh);
+  body_assemble<L, R>(d, C, B, Rout, blockIdx.x, sh, rk);
 }
 
 // ------------------------------------------------------------------------------ launchers
@@ -80,14 +81,15 @@ void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int
   }
 }
 
-void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, cudaStream_t s) {
+void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, const RkFuse& rk,
+                     cudaStream_t s) {
   unsigned nb = blocks_for(d.N, kRedBlock);
   if (C.mixed) {
-    if (C.L == 3) k_assemble<3, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
-    else k_assemble<2, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+    if (C.L == 3) k_assemble<3, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R, rk);
+    else k_assemble<2, float><<<nb, kRedBlock, 0, s>>>(d, C, B, R, rk);
   } else {
-    if (C.L == 3) k_assemble<3, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
-    else k_assemble<2, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R);
+    if (C.L == 3) k_assemble<3, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R, rk);
+    else k_assemble<2, double><<<nb, kRedBlock, 0, s>>>(d, C, B, R, rk);
   }
 }
 

@@ -56,7 +56,9 @@ void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
-void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, cudaStream_t s);
+// residual into R, or (rk.w set) the RK stage update of w and r_old without writing R
+void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, const RkFuse& rk,
+                     cudaStream_t s);
 void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_rk_update(const Dims& d, const Consts& C, const Bufs& B, double* w, double* r_old,
                       double alpha, double beta, cudaStream_t s);
