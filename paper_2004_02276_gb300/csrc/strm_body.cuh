@@ -54,6 +54,8 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
     B.lam[5][n] = ww + c;
     P.mu[n] = viscosity(C.k64, C.visc_law, T);
     P.srho[n] = rho * rs;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) B.mom[dd][n] = w[(1 + dd) * d.N + q];
     if (want_cfl)
       spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
   }
@@ -93,6 +95,8 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     P.p[n] = p;
     P.H[n] = H;
     P.srho[n] = rho * rs;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) B.mom[dd][n] = w[(1 + dd) * d.N + q];
     float rf = d2f(rho), pf = d2f(p), Tf = d2f(T);
     float cf = sqrtf(C.k32.gamma * pf / rf);
     F.rho[n] = rf;
@@ -205,6 +209,9 @@ __device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, lon
   double H = __fma_rn(C.cp, g.T, __dmul_rn(0.5, q2));
   P.H[dst] = H;
   P.srho[dst] = sqrt(g.rho);
+  B.mom[0][dst] = __dmul_rn(g.rho, g.u);
+  B.mom[1][dst] = __dmul_rn(g.rho, g.v);
+  B.mom[2][dst] = __dmul_rn(g.rho, g.w);
   if (!C.mixed) {
     double c = sqrt(C.gamma * g.p / g.rho);
     P.c[dst] = c;
@@ -248,6 +255,8 @@ __device__ __forceinline__ void copy_node(const Nodes<R>& P, long long dst, long
 __device__ __forceinline__ void copy_ghost(const Consts& C, const Bufs& B, long long dst, long long src) {
   copy_node(B.n64, dst, src, !C.mixed);
   B.n64.srho[dst] = B.n64.srho[src];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) B.mom[dd][dst] = B.mom[dd][src];
   if (C.mixed) {
     copy_node(B.n32, dst, src, true);
   } else {
@@ -879,7 +888,7 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
     double un = uu[DIR];
-    double run = rho * un;
+    double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;
@@ -998,7 +1007,7 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
     double un = uu[DIR];
-    double run = rho * un;
+    double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;

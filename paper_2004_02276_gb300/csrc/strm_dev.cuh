@@ -104,6 +104,8 @@ struct Bufs {
                                                 //   the threshold (count in wcount[3])
   double* lam[6];                               // FP64: u - c, u + c, v - c, v + c, w - c, w + c
                                                 //   at the nodes (ghosted), for the LF speeds
+  double* mom[3];                               // rho u, rho v, rho w at the nodes (ghosted, FP64
+                                                //   in both precisions), for the WENO projection
   double* grad;                                 // FP64: velocity gradients d_b u_a at the
                                                 //   interior nodes, [3a + b][N], from the sensor
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int u
 }
 
 template <int DIR, bool MIXED>
-__global__ void __launch_bounds__(128) k_weno(Dims d, Consts C, Bufs B) {
+__global__ void __launch_bounds__(128, MIXED ? 5 : 3) k_weno(Dims d, Consts C, Bufs B) {
   body_weno<DIR, MIXED>(d, C, B, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                         (long long)gridDim.x * blockDim.x);
 }
