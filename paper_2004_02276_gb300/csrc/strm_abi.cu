@@ -45,9 +45,9 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Node fields held in FP64 (all of them in FP64 precision; those the FP64 characteristic
 // projection reads in mixed precision) and in FP32 (mixed precision only).
-// FP64 node arrays: FP64 precision 12 fields, the 6 wave speeds u_d -+ c and the 3 momentum
-// components; mixed precision 9 fields and the 3 momentum components
-const int kN64All = 21, kN64Mixed = 12, kN32Mixed = 11;
+// FP64 node arrays: FP64 precision 12 fields, the 6 wave speeds u_d -+ c, the 3 momentum
+// components and the 3 normal momentum fluxes; mixed precision 9 fields and the same 6
+const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11;
 
 struct Layout {
   Dims d;
@@ -561,7 +561,10 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
   if (L.mixed) {
     double** f64[9] = {&N64.rho, &N64.u, &N64.v, &N64.w, &N64.p, &N64.T, &N64.H, &N64.srho, &N64.theta};
     for (int f = 0; f < 9; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
-    for (int dd = 0; dd < 3; ++dd) x->B.mom[dd] = (double*)(ws + L.off_n64[9 + dd]);
+    for (int dd = 0; dd < 3; ++dd) {
+      x->B.mom[dd] = (double*)(ws + L.off_n64[9 + dd]);
+      x->B.mflux[dd] = (double*)(ws + L.off_n64[12 + dd]);
+    }
     float** f32[kN32Mixed] = {&N32.rho, &N32.u, &N32.v, &N32.w, &N32.p, &N32.T,
                               &N32.H,   &N32.c, &N32.mu, &N32.theta, &N32.div};
     for (int f = 0; f < kN32Mixed; ++f) *f32[f] = (float*)(ws + L.off_n32[f]);
@@ -570,7 +573,10 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
                         &N64.H,   &N64.c, &N64.mu, &N64.theta, &N64.div, &N64.srho};
     for (int f = 0; f < 12; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
     for (int f = 0; f < 6; ++f) x->B.lam[f] = (double*)(ws + L.off_n64[12 + f]);
-    for (int dd = 0; dd < 3; ++dd) x->B.mom[dd] = (double*)(ws + L.off_n64[18 + dd]);
+    for (int dd = 0; dd < 3; ++dd) {
+      x->B.mom[dd] = (double*)(ws + L.off_n64[18 + dd]);
+      x->B.mflux[dd] = (double*)(ws + L.off_n64[21 + dd]);
+    }
   }
   for (int dir = 0; dir < 3; ++dir) {
     x->B.fh64[dir] = L.mixed ? nullptr : (double*)(ws + L.off_fh[dir]);

@@ -54,8 +54,13 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
     B.lam[5][n] = ww + c;
     P.mu[n] = viscosity(C.k64, C.visc_law, T);
     P.srho[n] = rho * rs;
+    const double vel[3] = {u, v, ww};
 #pragma unroll
-    for (int dd = 0; dd < 3; ++dd) B.mom[dd][n] = w[(1 + dd) * d.N + q];
+    for (int dd = 0; dd < 3; ++dd) {
+      const double m = w[(1 + dd) * d.N + q];
+      B.mom[dd][n] = m;
+      B.mflux[dd][n] = fma(m, vel[dd], p);
+    }
     if (want_cfl)
       spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
   }
@@ -95,8 +100,13 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     P.p[n] = p;
     P.H[n] = H;
     P.srho[n] = rho * rs;
+    const double vel[3] = {u, v, ww};
 #pragma unroll
-    for (int dd = 0; dd < 3; ++dd) B.mom[dd][n] = w[(1 + dd) * d.N + q];
+    for (int dd = 0; dd < 3; ++dd) {
+      const double m = w[(1 + dd) * d.N + q];
+      B.mom[dd][n] = m;
+      B.mflux[dd][n] = fma(m, vel[dd], p);
+    }
     float rf = d2f(rho), pf = d2f(p), Tf = d2f(T);
     float cf = sqrtf(C.k32.gamma * pf / rf);
     F.rho[n] = rf;
@@ -209,9 +219,13 @@ __device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, lon
   double H = __fma_rn(C.cp, g.T, __dmul_rn(0.5, q2));
   P.H[dst] = H;
   P.srho[dst] = sqrt(g.rho);
-  B.mom[0][dst] = __dmul_rn(g.rho, g.u);
-  B.mom[1][dst] = __dmul_rn(g.rho, g.v);
-  B.mom[2][dst] = __dmul_rn(g.rho, g.w);
+  const double gm[3] = {__dmul_rn(g.rho, g.u), __dmul_rn(g.rho, g.v), __dmul_rn(g.rho, g.w)};
+  const double gv[3] = {g.u, g.v, g.w};
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    B.mom[dd][dst] = gm[dd];
+    B.mflux[dd][dst] = __fma_rn(gm[dd], gv[dd], g.p);
+  }
   if (!C.mixed) {
     double c = sqrt(C.gamma * g.p / g.rho);
     P.c[dst] = c;
@@ -256,7 +270,10 @@ __device__ __forceinline__ void copy_ghost(const Consts& C, const Bufs& B, long 
   copy_node(B.n64, dst, src, !C.mixed);
   B.n64.srho[dst] = B.n64.srho[src];
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) B.mom[dd][dst] = B.mom[dd][src];
+  for (int dd = 0; dd < 3; ++dd) {
+    B.mom[dd][dst] = B.mom[dd][src];
+    B.mflux[dd][dst] = B.mflux[dd][src];
+  }
   if (C.mixed) {
     copy_node(B.n32, dst, src, true);
   } else {
@@ -887,16 +904,15 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     double rho = __ldg(P.rho + nn);
     double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double un = uu[DIR];
     double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;
     double Aw = fma(rho, K, -b1p);  // acoustic rows: (l0 + l4) w = A_w, c (l0 - l4) w = cB_w
     double Af = fma(run, K, -b1p * un_a);
-    double du = un_a - un;
-    double cBw = rho * du;
-    double cBf = fma(run, du, -p);
+    // c B rows: rho (ua_n - u_n) and rho u_n (ua_n - u_n) - p = rho u_n ua_n - (rho u_n^2 + p)
+    double cBw = fma(rho, un_a, -run);
+    double cBf = fma(run, un_a, -__ldg(B.mflux[DIR] + nn));
     double Sw = fma(ic, cBw, Aw), Sf = fma(ic, cBf, Af), Dw = fma(-ic, cBw, Aw), Df = fma(-ic, cBf, Af);
     gp[0][q] = fma(lam0, Sw, Sf);
     gm[0][q] = fma(-lam0, Sw, Sf);
@@ -1006,15 +1022,13 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     double rho = __ldg(P.rho + nn);
     double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
     double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double un = uu[DIR];
     double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;
     double Aw = fma(rho, K, -b1p);
     double Af = fma(run, K, -b1p * un_a);
-    double du = un_a - un;
-    double cBw = rho * du, cBf = fma(run, du, -p);
+    double cBw = fma(rho, un_a, -run), cBf = fma(run, un_a, -__ldg(B.mflux[DIR] + nn));
     float Sw = d2f(fma(ic, cBw, Aw)), Sf = d2f(fma(ic, cBf, Af)), Dw = d2f(fma(-ic, cBw, Aw)),
           Df = d2f(fma(-ic, cBf, Af));
     float Awf = d2f(Aw), Aff = d2f(Af);

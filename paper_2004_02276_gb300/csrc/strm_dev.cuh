@@ -106,6 +106,8 @@ struct Bufs {
                                                 //   at the nodes (ghosted), for the LF speeds
   double* mom[3];                               // rho u, rho v, rho w at the nodes (ghosted, FP64
                                                 //   in both precisions), for the WENO projection
+  double* mflux[3];                             // rho u_d^2 + p, d = x, y, z (the normal momentum
+                                                //   flux; ghosted, FP64), for the WENO projection
   double* grad;                                 // FP64: velocity gradients d_b u_a at the
                                                 //   interior nodes, [3a + b][N], from the sensor
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j
