@@ -47,8 +47,8 @@ FLOPS_PER_UNIT_MIXED = {"weno_x": 180, "weno_y": 180, "weno_z": 180}
 # DRAM bytes (read + write) per WENO face from one ncu capture of the current kernels on the
 # 192x144x96 channel (dram__bytes_read.sum + dram__bytes_write.sum of the launch over its WENO
 # faces), scaled to a launch by the faces it processes.
-DRAM_BYTES_PER_UNIT = {"weno_x": 112.9, "weno_y": 152.3, "weno_z": 332.9}
-DRAM_BYTES_PER_UNIT_MIXED = {"weno_x": 102.0, "weno_y": 133.2, "weno_z": 204.5}
+DRAM_BYTES_PER_UNIT = {"weno_x": 131.9, "weno_y": 190.8, "weno_z": 423.6}
+DRAM_BYTES_PER_UNIT_MIXED = {"weno_x": 120.5, "weno_y": 160.6, "weno_z": 242.9}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 (the profiling recipe's unit table); a probe of
 # dependent-chain-free DFMA on this pool measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 1.25

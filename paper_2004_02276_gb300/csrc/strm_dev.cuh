@@ -5,8 +5,8 @@
 //   node fields (workspace): ghosted [nz+2G][ny+2G][px]; the interior node (i,j,k) sits at
 //     ((k+G)*py + j+G)*px + i+GX; GX = 4 keeps interior rows 32-byte aligned, px is a multiple
 //     of 4. FP64 precision keeps every node field in FP64. Mixed precision keeps the fields the
-//     characteristic projection reads (rho, u, v, w, p, T, H, sqrt rho) in FP64 and FP32 copies
-//     of all fields for the FP32 kernels.
+//     characteristic projection reads (rho, u, v, w, p, T, H, sqrt rho, and in both precisions
+//     rho u_d and rho u_d^2 + p) in FP64 and FP32 copies of all fields for the FP32 kernels.
 //   interface fluxes (workspace): x faces [5][nz][ny][nx+1], y faces [5][nz][ny+1][nx],
 //     z faces [5][nz+1][ny][nx] (FP64, or FP32 in mixed precision); face s along a direction
 //     lies between nodes s-1 and s.
