@@ -71,13 +71,14 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
 }
 
 // Mixed precision: the fields the characteristic projection reads are formed in FP64 (rho, u,
-// v, w, p, T, H, sqrt rho); FP32 copies of all fields feed the FP32 kernels, with c and mu(T)
-// evaluated in FP32. The CFL partial is formed in FP64 from the FP64 velocities.
+// v, w, p, T, H, sqrt rho, rho u_d, rho u_d^2 + p); FP32 copies of all fields feed the FP32
+// kernels, with c and mu(T) evaluated in FP32. The CFL partial is formed in FP32 (the FP64 pipe
+// binds this kernel; the step needs no FP64 accuracy in this precision).
 __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C, const Bufs& B,
                                                  const double* __restrict__ w, int want_cfl, int blk,
                                                  double* sh) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
-  double spec = 0.0;
+  float spec = 0.f;
   if (q < d.N) {
     int i, j, k;
     node_ijk(d, q, i, j, k);
@@ -109,23 +110,22 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     }
     float rf = d2f(rho), pf = d2f(p), Tf = d2f(T);
     float cf = sqrtf(C.k32.gamma * pf / rf);
+    const float uf = d2f(u), vf = d2f(v), wf = d2f(ww);
     F.rho[n] = rf;
-    F.u[n] = d2f(u);
-    F.v[n] = d2f(v);
-    F.w[n] = d2f(ww);
+    F.u[n] = uf;
+    F.v[n] = vf;
+    F.w[n] = wf;
     F.p[n] = pf;
     F.T[n] = Tf;
     F.H[n] = d2f(H);
     F.c[n] = cf;
     F.mu[n] = viscosity(C.k32, C.visc_law, Tf);
-    if (want_cfl) {
-      double c = f2d(cf);
-      spec = (fabs(u) + c) * C.k64.inv_dx + (fabs(v) + c) * B.m64.inv_hy[j] + (fabs(ww) + c) * C.k64.inv_dz;
-    }
+    if (want_cfl)  // FP32 spectral radius: the step needs no more than FP32 accuracy here
+      spec = (fabsf(uf) + cf) * C.k32.inv_dx + (fabsf(vf) + cf) * B.m32.inv_hy[j] + (fabsf(wf) + cf) * C.k32.inv_dz;
   }
   if (want_cfl) {
-    double m = block_max(spec, sh);
-    if (threadIdx.x == 0) B.red[blk] = m;
+    float m = block_max_f(spec, reinterpret_cast<float*>(sh));
+    if (threadIdx.x == 0) B.red[blk] = f2d(m);
   }
 }
 

@@ -421,6 +421,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // max that propagates NaN (a NaN anywhere must reach the CFL step and the totals)
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
 
+__device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a != a) ? a : b; }
+
+// FP32 block maximum (NaN-propagating) through a shared array of at least 32 floats.
+__device__ __forceinline__ float block_max_f(float v, float* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = nanmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.f;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v = nanmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ double block_max(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
