@@ -273,15 +273,6 @@ __device__ __forceinline__ R viscosity(const Coefs<R>& K, int law, R T) {
   return K.mu_ref * rpow(tr, K.visc_exp);
 }
 
-// sum_l b_l (f_{+l} + f_{-l} - 2 f_0) along a line (second-derivative numerator of order 2L)
-template <int L, typename R>
-__device__ __forceinline__ R dsum2(const R* __restrict__ f, long long n, long long st, const R* b) {
-  R f0 = __ldg(f + n), s2 = R(0);
-#pragma unroll
-  for (int l = 1; l <= L; ++l) s2 += b[l] * ((__ldg(f + n + l * st) + __ldg(f + n - l * st)) - R(2) * f0);
-  return s2;
-}
-
 // FP64 Laplacian numerator at node n on the stretched grid, without the y first-derivative term:
 //   cc f_0 + sum_l [bx_l (f_{+l x} + f_{-l x}) + bz_l (f_{+l z} + f_{-l z})]
 //          + c2 sum_l b_l (f_{+l y} + f_{-l y}),
