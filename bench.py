@@ -38,7 +38,7 @@ CASE = inputs.C2
 FLOPS_PER_UNIT = {
     "weno_x": 900, "weno_y": 900, "weno_z": 900,
     "faces_x": 151, "faces_y": 151, "faces_z": 151,
-    "assemble": 430, "sensor": 105, "prims": 25,
+    "assemble": 430, "sensor": 105, "prims": 28,
 }
 # Mixed precision: FP64 flops of the projection into characteristic variables per WENO face
 # (Roe state and eigen-scalars 30, acoustic-row scalars 25 per stencil node); the FP32 flux
