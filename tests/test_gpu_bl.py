@@ -128,12 +128,26 @@ def test_c4_full_size_steps():
                        bc_xmin="periodic", bc_xmax="periodic", shock=False, shock_theta=0.0)
     cfg = O.make_cfg(sub)
     jmax = case.ny - 8
-    for i0, k0 in ((300, 40), (1229, 128), (1700, 200), (2000, 100)):
+    cols = ((300, 40), (1229, 128), (1700, 200), (2000, 100))
+    refs = {}
+    for i0, k0 in cols:
         blk = np.ascontiguousarray(w0[:, k0 - h:k0 + h, :, i0 - h:i0 + h])
-        ref = O.rhs(cfg, blk)[:, h, :jmax, h]
+        refs[i0, k0] = O.rhs(cfg, blk)[:, h, :jmax, h]
         got = r[:, k0, :jmax, i0].cpu().numpy()
-        err = rel_max(got, ref)
+        err = rel_max(got, refs[i0, k0])
         assert err.max() <= TOL, ((i0, k0), err)
+    # the mixed-precision path at full size on the same columns: FP32 flux arithmetic, whose
+    # rounding (~6e-8 of a flux) is amplified by the flux differences of the small wall-normal
+    # and spanwise residuals (measured up to 1.2e-4 of the column's largest |R_rho v|)
+    del r
+    sm = binding.Solver(case.replace(precision="mixed"))
+    rm = sm.compute_rhs(w)
+    for i0, k0 in cols:
+        err = rel_max(rm[:, k0, :jmax, i0].cpu().numpy(), refs[i0, k0])
+        print("C4 mixed-precision RHS error at column", (i0, k0), err)
+        assert err.max() <= 1e-3, ((i0, k0), err)
+    sm.close()
+    del rm
     r_old = torch.zeros_like(w)
     s.advance_n(w, r_old, 5, cfl=case.cfl)
     s.compute_rhs(w)

@@ -76,3 +76,17 @@ def test_overlap_toggle_rebuilds_graph():
     assert binding.lib().strm_set_overlap(s.ctx, 4) == -1
     ref.close()
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_overlap_full_size_rhs_bitwise(prec):
+    """The 256x192x128 benchmark channel: right-hand side with both overlap bits equals the
+    sequential one bit for bit."""
+    case = inputs.C2.replace(precision=prec)
+    w = state(case)
+    out = []
+    for ov in (0, 3):
+        s = solver(case, ov)
+        out.append(s.compute_rhs(w).cpu())
+        s.close()
+    assert torch.equal(out[0], out[1])
