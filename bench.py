@@ -50,7 +50,7 @@ FLOPS_PER_UNIT_MIXED = {"weno_x": 180, "weno_y": 180, "weno_z": 180}
 DRAM_BYTES_PER_UNIT = {"weno_x": 131.9, "weno_y": 190.8, "weno_z": 423.6}
 DRAM_BYTES_PER_UNIT_MIXED = {"weno_x": 120.5, "weno_y": 160.6, "weno_z": 242.9}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 (the profiling recipe's unit table); a probe of
-# dependent-chain-free DFMA on this pool measured 1.20 TFLOP/s at ~1.97 GHz.
+# dependent-chain-free DFMA on a GB300 measured 1.20 TFLOP/s at ~1.97 GHz.
 FP64_PEAK_TFLOPS = 1.25
 
 

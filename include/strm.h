@@ -343,7 +343,7 @@ int strm_debug_build(void);
 /* The context's error word (always 0 in the release build). Synchronises. */
 int strm_debug_flags(strm_ctx* ctx, unsigned* flags_host);
 
-/* ---- Precision conversions of the mixed-precision kernels. On this GPU the FP64 <-> FP32
+/* ---- Precision conversions of the mixed-precision kernels. On GB300 (sm_103) the FP64 <-> FP32
  * conversion instructions issue on the FP64 pipe; the mixed-precision kernels convert with
  * integer operations on the IEEE-754 bit patterns instead. These two calls apply the same
  * conversions elementwise to device arrays, so that they can be checked against IEEE-754

@@ -215,7 +215,7 @@ __device__ __forceinline__ double join64(unsigned lo, unsigned hi) {
 }
 
 // ---------------------------------------------------------------- FP64 <-> FP32 conversions
-// On this GPU the conversions between FP64 and FP32 issue on the FP64 pipe, which runs at 1/64
+// On GB300 (sm_103) the conversions between FP64 and FP32 issue on the FP64 pipe, which runs at 1/64
 // of the FP32 rate. The mixed-precision kernels convert several values per stencil node, so
 // they convert with 32-bit integer operations on the IEEE-754 bit patterns instead.
 //
