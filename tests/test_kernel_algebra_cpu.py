@@ -1,0 +1,82 @@
+"""Algebraic identities behind the rewritten formulas of the CUDA kernels, checked symbolically
+(no GPU): each rewrite must equal the textbook form it replaces, so that the kernels compute the
+oracle's quantities up to rounding.
+
+* WENO5 (Jiang-Shu, Section 2.1): the smoothness indicators as completed squares in the first
+  differences a..d of the stencil, and the candidate numerators carried by the kernel;
+* the acoustic difference rows of the characteristic projection written with the stored
+  momentum rho u_n and normal momentum flux rho u_n^2 + p;
+* the Laplacian with one shared centre term.
+"""
+import sympy as sp
+
+f0, f1, f2, f3, f4 = sp.symbols("f0:5", real=True)
+a, b, c, d = f1 - f0, f2 - f1, f3 - f2, f4 - f3
+R = sp.Rational
+
+
+def test_weno5_indicators_completed_squares():
+    beta0 = R(13, 12) * (f0 - 2 * f1 + f2) ** 2 + R(1, 4) * (f0 - 4 * f1 + 3 * f2) ** 2
+    beta1 = R(13, 12) * (f1 - 2 * f2 + f3) ** 2 + R(1, 4) * (f1 - f3) ** 2
+    beta2 = R(13, 12) * (f2 - 2 * f3 + f4) ** 2 + R(1, 4) * (3 * f2 - 4 * f3 + f4) ** 2
+    k = R(39, 64)
+    q0 = (a - R(11, 8) * b) ** 2 + k * b ** 2
+    q1 = (b - R(5, 8) * c) ** 2 + k * c ** 2
+    q2 = (d - R(11, 8) * c) ** 2 + k * c ** 2
+    for beta, q in ((beta0, q0), (beta1, q1), (beta2, q2)):
+        assert sp.expand(R(3, 4) * beta - q) == 0
+
+
+def test_weno5_candidate_numerators():
+    p0 = (2 * f0 - 7 * f1 + 11 * f2) / 6
+    p1 = (-f1 + 5 * f2 + 2 * f3) / 6
+    p2 = (2 * f2 + 5 * f3 - f4) / 6
+    e0 = a - R(5, 2) * b
+    e1 = -3 * b - 6 * c
+    e2 = R(3, 2) * d - 6 * c
+    assert sp.expand(e0 + 3 * (p0 - f2)) == 0
+    assert sp.expand(e1 + 18 * (p1 - f2)) == 0
+    assert sp.expand(e2 + 9 * (p2 - f2)) == 0
+    # with weights (w0, 6 v1, 3 v2) proportional to the normalised ones, the value is
+    # f2 - num / (3 den)
+    w0, v1, v2 = sp.symbols("w0 v1 v2", positive=True)
+    den = w0 + 6 * v1 + 3 * v2
+    num = w0 * e0 + v1 * e1 + v2 * e2
+    value = (w0 * p0 + 6 * v1 * p1 + 3 * v2 * p2) / den
+    assert sp.simplify(value - (f2 - num / (3 * den))) == 0
+
+
+def test_acoustic_rows_from_stored_momentum_flux():
+    rho, un, uan, p = sp.symbols("rho u_n ua_n p", real=True)
+    m = rho * un               # stored rho u_n
+    mflux = rho * un ** 2 + p  # stored rho u_n^2 + p
+    cBw = rho * (uan - un)
+    cBf = rho * un * (uan - un) - p
+    assert sp.expand(cBw - (rho * uan - m)) == 0
+    assert sp.expand(cBf - (m * uan - mflux)) == 0
+
+
+def test_laplacian_shared_centre_term():
+    L = 3
+    bl = [R(-49, 18), R(3, 2), R(-3, 20), R(1, 90)]
+    fx = sp.symbols("x_m3 x_m2 x_m1 c x_p1 x_p2 x_p3", real=True)
+    fy = sp.symbols("y_m3 y_m2 y_m1 y_p1 y_p2 y_p3", real=True)
+    fz = sp.symbols("z_m3 z_m2 z_m1 z_p1 z_p2 z_p3", real=True)
+    f0 = fx[3]
+    ix, iy, iz, c2 = sp.symbols("ix2 iy2 iz2 c2", positive=True)
+    xp = {l: fx[3 + l] for l in range(1, L + 1)}
+    xm = {l: fx[3 - l] for l in range(1, L + 1)}
+    yp = {l: fy[2 + l] for l in range(1, L + 1)}
+    ym = {l: fy[3 - l] for l in range(1, L + 1)}
+    zp = {l: fz[2 + l] for l in range(1, L + 1)}
+    zm = {l: fz[3 - l] for l in range(1, L + 1)}
+    # difference form per direction: sum_l b_l (f_+l + f_-l - 2 f0)
+    d2 = lambda P, M: sum(bl[l] * (P[l] + M[l] - 2 * f0) for l in range(1, L + 1))
+    lap_ref = d2(xp, xm) * ix + d2(yp, ym) * c2 + d2(zp, zm) * iz
+    # kernel form: cc f0 + sum bx (x pairs) + sum bz (z pairs) + c2 sum b (y pairs),
+    # cc = b0 (1/dx^2 + 1/dz^2 + c2), b0 = -2 sum_l b_l
+    assert bl[0] == -2 * sum(bl[1:])
+    cc = bl[0] * ix + bl[0] * iz + bl[0] * c2
+    lap = cc * f0 + sum(bl[l] * ix * (xp[l] + xm[l]) + bl[l] * iz * (zp[l] + zm[l])
+                        for l in range(1, L + 1)) + c2 * sum(bl[l] * (yp[l] + ym[l]) for l in range(1, L + 1))
+    assert sp.expand(lap - lap_ref) == 0
