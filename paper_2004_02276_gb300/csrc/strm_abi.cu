@@ -965,6 +965,7 @@ int strm_stats_read(strm_ctx* x, double* out_host, long long* nsamples_host) {
 
 int strm_convert_f64_f32(const double* x, float* y, long long n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return fail(STRM_EINVAL, "bad conversion arguments");
+  if (n == 0) return STRM_OK;
   launch_d2f(x, y, n, (cudaStream_t)stream);
   STRM_CK(cudaGetLastError());
   return STRM_OK;
@@ -972,6 +973,7 @@ int strm_convert_f64_f32(const double* x, float* y, long long n, void* stream) {
 
 int strm_convert_f32_f64(const float* x, double* y, long long n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return fail(STRM_EINVAL, "bad conversion arguments");
+  if (n == 0) return STRM_OK;
   launch_f2d(x, y, n, (cudaStream_t)stream);
   STRM_CK(cudaGetLastError());
   return STRM_OK;

@@ -86,3 +86,17 @@ def test_init_rejects_bad_arguments_before_any_cuda_call(lib):
     assert rc == -1
     assert lib.strm_set_bc(None, 0, 1, None, 0) == -1
     lib.strm_destroy(None)
+
+
+def test_host_side_argument_checks(lib):
+    """Calls that fail before touching a device: null pointers and bad sizes or bits return
+    STRM_EINVAL with a message, and the binding refuses host tensors for the conversions."""
+    import torch
+
+    assert lib.strm_convert_f64_f32(None, None, -1, None) == -1
+    assert lib.strm_convert_f32_f64(None, None, 5, None) == -1
+    assert lib.strm_convert_f64_f32(None, None, 0, None) == 0  # nothing to do
+    assert lib.strm_set_overlap(None, 1) == -1
+    assert b"conversion" in lib.strm_last_error() or b"context" in lib.strm_last_error()
+    with pytest.raises(ValueError):
+        binding.convert(torch.zeros(4, dtype=torch.float64))
