@@ -100,3 +100,25 @@ def test_host_side_argument_checks(lib):
     assert b"conversion" in lib.strm_last_error() or b"context" in lib.strm_last_error()
     with pytest.raises(ValueError):
         binding.convert(torch.zeros(4, dtype=torch.float64))
+
+
+def test_face_settings_of_the_workloads():
+    """The (face, kind, params) calls the binding makes for each boundary configuration."""
+    F, K = binding.FACES, binding.BC_KINDS
+    ch = binding.face_settings(inputs.C1)
+    assert ch == [(F["xmin"], K["periodic"], None), (F["xmax"], K["periodic"], None),
+                  (F["ymin"], K["wall"], None), (F["ymax"], K["wall"], None)]
+    c4 = inputs.C4
+    got = {face: (kind, params) for face, kind, params in binding.face_settings(c4)}
+    ref = [1.0, 1.0, 0.0, 0.0, c4.r_gas]
+    assert got[F["xmin"]] == (K["recycle"], ref + [float(c4.i_recycle), c4.delta_in])
+    assert got[F["xmax"]] == (K["char"], ref)
+    assert got[F["ymin"]] == (K["wall"], None)
+    assert got[F["ymax"]] == (K["shock"], ref + [c4.shock_theta, c4.shock_ximp])
+    # the digital-filter inflow face is set with its profiles, not by strm_set_bc
+    df = inputs.PAPER_BL
+    assert F["xmin"] not in [f for f, _, _ in binding.face_settings(df)]
+    g, p, s = binding.structs(df)
+    assert (g.y_map, s.L, p.visc_law) == (binding.Y_MAPS["sinh1"], 2, binding.VISC_LAWS["sutherland"])
+    with pytest.raises(ValueError):
+        binding.face_settings(inputs.C1.replace(bc_xmin="bogus"))
