@@ -43,10 +43,9 @@ const double kBeta[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Node fields held in FP64 (all of them in FP64 precision; those the FP64 characteristic
-// projection reads in mixed precision) and in FP32 (mixed precision only).
-// FP64 node arrays: FP64 precision 12 fields, the 6 wave speeds u_d -+ c, the 3 momentum
-// components and the 3 normal momentum fluxes; mixed precision 9 fields and the same 6
+// Node fields held in FP64 and in FP32 (mixed precision only). FP64 precision: 12 fields, the
+// 6 wave speeds u_d -+ c, the 3 momentum components and the 3 normal momentum fluxes; mixed
+// precision: the 9 fields the FP64 characteristic projection and switch read and the same 6.
 const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11;
 
 struct Layout {
