@@ -774,7 +774,7 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
 //   12 beta_2 = 16 [(d - 11c/8)^2 + (39/64) c^2],
 // so q_k = (3/4) beta_k + eps3 (eps3 = (3/4) eps keeps the weights) takes ten operations, the
 // (39/64) c^2 term being shared by q_1 and q_2. The weights d_k/(eps+beta_k)^2 are multiplied
-// through by 10 (3/4)^2 q_0^2 q_1^2 q_2^2: (w0, 6 v1, 3 v2). With the candidates
+// through by 10 (4/3)^2 q_0^2 q_1^2 q_2^2: (w0, 6 v1, 3 v2). With the candidates
 //   p_0 = f2 + (5b - 2a)/6,  p_1 = f2 + (b + 2c)/6,  p_2 = f2 + (4c - d)/6,
 // the result is f2 - num/(3 den), num = w0 e0 + v1 e1 + v2 e2 with e0 = a - 5b/2 = -3 (p_0 - f2),
 // e1 = -3b - 6c = -18 (p_1 - f2), e2 = 3d/2 - 6c = -9 (p_2 - f2), and den = w0 + 6 v1 + 3 v2.
