@@ -595,7 +595,7 @@ __device__ __forceinline__ bool sensor_node(const Dims& d, int region, int L, lo
 template <int L, typename R>
 __device__ __forceinline__ void body_sensor(const Dims& d, const Consts& C, const Bufs& B, int blk,
                                             int region = 0) {
-  long long q;
+  long long q = 0;  // set by sensor_node for the threads that own a node
   const bool mine = sensor_node(d, region, L, (long long)blk * blockDim.x + threadIdx.x, q);
   if constexpr (!std::is_same<R, double>::value) {
     // mixed precision: FP32 theta; the switch decides on an FP64 theta field, which holds the
