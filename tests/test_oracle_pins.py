@@ -152,6 +152,67 @@ def test_channel_mass_and_bulk_flow_constant(orc):
     assert orc.totals(cfg_nf, w2)[1] < t0[1] - 1e-6
 
 
+@pytest.mark.parametrize("mode", ["off", "sensor", "all"])
+def test_wall_faces_carry_no_mass_tangential_momentum_or_energy(orc, mode):
+    """Staggered isothermal walls (Section 3.1: the walls lie on interfaces, and no convective
+    mass, tangential momentum or energy crosses them). Inviscid, unforced, periodic in x and z,
+    random interior state: the x and z faces telescope, so sum_V R_m is the net flux through
+    the two wall faces. It vanishes to round-off for rho, rho u, rho w and rho E; the wall-normal
+    momentum keeps the pressure acting on the walls, so sum_V R_rhov does not."""
+    c = inputs.Case(nx=12, ny=14, nz=10, forcing=False, viscous=False, weno_mode=mode,
+                    theta_thr=0.6)
+    cfg = orc.make_cfg(c)
+    w = inputs.random_state(c, seed=5)
+    r = orc.rhs(cfg, w)
+    vol = volumes(orc, cfg, c)
+    if mode == "sensor":
+        _, _, _, fy, _ = orc.sensor(cfg, w)
+        frac = fy.mean()
+        assert 0.05 < frac < 0.95  # walls see both central and WENO faces
+    for m in (0, 1, 3, 4):
+        s = (r[m] * vol).sum()
+        scale = np.abs(r[m] * vol).sum()
+        assert abs(s) <= 1e-14 * scale, (m, s, scale)
+    # rho v: the wall pressure. With the mirrored ghost (p_g = p) the central pressure flux at
+    # a wall face is a positive combination of near-wall pressures, so the net force is O(p).
+    s_v = (r[2] * vol).sum()
+    assert abs(s_v) > 1e-3 * np.abs(r[2] * vol).sum()
+
+
+@pytest.mark.parametrize("mode", ["off", "sensor"])
+def test_forcing_adds_f_and_f_u(orc, mode):
+    """Constant-mass-flow forcing (Eqs. 1b, 1c): f is the uniform x-momentum source that makes
+    the volume integral of R_rhou vanish, and the energy equation gains the power f u.
+    Comparing the right-hand sides with forcing on and off on the same state: R_rhou changes by
+    f = -sum_V R_rhou(off) / V at every node, R_rhoE by f u (u = rho u / rho of that node), and
+    rho, rho v, rho w are unchanged. (Viscous: without wall shear nothing decelerates the flow
+    and f would vanish, as the wall-face pin shows.)"""
+    c = inputs.Case(nx=12, ny=14, nz=10, reynolds=500.0, weno_mode=mode)
+    # Poiseuille flow with density and temperature varying by +-20 % (so that u, rho u and
+    # rho differ node by node)
+    s = 2.0 * inputs.uniform(21, (2, c.nz, c.ny, c.nx)) - 1.0
+    ch = inputs.channel_state(c, seed=2)
+    u0, v0, w0 = ch[1], ch[2], ch[3]
+    w = inputs.primitive_state(c, 1.0 + 0.2 * s[0], u0, v0, w0, 1.0 + 0.2 * s[1])
+    on = orc.rhs(orc.make_cfg(c, forcing=True), w)
+    off = orc.rhs(orc.make_cfg(c, forcing=False), w)
+    cfg = orc.make_cfg(c)
+    vol = np.broadcast_to(volumes(orc, cfg, c), w[0].shape)
+    f = -(off[1] * vol).sum() / vol.sum()
+    assert abs(f) > 1e-4  # the walls decelerate the unforced flow
+    u = w[1] / w[0]
+    for m in (0, 2, 3):
+        assert np.array_equal(on[m], off[m])
+    np.testing.assert_allclose(on[1] - off[1], f, rtol=1e-11, atol=0)
+    ulp = 4 * np.finfo(float).eps * (np.abs(on[4]) + np.abs(off[4]))
+    assert np.all(np.abs((on[4] - off[4]) - f * u) <= ulp + 1e-13 * abs(f))
+    # the energy budget: the forcing's power integrates to f times the bulk velocity flux
+    power = ((on[4] - off[4]) * vol).sum()
+    assert abs(power - f * (u * vol).sum()) <= 1e-12 * abs(power)
+    # and the forced x-momentum residual integrates to zero
+    assert abs((on[1] * vol).sum()) <= 1e-13 * np.abs(on[1] * vol).sum()
+
+
 # ----------------------------------------------------------------------- textbook reduction
 
 @pytest.mark.parametrize("L", [2, 3])
