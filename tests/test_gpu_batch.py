@@ -4,11 +4,13 @@ same kernel bodies with the same per-instance reduction order. The only freedom 
 compiler's choice of where to contract a multiply and an add into an FMA, which may differ
 between the batched and the single-grid kernel that inline the same body; the comparison is
 therefore to a few ulp (FP64) or FP32 round-off (mixed), through the C ABI, before and after the
-autotuner picks launch shapes."""
+autotuner picks launch shapes. Every instance is also checked against the FP64 oracle, so that a
+defect shared by the batched and the single-grid kernels cannot pass unseen."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2004_02276_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
@@ -138,3 +140,45 @@ def test_ensemble_with_boundary_layer_instances(precision):
     assert max(errs) <= TOL[precision], errs
     np.testing.assert_allclose(E.times(), tref, rtol=1e-13)
     E.close()
+
+
+# the oracle comparison: relative L2 per conserved field after the steps
+ORACLE_TOL = {"fp64": 1e-12, "mixed": 1e-4}
+
+
+def oracle_run(c, w0, nsteps):
+    df = O.DFState(c, inputs.df_profiles(c)) if c.bc_xmin == "df" else None
+    wo, to, _ = O.advance(O.make_cfg(c, df=df), w0, nsteps, cfl=0.8)
+    return wo, to
+
+
+def rel_l2(a, b):
+    return np.array([np.linalg.norm(a[m] - b[m]) / max(np.linalg.norm(b[m]), 1e-300)
+                     for m in range(5)])
+
+
+@pytest.mark.parametrize("bag", ["channels", "boundary-layers"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_instances_match_oracle(bag, precision):
+    """Every instance of the ensemble after 4 CFL steps against 4 oracle steps of that instance
+    alone: relative L2 <= 1e-12 per field in FP64 (the FP64 target), <= 1e-4 in mixed precision
+    (FP32 flux arithmetic over 12 stages); the same simulated time."""
+    cases = mixed_bag(precision) if bag == "channels" else bl_bag(precision)
+    w0s = [inputs.channel_state(c, seed=c.nx) if c.kind == "channel" else inputs.bl_state(c, seed=c.nx)
+           for c in cases]
+    inflows = {e: inputs.df_profiles(c) for e, c in enumerate(cases) if c.bc_xmin == "df"}
+    E = binding.Ensemble(cases, inflows=inflows)
+    ws = [torch.from_numpy(w0).cuda() for w0 in w0s]
+    rs = [torch.zeros_like(w) for w in ws]
+    E.advance(ws, rs, 4, cfl=0.8)
+    times = E.times()
+    got = [w.cpu().numpy() for w in ws]
+    E.close()
+    worst = 0.0
+    for e, c in enumerate(cases):
+        wo, to = oracle_run(c, w0s[e], 4)
+        err = rel_l2(got[e], wo)
+        worst = max(worst, err.max())
+        assert err.max() <= ORACLE_TOL[precision], (c.name, err)
+        assert abs(times[e] - to) <= (1e-13 if precision == "fp64" else 1e-5) * to, (c.name, times[e], to)
+    print(bag, precision, "ensemble vs oracle, worst relative L2:", worst)

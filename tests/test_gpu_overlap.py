@@ -3,10 +3,13 @@ Ducros sensor (bit 1), and the x, y, z face stages as concurrent branches (bit 2
 independent kernels changes, so every result must equal the sequential order bit for bit:
 eager right-hand sides, eager RK steps and graph-replayed steps, in FP64 and mixed precision,
 for the channel, the recycling shock/boundary layer, the digital-filter inflow and a grid too
-thin for an interior region."""
+thin for an interior region. The overlapped modes are also checked against the FP64 oracle
+directly, so that parity does not rest on the sequential order alone."""
+import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2004_02276_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
@@ -90,3 +93,34 @@ def test_overlap_full_size_rhs_bitwise(prec):
         out.append(s.compute_rhs(w).cpu())
         s.close()
     assert torch.equal(out[0], out[1])
+
+
+def rel_max(a, b):
+    return np.array([np.abs(a[m] - b[m]).max() / max(np.abs(b[m]).max(), 1e-300) for m in range(5)])
+
+
+def rel_l2(a, b):
+    return np.array([np.linalg.norm(a[m] - b[m]) / max(np.linalg.norm(b[m]), 1e-300) for m in range(5)])
+
+
+@pytest.mark.parametrize("case", [CH, SBLI], ids=lambda c: c.name)
+def test_overlap_modes_match_oracle(case):
+    """Each overlap mode (ghost fill beside the inner sensor, concurrent face branches, both):
+    the right-hand side element-wise within 1e-12 of each field's largest value and 4
+    graph-replayed CFL steps within relative L2 1e-12 per field of the oracle, same time."""
+    w0 = inputs.channel_state(case, seed=0) if case.kind == "channel" else inputs.bl_state(case, seed=0)
+    cfg = O.make_cfg(case)
+    r_ref = O.rhs(cfg, w0)
+    w_ref, t_ref, _ = O.advance(cfg, w0, 4, cfl=case.cfl)
+    for ov in (1, 2, 3):
+        s = solver(case, ov)
+        r = s.compute_rhs(torch.from_numpy(w0).cuda()).cpu().numpy()
+        w = torch.from_numpy(w0).cuda()
+        s.advance_n(w, torch.zeros_like(w), 4, cfl=case.cfl)
+        t, _ = s.time()
+        wg = w.cpu().numpy()
+        s.close()
+        e_r, e_w = rel_max(r, r_ref), rel_l2(wg, w_ref)
+        assert e_r.max() <= 1e-12, (ov, e_r)
+        assert e_w.max() <= 1e-12, (ov, e_w)
+        assert abs(t - t_ref) <= 1e-13 * t_ref, (ov, t, t_ref)
