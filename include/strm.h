@@ -331,6 +331,18 @@ void strm_ensemble_destroy(strm_ensemble* ens);
 #define STRM_OVERLAP_FACES 2
 int strm_set_overlap(strm_ctx* ctx, int mode);
 
+/* ---- Prescribed switch input: a test device of the hybrid scheme. The paper's switch (Eq.
+ * sensor, Section 2.1) decides per face from the Ducros sensor of the current state; two runs
+ * that differ by round-off (FP64 and mixed precision) eventually take different decisions at
+ * faces whose sensor sits at the threshold, and each flip changes a flux by O(truncation). With
+ * theta set, every later right-hand side of this context (sensor mode only) decides from the
+ * caller's sensor values instead: theta is a device array of N doubles at the interior nodes
+ * (layout of strm_sensor's theta), read at every evaluation, kept alive and unchanged by the
+ * caller while set; the computed sensor still feeds the viscous terms (node divergence).
+ * theta = NULL returns to the computed sensor. The step graph of strm_advance_n is rebuilt on
+ * its next call. STRM_EINVAL: null context, or theta set outside STRM_WENO_SENSOR. */
+int strm_set_theta(strm_ctx* ctx, const double* theta);
+
 /* ---- Bounds checking. A library built with -DSTRM_DEBUG (paper_2004_02276_gb300/build.py,
  * debug=True: libstrm_debug.so) checks in every kernel the extreme nodes of each stencil, the
  * source node of each ghost and each face-list entry before using them; a violation ORs a code
@@ -360,25 +372,40 @@ int strm_debug_flags(strm_ctx* ctx, unsigned* flags_host);
 int strm_convert_f64_f32(const double* x, float* y, long long n, void* stream);
 int strm_convert_f32_f64(const float* x, double* y, long long n, void* stream);
 
+/* ---- FMA issue-rate probe: the denominator of the ALU roofline. The paper has no counterpart
+ * (its P100 ran FP64 at half the FP32 rate; on GB300 the FP64 pipe issues two DFMA per clock per
+ * SM against 128 FP32 FMA, so every FP64 kernel of this library is bound by it). Launches
+ * launches + 1 kernels (the first untimed) of independent FMA chains, kChains per thread, four
+ * 256-thread blocks per SM, about 40 ms each at the nominal rate, on `stream` (NULL: the legacy
+ * default stream), timed with CUDA events, and writes the best launch's rate in TFLOP/s
+ * (2 flops per FMA) and its milliseconds (nullable). precision: STRM_PREC_FP64 for FP64 FMA,
+ * STRM_PREC_MIXED for FP32 FMA. Synchronises. STRM_EINVAL for another precision, launches
+ * outside 1..1000 or a null rate pointer; STRM_ECUDA if a CUDA call fails. */
+int strm_peak_fma(int precision, int launches, void* stream, double* tflops_host, double* ms_host);
+
 /* Largest grid (nx*ny*nz) strm_conserved_totals_static accepts. */
 #define STRM_STATIC_MAX_NODES 67108864
 
 /* Conserved totals for callers that cannot allocate device memory. The paper has no
  * counterpart: this is a service of the library, not a step of the method.
  *
- * Same result as strm_conserved_totals (out_host[m] = sum w_m dx (y_eta deta) dz over the
- * interior), but it needs no context and no workspace and allocates nothing, so it can be
- * called by code that must not call cudaMalloc: an in-situ monitor attached to a solver whose
- * allocator already holds the device memory, or a tool running where allocation is not
- * allowed. The caller passes the grid, the device state w (layout as above) and a stream
- * (NULL: the legacy default stream); the call synchronises that stream.
+ * The totals of strm_conserved_totals (out_host[m] = sum w_m dx (y_eta deta) dz over the
+ * interior, for any of the STRM_MAP_* wall-normal maps), up to rounding: the node volumes are
+ * evaluated on the device here rather than uploaded from the host. It needs no context and no
+ * workspace and allocates nothing, so it can be called by code that must not call cudaMalloc:
+ * an in-situ monitor attached to a solver whose allocator already holds the device memory, or
+ * a tool running where allocation is not allowed. The caller passes the grid, the device state
+ * w (layout as above, on the current device) and a stream (NULL: the legacy default stream);
+ * the call synchronises that stream.
  *
  * Its scratch (partial sums and results, about 0.66 MB) is a file-scope __device__ array of
  * the library: every GPU that loads the library holds it until the process exits, and every
  * call on a device shares it. Calls that overlap on the GPU (for example on two streams) race
- * on that array; serialise them. The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture. Grids above STRM_STATIC_MAX_NODES nodes are rejected with STRM_EINVAL. */
+ * on that array; serialise them. Each call looks up the array's device address
+ * (cudaGetSymbolAddress, in the current device's context); make the first call on a device
+ * before any stream capture, since the lookup may load the module. Grids above
+ * STRM_STATIC_MAX_NODES nodes, unknown maps and non-positive sizes are rejected with
+ * STRM_EINVAL and a message naming the cause. */
 int strm_conserved_totals_static(const strm_grid* g, const double* w, double out_host[5],
                                  void* stream);
 

@@ -35,6 +35,7 @@ class OrcCfg(ctypes.Structure):
         ("L", ctypes.c_int), ("weno_mode", ctypes.c_int), ("theta_thr", ctypes.c_double),
         ("weno_eps", ctypes.c_double), ("u0", ctypes.c_double), ("l0", ctypes.c_double),
         ("convective", ctypes.c_int), ("viscous", ctypes.c_int),
+        ("theta_fixed", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -78,6 +79,8 @@ def lib():
         _lib.orc_splitmix64.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
         _lib.orc_splitmix64.restype = ctypes.c_ulonglong
         _lib.orc_df_plane.argtypes = [cp, ctypes.c_longlong, dp]
+        _lib.orc_set_threads.argtypes = [i]
+        _lib.orc_set_threads.restype = i
     return _lib
 
 
@@ -104,7 +107,8 @@ class DFState:
 def make_cfg(case, df=None, **over) -> OrcCfg:
     """Oracle configuration from a workload description; keyword overrides win. With a
     digital-filter inflow face, `df` is the DFState the configuration points to (and the first
-    plane is drawn if its counter is still 0)."""
+    plane is drawn if its counter is still 0). ``theta_fixed=`` ([nz, ny, nx] array) makes the
+    hybrid switch read that sensor field instead of the computed one."""
     get = lambda k, dflt=None: over.get(k, getattr(case, k, dflt))
     c = OrcCfg()
     c.nx, c.ny, c.nz = get("nx"), get("ny"), get("nz")
@@ -143,6 +147,12 @@ def make_cfg(case, df=None, **over) -> OrcCfg:
     c.u0, c.l0 = get("u0", 1.0), get("l0", 1.0)
     c.convective = int(bool(get("convective", True)))
     c.viscous = int(bool(get("viscous", True)))
+    th = over.get("theta_fixed")
+    if th is not None:
+        th = np.ascontiguousarray(th, dtype=np.float64)
+        assert th.shape == (c.nz, c.ny, c.nx), th.shape
+        c.theta_fixed = _dp(th)
+        c._theta = th  # keep the array alive with the configuration
     if df is not None:
         c.df_prof = _dp(df.prof)
         c.df_psi = _dp(df.psi)
@@ -292,6 +302,10 @@ def weno5(f, eps=1e-6):
 
 
 def threads():
-    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else all cores)."""
-    env = os.environ.get("OMP_NUM_THREADS")
-    return int(env) if env else os.cpu_count()
+    """Threads the oracle's OpenMP loops use."""
+    return lib().orc_set_threads(0)
+
+
+def set_threads(n):
+    """Use n threads in the oracle's OpenMP loops (timing only; results do not depend on it)."""
+    return lib().orc_set_threads(int(n))

@@ -64,6 +64,19 @@ typedef struct {
 
 int orc_ghosts(void) { return G; }
 
+#ifdef _OPENMP
+#include <omp.h>
+int orc_set_threads(int n) {
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+}
+#else
+int orc_set_threads(int n) {
+  (void)n;
+  return 1;
+}
+#endif
+
 static ptrdiff_t gidx(const grid_t* g, int i, int j, int k) {
   return ((ptrdiff_t)(k + G) * g->nyg + (ptrdiff_t)(j + G)) * g->nxg + (ptrdiff_t)(i + G);
 }
@@ -749,6 +762,10 @@ static void sensor(const grid_t* g, const prims_t* P, double* theta, double* div
         theta[n] = th > 0.0 ? th : 0.0;
         divg[n] = div;
       }
+  if (c->theta_fixed) /* prescribed switch input replaces the computed sensor */
+    for (int k = 0; k < g->nz; ++k)
+      for (int j = 0; j < g->ny; ++j)
+        for (int i = 0; i < g->nx; ++i) theta[gidx(g, i, j, k)] = c->theta_fixed[iidx(g, i, j, k)];
   fill_ghosts_scalar(g, theta);
   fill_ghosts_scalar(g, divg);
 }

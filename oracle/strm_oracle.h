@@ -70,6 +70,10 @@ typedef struct {
   double weno_eps;      /* WENO epsilon */
   double u0, l0;        /* sensor velocity and length scales */
   int convective, viscous; /* term switches (both 1 for the full method) */
+  /* nullable: a prescribed sensor value at the interior nodes ([nz][ny][nx]) that the hybrid
+   * switch reads instead of the computed Ducros sensor (a test device: it fixes the
+   * central/WENO decisions so that two runs can be compared without decision flips) */
+  const double* theta_fixed;
 } orc_cfg;
 
 /* Full right-hand side R(w) (convective + viscous + forcing), interior only. */
@@ -123,6 +127,10 @@ unsigned long long orc_splitmix64(unsigned long long seed, unsigned long long k)
 
 /* Filtered (not time-correlated) random plane of draw number `draw`, psi[3][nz][ny]. */
 int orc_df_plane(const orc_cfg* c, long long draw, double* psi);
+
+/* Threads of the OpenMP loops (n >= 1); returns the number in use afterwards. Timing only: the
+ * results do not depend on it (every loop writes disjoint nodes in a fixed order per node). */
+int orc_set_threads(int n);
 
 /* Recycling rescale factor s = delta_r / delta_in for the state w (1 if no recycling face). */
 double orc_recycle_scale(const orc_cfg* c, const double* w);

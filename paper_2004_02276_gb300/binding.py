@@ -82,6 +82,7 @@ SIGNATURES = {
     "strm_inflow_df_bytes": ([_vp, _P(DF)], _sz),
     "strm_set_inflow_df": ([_vp, _P(DF), _P(_d), _vp, _sz], _i),
     "strm_set_overlap": ([_vp, _i], _i),
+    "strm_set_theta": ([_vp, _vp], _i),
     "strm_debug_build": ([], _i),
     "strm_debug_flags": ([_vp, _P(ctypes.c_uint)], _i),
     "strm_stats_bytes": ([_vp, _i], _sz),
@@ -94,6 +95,7 @@ SIGNATURES = {
     "strm_timing_read": ([_vp, _P(_d), _P(ctypes.c_longlong), _P(ctypes.c_longlong)], _i),
     "strm_launch_count": ([_vp, _P(ctypes.c_longlong)], _i),
     "strm_conserved_totals_static": ([_P(Grid), _vp, _P(_d), _vp], _i),
+    "strm_peak_fma": ([_i, _i, _vp, _P(_d), _P(_d)], _i),
     "strm_convert_f64_f32": ([_vp, _vp, ctypes.c_longlong, _vp], _i),
     "strm_convert_f32_f64": ([_vp, _vp, ctypes.c_longlong, _vp], _i),
     "strm_ensemble_workspace_bytes": ([_i, _P(Grid), _P(Scheme)], _sz),
@@ -195,14 +197,32 @@ def apply_faces(lib_, ctx, case):
 
 def conserved_totals_static(case, w, stream=None):
     """Totals of a device state through the entry point that allocates nothing (no context,
-    no workspace); for callers that cannot allocate device memory."""
+    no workspace); for callers that cannot allocate device memory. ``w`` must be a contiguous
+    float64 CUDA tensor of shape [5, nz, ny, nx]; the call runs with w's device current."""
+    shape = (5, case.nz, case.ny, case.nx)
+    if not (isinstance(w, torch.Tensor) and w.is_cuda and w.dtype == torch.float64
+            and w.is_contiguous() and tuple(w.shape) == shape):
+        raise ValueError(f"state must be a contiguous float64 CUDA tensor of shape {shape}")
     g, _, _ = structs(case)
     out = (ctypes.c_double * 5)()
-    st = stream if stream is not None else torch.cuda.current_stream(w.device)
-    _check("strm_conserved_totals_static",
-           lib().strm_conserved_totals_static(ctypes.byref(g), _ptr(w), out,
-                                              ctypes.c_void_p(st.cuda_stream)))
+    with torch.cuda.device(w.device):
+        st = stream if stream is not None else torch.cuda.current_stream(w.device)
+        _check("strm_conserved_totals_static",
+               lib().strm_conserved_totals_static(ctypes.byref(g), _ptr(w), out,
+                                                  ctypes.c_void_p(st.cuda_stream)))
     return list(out)
+
+
+def peak_fma(precision="fp64", launches=10, device=None):
+    """Measured FMA rate of the current GPU in TFLOP/s (FP64 or, with "fp32", FP32) and the best
+    launch's milliseconds, on the current torch stream (strm_peak_fma)."""
+    dev = torch.device(device if device is not None else "cuda")
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        _check("strm_peak_fma", lib().strm_peak_fma(0 if precision == "fp64" else 1, int(launches), st,
+                                                    ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def convert(x):
@@ -313,6 +333,17 @@ class Solver:
         True means both, False or 0 the sequential order."""
         mode = 3 if mode is True else int(mode)
         _check("strm_set_overlap", lib().strm_set_overlap(self.ctx, mode))
+
+    def set_theta(self, theta=None):
+        """Prescribe the sensor field the hybrid switch reads ([nz, ny, nx] float64 CUDA tensor,
+        kept alive here while set), or None to return to the computed sensor."""
+        if theta is not None:
+            c = self.case
+            if not (theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+                    and tuple(theta.shape) == (c.nz, c.ny, c.nx)):
+                raise ValueError("theta must be a contiguous float64 CUDA tensor of shape [nz, ny, nx]")
+        self._theta = theta
+        _check("strm_set_theta", lib().strm_set_theta(self.ctx, None if theta is None else _ptr(theta)))
 
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()

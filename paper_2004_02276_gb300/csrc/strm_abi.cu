@@ -178,6 +178,8 @@ struct strm_ctx {
   DFParams df = {};
   std::vector<double> df_host;  // profiles and filter coefficients, kept for the async upload
   // overlap (strm_set_overlap): two side streams and the fork/join events of one right-hand side
+  // prescribed switch input (strm_set_theta): caller-owned device array of N doubles, or null
+  const double* theta_fixed = nullptr;
   int overlap = 0;  // STRM_OVERLAP_* bits
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -451,7 +453,8 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
     STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_ghost_prims(d, C, B, st));
     STRM_LAUNCH(STRM_K_SENSOR, launch_sensor(d, C, B, 0, st));
   }
-  if (C.mixed && C.weno_mode == 1) STRM_LAUNCH(STRM_K_SENSOR, launch_band_theta(d, C, B, st));
+  if (C.mixed && C.weno_mode == 1 && !x->theta_fixed) STRM_LAUNCH(STRM_K_SENSOR, launch_band_theta(d, C, B, st));
+  if (x->theta_fixed) STRM_LAUNCH(STRM_K_SENSOR, launch_theta_set(d, B, x->theta_fixed, st));
   STRM_LAUNCH(STRM_K_GHOST_SENSOR, launch_ghost_scalars(d, C, B, st));
   if (C.convective && (ovl & STRM_OVERLAP_FACES)) {
     STRM_CK(cudaEventRecord(x->ev[2], st));
@@ -993,6 +996,18 @@ int strm_set_overlap(strm_ctx* x, int mode) {
   return STRM_OK;
 }
 
+int strm_set_theta(strm_ctx* x, const double* theta) {
+  if (!x) return fail(STRM_EINVAL, "null context");
+  if (theta && x->C.weno_mode != STRM_WENO_SENSOR)
+    return fail(STRM_EINVAL, "a prescribed switch input needs the sensor mode (STRM_WENO_SENSOR)");
+  x->theta_fixed = theta;
+  if (x->gexec) {  // the captured graph has the other launch structure
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
+  return STRM_OK;
+}
+
 int strm_debug_build(void) { return kDebug ? 1 : 0; }
 
 int strm_debug_flags(strm_ctx* x, unsigned* flags_host) {
@@ -1044,7 +1059,8 @@ int strm_sensor(strm_ctx* x, const double* w, double* theta, double* div, unsign
   if (x->C.bc[0] == kBcRecycle) launch_recycle(x->d, x->C, x->B, x->stream);
   launch_ghost_prims(x->d, x->C, x->B, x->stream);
   launch_sensor(x->d, x->C, x->B, 0, x->stream);
-  if (x->C.mixed && x->C.weno_mode == 1) launch_band_theta(x->d, x->C, x->B, x->stream);
+  if (x->C.mixed && x->C.weno_mode == 1 && !x->theta_fixed) launch_band_theta(x->d, x->C, x->B, x->stream);
+  if (x->theta_fixed) launch_theta_set(x->d, x->B, x->theta_fixed, x->stream);
   launch_ghost_scalars(x->d, x->C, x->B, x->stream);
   launch_export_sensor(x->d, x->C, x->B, theta, div, x->stream);
   unsigned char* fl[3] = {fx, fy, fz};

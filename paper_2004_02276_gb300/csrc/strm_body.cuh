@@ -828,18 +828,28 @@ struct AbsMax {
 // Reciprocals of five positive doubles with one division (prefix-product method): each value
 // is first brought to [1, 2) by replacing its exponent field (integer operations on the high
 // word), the five mantissas are inverted together, and each reciprocal gets its exponent back
-// by an integer subtraction on its exponent field. Valid for positive normal inputs below
-// 2^1022 (the reciprocals stay normal); a NaN input yields a finite value here, so callers
-// multiply by a numerator that carries the NaN.
+// by an integer subtraction on its exponent field. That is valid for positive normal inputs
+// below 2^1022 (biased exponent field 1 .. 2044: the reciprocals stay normal). Any other input
+// (zero, subnormal, 2^1022 or more, infinity, NaN, negative) sends the five through plain
+// correctly rounded divisions instead, so the result is 1/y in every case; the range test is
+// integer work and the fallback is not taken for the states of the method.
 __device__ __forceinline__ void recip5(const double* y, double* r) {
   double m[5];
   int e[5];
+  bool in_range = true;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     unsigned lo, hi;
     split64(y[k], lo, hi);
-    e[k] = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const unsigned field = hi >> 20;  // sign and biased exponent
+    in_range = in_range && field >= 1u && field <= 2044u;
+    e[k] = (int)(field & 0x7ffu) - 1023;
     m[k] = join64(lo, (hi & 0x000fffffu) | 0x3ff00000u);
+  }
+  if (!in_range) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r[k] = 1.0 / y[k];
+    return;
   }
   double p1 = m[0] * m[1], p2 = p1 * m[2], p3 = p2 * m[3], p4 = p3 * m[4];
   double inv = 1.0 / p4;

@@ -54,6 +54,8 @@ void launch_sensor(const Dims& d, const Consts& C, const Bufs& B, int region, cu
 // mixed precision: FP64 theta at the nodes the sensor listed as near the switch threshold
 void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// prescribed switch input: the FP64 sensor field at the interior nodes from theta[N]
+void launch_theta_set(const Dims& d, const Bufs& B, const double* theta, cudaStream_t s);
 void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 // residual into R, or (rk.w set) the RK stage update of w and r_old without writing R

@@ -133,6 +133,16 @@ __global__ void __launch_bounds__(256) k_export_interior(Dims d, const R* __rest
   dst[q] = (double)src[gidx(d, i, j, k)];
 }
 
+// Prescribed switch input (strm_set_theta): the FP64 sensor field the hybrid switch reads takes
+// the caller's values at the interior nodes (after the sensor, before its ghost fill).
+__global__ void __launch_bounds__(256) k_theta_set(Dims d, Bufs B, const double* __restrict__ theta) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= d.N) return;
+  int i, j, k;
+  node_ijk(d, q, i, j, k);
+  B.n64.theta[gidx(d, i, j, k)] = theta[q];
+}
+
 // elementwise FP64 <-> FP32 with the integer-pipe conversions of the mixed-precision kernels
 __global__ void __launch_bounds__(256) k_convert_d2f(const double* __restrict__ x, float* __restrict__ y,
                                                      long long n) {
@@ -252,6 +262,10 @@ void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double*
     if (theta) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.theta, theta);
     if (div) k_export_interior<double><<<nb, 256, 0, s>>>(d, B.n64.div, div);
   }
+}
+
+void launch_theta_set(const Dims& d, const Bufs& B, const double* theta, cudaStream_t s) {
+  k_theta_set<<<blocks_for(d.N, 256), 256, 0, s>>>(d, B, theta);
 }
 
 void launch_d2f(const double* x, float* y, long long n, cudaStream_t s) {

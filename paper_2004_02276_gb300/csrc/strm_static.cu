@@ -6,7 +6,6 @@
 // context nor a workspace: its scratch (per-block partial sums and the five results) is the
 // file-scope array below, which every GPU that loads this library keeps until the process exits.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/strm.h"
@@ -26,41 +25,45 @@ static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
 int static_fail(int code, const std::string& msg) { return strm::record_error(code, msg); }
 
-// Device address of g_static_scratch on the current device, looked up once per device. In host
-// code the array's name is only a host-side stand-in, so kernels get this address instead.
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-double* g_static_ptr[kMaxDevices] = {};
-
+// Device address of g_static_scratch in the current context. In host code the array's name is
+// only a host-side stand-in, so kernels get this address instead. It is looked up on every call
+// (cheap next to the call's synchronisation): an address cached per device could outlive the
+// module after a device reset or a released primary context.
 cudaError_t static_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = (double*)p;
-  }
-  *out = g_static_ptr[dev];
+  *out = (double*)p;
   return cudaSuccess;
 }
 
 struct StaticGrid {
-  int nx, ny, nz, tanh_map;
+  int nx, ny, nz, y_map;
   double beta, ly, deta, dxdz;
 };
 
-// Node volume dx (y_eta deta) dz of row j (tanh or uniform wall-normal map).
+// Node volume dx (y_eta deta) dz of row j, with y_eta of the wall-normal map (the maps of
+// include/strm.h, as the context's metrics take them).
 __device__ __forceinline__ double static_volume(const StaticGrid& g, int j) {
+  const double eta = (j + 0.5) * g.deta, b = g.beta;
   double ye;
-  if (g.tanh_map) {
-    double eta = (j + 0.5) * g.deta;
-    double A = 0.5 * g.ly / tanh(g.beta);
-    double th = tanh(g.beta * (2.0 * eta - 1.0));
-    ye = 2.0 * g.beta * A * (1.0 - th * th);
+  if (g.y_map == STRM_MAP_TANH) {
+    // y = (ly/2) tanh(b (2 eta - 1)) / tanh(b)
+    double A = 0.5 * g.ly / tanh(b);
+    double th = tanh(b * (2.0 * eta - 1.0));
+    ye = 2.0 * b * A * (1.0 - th * th);
+  } else if (g.y_map == STRM_MAP_TANH_ONESIDED) {
+    // y = ly (1 - tanh(b (1 - eta)) / tanh(b))
+    double A = g.ly / tanh(b);
+    double th = tanh(b * (1.0 - eta));
+    ye = A * b * (1.0 - th * th);
+  } else if (g.y_map == STRM_MAP_ERF) {
+    // y = (ly/2) erf(b (2 eta - 1)) / erf(b)
+    double sv = 2.0 * eta - 1.0;
+    ye = 2.0 * g.ly * b / (sqrt(acos(-1.0)) * erf(b)) * exp(-b * b * sv * sv);
+  } else if (g.y_map == STRM_MAP_SINH_ONESIDED) {
+    // y = ly sinh(b eta) / sinh(b)
+    ye = g.ly * b * cosh(b * eta) / sinh(b);
   } else {
     ye = g.ly;
   }
@@ -105,10 +108,12 @@ __global__ void __launch_bounds__(1024) k_static_finalize(double* scratch, int n
 extern "C" int strm_conserved_totals_static(const strm_grid* g, const double* w, double out_host[5],
                                             void* stream) {
   if (!g || !w || !out_host) return static_fail(STRM_EINVAL, "null argument");
-  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0) ||
-      (g->y_map == STRM_MAP_TANH && !(g->beta > 0)) ||
-      (g->y_map != STRM_MAP_TANH && g->y_map != STRM_MAP_UNIFORM))
-    return static_fail(STRM_EINVAL, "invalid grid");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0))
+    return static_fail(STRM_EINVAL, "invalid grid: sizes and lengths must be positive");
+  if (g->y_map < STRM_MAP_UNIFORM || g->y_map > STRM_MAP_SINH_ONESIDED)
+    return static_fail(STRM_EINVAL, "invalid grid: unknown wall-normal map " + std::to_string(g->y_map));
+  if (g->y_map != STRM_MAP_UNIFORM && !(g->beta > 0))
+    return static_fail(STRM_EINVAL, "invalid grid: the wall-normal map needs beta > 0");
   long long N = (long long)g->nx * g->ny * g->nz;
   if (N > STRM_STATIC_MAX_NODES)
     return static_fail(STRM_EINVAL, "grid has " + std::to_string(N) + " nodes; the static scratch of "
@@ -123,7 +128,7 @@ extern "C" int strm_conserved_totals_static(const strm_grid* g, const double* w,
   sg.nx = g->nx;
   sg.ny = g->ny;
   sg.nz = g->nz;
-  sg.tanh_map = g->y_map == STRM_MAP_TANH ? 1 : 0;
+  sg.y_map = g->y_map;
   sg.beta = g->beta;
   sg.ly = g->ly;
   sg.deta = 1.0 / g->ny;

@@ -122,3 +122,17 @@ def test_face_settings_of_the_workloads():
     assert (g.y_map, s.L, p.visc_law) == (binding.Y_MAPS["sinh1"], 2, binding.VISC_LAWS["sutherland"])
     with pytest.raises(ValueError):
         binding.face_settings(inputs.C1.replace(bc_xmin="bogus"))
+
+
+def test_static_totals_binding_rejects_bad_state_before_the_library():
+    """The binding of the allocation-free totals checks the state (contiguous float64 CUDA
+    tensor of shape [5, nz, ny, nx]) before any call into the library, so that a mis-sized,
+    FP32 or host tensor never reaches a kernel."""
+    import torch
+
+    case = inputs.Case(nx=8, ny=6, nz=4)
+    for bad in (torch.zeros(8, dtype=torch.float64),
+                torch.zeros((5, 4, 6, 8), dtype=torch.float64),       # host memory
+                torch.zeros((5, 4, 6, 8), dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            binding.conserved_totals_static(case, bad)

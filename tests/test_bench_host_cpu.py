@@ -43,11 +43,36 @@ def test_case_override_only_changes_the_grid():
         grid = ""
 
     assert bench.bench_case(A()) is bench.CASE
-    A.grid = "192x144x96"
+    assert bench.CASE.name == "sbli-2048x384x256" and bench.CASE.shock
+    A.grid = "512x192x64"
     c = bench.bench_case(A())
-    assert (c.nx, c.ny, c.nz) == (192, 144, 96) and c.name == "channel-192x144x96"
-    assert (c.mach, c.reynolds, c.lx, c.ly, c.lz) == (bench.CASE.mach, bench.CASE.reynolds,
-                                                      bench.CASE.lx, bench.CASE.ly, bench.CASE.lz)
+    assert (c.nx, c.ny, c.nz) == (512, 192, 64) and c.name == "sbli-512x192x64"
+    # same spacing, gas, scheme and boundary kinds as the workload
+    for a, b in ((c.lx / c.nx, bench.CASE.lx / bench.CASE.nx), (c.ly / c.ny, bench.CASE.ly / bench.CASE.ny),
+                 (c.lz / c.nz, bench.CASE.lz / bench.CASE.nz)):
+        assert abs(a - b) <= 1e-12 * b
+    for k in ("mach", "reynolds", "t_wall", "shock", "shock_theta", "bc_xmin", "bc_xmax", "bc_ymin",
+              "bc_ymax", "noise", "L", "weno_mode", "y_map", "beta"):
+        assert getattr(c, k) == getattr(bench.CASE, k), k
+
+
+def test_kernel_units_and_step_flops():
+    """Units per kernel class from the timing record: WENO faces as counted, central faces as the
+    direction's faces minus its WENO faces, nodes per launch otherwise; the step's flops are the
+    sum over classes of flops per unit x units."""
+    c = bench.inputs.Case(nx=4, ny=3, nz=2)
+    kt = {"prims": (1.0, 3), "sensor": (1.0, 3), "faces_x": (1.0, 3), "faces_y": (1.0, 3),
+          "faces_z": (1.0, 3), "weno_x": (1.0, 3), "weno_y": (1.0, 3), "weno_z": (2.0, 3),
+          "assemble": (1.0, 3), "dt_finalize": (0.1, 1), "force_finalize": (0.0, 0)}
+    wf = [10, 11, 12]
+    u = bench.kernel_units(c, kt, wf)
+    assert u["weno_z"] == 12 and u["faces_x"] == 5 * 3 * 2 * 3 - 10 and u["faces_z"] == 4 * 3 * 3 * 3 - 12
+    assert u["assemble"] == 24 * 3 and u["rk_update"] == 24 * 3 and "force_finalize" not in u
+    r = bench.roofline(c, kt, wf, 1.0, 1, 1.0, bench.FLOPS_PER_UNIT, {}, "fp64")
+    assert r["kernel"] == "weno_z" and r["flops_per_unit"] == 900
+    want = sum(bench.FLOPS_PER_UNIT.get(k, 0) * v for k, v in u.items())
+    assert abs(r["step_flops"] - want) <= 1e-9 * want
+    assert abs(r["weno_face_fraction"] - 33 / (3 * 3 * 24)) < 1e-4
 
 
 def test_job_rate_counts_all_ranks():

@@ -25,7 +25,7 @@ def test_reference_arm_json_line():
     assert out["impl"] == "reference" and out["higher_is_better"] is True
     assert out["metric"].startswith("grid-pt RK-stage updates/s")
     assert out["unit"] == "grid-pt RK-stage updates/s" and out["value"] > 0
-    assert out["config"]["workload"] == "channel-256x192x128"
+    assert out["config"]["workload"] == "sbli-2048x384x256"
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}

@@ -80,3 +80,63 @@ def test_laplacian_shared_centre_term():
     lap = cc * f0 + sum(bl[l] * ix * (xp[l] + xm[l]) + bl[l] * iz * (zp[l] + zm[l])
                         for l in range(1, L + 1)) + c2 * sum(bl[l] * (yp[l] + ym[l]) for l in range(1, L + 1))
     assert sp.expand(lap - lap_ref) == 0
+
+
+def _recip5_emulated(y, guard=True):
+    """The WENO kernel's shared reciprocal of five positive doubles, emulated bit for bit in
+    numpy: mantissas brought to [1, 2) by rewriting the exponent field, inverted together by
+    prefix products and one division, exponents restored by an integer subtraction; with the
+    guard, inputs outside the valid exponent range go through plain division."""
+    import numpy as np
+
+    y = np.asarray(y, dtype=np.float64)
+    bits = y.view(np.uint64)
+    hi = (bits >> np.uint64(32)).astype(np.uint64)
+    field = hi >> np.uint64(20)
+    if guard and not np.all((field >= 1) & (field <= 2044)):
+        return 1.0 / y
+    e = (field & np.uint64(0x7FF)).astype(np.int64) - 1023
+    mbits = (bits & np.uint64(0x000FFFFFFFFFFFFF)) | np.uint64(0x3FF0000000000000)
+    m = mbits.view(np.float64)
+    p1 = m[0] * m[1]
+    p2 = p1 * m[2]
+    p3 = p2 * m[3]
+    p4 = p3 * m[4]
+    inv = 1.0 / p4
+    i4 = inv * p3
+    inv *= m[4]
+    i3 = inv * p2
+    inv *= m[3]
+    i2 = inv * p1
+    inv *= m[2]
+    i1, i0 = inv * m[0], inv * m[1]
+    im = np.array([i0, i1, i2, i3, i4]).view(np.uint64)
+    out = (im - (e.astype(np.uint64) << np.uint64(52))) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    return out.view(np.float64)
+
+
+def test_recip5_extreme_magnitudes():
+    """Inside [2^-1022, 2^1022) the exponent-field reciprocal agrees with 1/y to a few ulp
+    (three roundings of the prefix products); at 2^1022 and above, and for zeros and
+    subnormals, the exponent subtraction wraps and gives a wrong value, which is why the kernel
+    checks the range and divides plainly there. The guarded form is 1/y to a few ulp everywhere."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    ok = np.exp2(rng.uniform(-1021.9, 1021.9, size=(200, 5)))
+    for y in ok:
+        np.testing.assert_allclose(_recip5_emulated(y, guard=False), 1.0 / y, rtol=8e-16, atol=0.0)
+    extremes = [
+        [1.5 * 2.0 ** 1022, 1.0, 3.0, 5.0, 7.0],    # reciprocal below 2^-1022
+        [1.5 * 2.0 ** 1023, 1.0, 2.0, 3.0, 4.0],    # reciprocal subnormal
+        [5e-324, 1.0, 2.0, 3.0, 4.0],               # subnormal input
+        [0.0, 1.0, 2.0, 3.0, 4.0],
+        [np.inf, 1.0, 2.0, 3.0, 4.0],
+    ]
+    with np.errstate(all="ignore"):
+        wrong = [not np.allclose(_recip5_emulated(np.array(y), guard=False), 1.0 / np.array(y),
+                                 rtol=1e-15, atol=0.0, equal_nan=True) for y in extremes]
+        assert all(wrong)
+        for y in extremes:
+            y = np.array(y)
+            np.testing.assert_allclose(_recip5_emulated(y), 1.0 / y, rtol=8e-16, atol=0.0)

@@ -571,3 +571,23 @@ def test_totals_uniform(orc):
     st = inputs.primitive_state(c, 1.1, 0.4, -0.3, 0.2, 1.2)
     np.testing.assert_allclose(orc.totals(cfg, st), st[:, 0, 0, 0] * c.lx * c.ly * c.lz,
                                rtol=1e-14)
+
+
+def test_prescribed_switch_input(orc):
+    """The prescribed sensor field (a test device that fixes the central/WENO decisions): given
+    the sensor's own values it changes nothing; zero everywhere gives the central flux at every
+    face (WENO off), one everywhere gives WENO at every face (the switch's two limits)."""
+    c = inputs.Case(nx=16, ny=12, nz=10, reynolds=3000.0)
+    w = inputs.channel_state(c, seed=7)
+    cfg = orc.make_cfg(c)
+    th, _, fx, fy, fz = orc.sensor(cfg, w)
+    assert 0.05 < np.mean(np.concatenate([fx.ravel(), fy.ravel(), fz.ravel()])) < 0.95
+    base = orc.rhs(cfg, w)
+    assert np.array_equal(orc.rhs(orc.make_cfg(c, theta_fixed=th), w), base)
+    zero, one = np.zeros_like(th), np.ones_like(th)
+    assert np.array_equal(orc.rhs(orc.make_cfg(c, theta_fixed=zero), w),
+                          orc.rhs(orc.make_cfg(c, weno_mode="off"), w))
+    assert np.array_equal(orc.rhs(orc.make_cfg(c, theta_fixed=one), w),
+                          orc.rhs(orc.make_cfg(c, weno_mode="all"), w))
+    _, _, gx, gy, gz = orc.sensor(orc.make_cfg(c, theta_fixed=one), w)
+    assert gx.all() and gy.all() and gz.all()
