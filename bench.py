@@ -659,12 +659,20 @@ def main():
     ap.add_argument("--grid", default="", help="NXxNYxNZ of the same workload, for profiling captures only")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     ap.add_argument("--no-variants", action="store_true", help="skip the channel and batched variants")
+    ap.add_argument("--peaks-only", action="store_true",
+                    help="only measure and print the FP64/FP32 FMA rates (strm_peak_fma) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.steps < 1 or args.timing_steps < 1:
         ap.error("--steps and --timing-steps must be >= 1")
     world, rank, local = dist_setup()
+    if args.peaks_only:
+        import torch
+
+        torch.cuda.set_device(local)
+        print(json.dumps(measure_peaks(local)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -301,6 +301,7 @@ void set_consts(strm_ctx* x) {
   C.convective = s.convective ? 1 : 0;
   C.viscous = s.viscous ? 1 : 0;
   C.mixed = s.precision == STRM_PREC_MIXED ? 1 : 0;
+  C.p_shift = (double)(float)(p.r_gas * p.t_ref);
   fill_coefs(C.k64, p, s, x->g);
   fill_coefs(C.k32, p, s, x->g);
 }

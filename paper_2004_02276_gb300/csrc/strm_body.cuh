@@ -115,7 +115,7 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     F.u[n] = uf;
     F.v[n] = vf;
     F.w[n] = wf;
-    F.p[n] = pf;
+    F.p[n] = d2f(p - C.p_shift);  // shifted copy (see Consts::p_shift); c uses the full pf
     F.T[n] = Tf;
     F.H[n] = d2f(H);
     F.c[n] = cf;
@@ -243,7 +243,7 @@ __device__ __forceinline__ void store_pstate(const Consts& C, const Bufs& B, lon
     F.u[dst] = d2f(g.u);
     F.v[dst] = d2f(g.v);
     F.w[dst] = d2f(g.w);
-    F.p[dst] = pf;
+    F.p[dst] = d2f(__dadd_rn(g.p, -C.p_shift));  // shifted copy (see Consts::p_shift)
     F.T[dst] = Tf;
     F.H[dst] = d2f(H);
     F.c[dst] = sqrtf(C.k32.gamma * pf / rf);
@@ -733,7 +733,9 @@ __device__ __forceinline__ void face_node(const Dims& d, long long q, int& i, in
 // q = a_l (rho_a + rho_b)(u_a + u_b)/4 this is sum_{l,m} q (phi_a + phi_b) (the 1/4 is carried in
 // the coefficients a_l/4, and f_rho = 2 sum q); the pressure enters the normal momentum as
 // sum_l a_l sum_m (p_a + p_b) = sum_r ap_r (p_{n-r} + p_{n+1+r}), ap_r = a_{r+1} + .. + a_L,
-// r = 0..L-1, since the pressure sum is linear. R is the arithmetic precision.
+// r = 0..L-1, since the pressure sum is linear. R is the arithmetic precision; in mixed
+// precision the FP32 pressure copy is p - p_shift, so the face flux is short of the constant
+// p_shift, as every mixed face flux is (the constant cancels in the flux differences).
 template <int L, int DIR, typename R>
 __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, long long n, long long st,
                                              R* f) {
@@ -1078,6 +1080,10 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
   f[1 + T2] += g[3];
   f[4] = Haf * (g[0] + g[4]) + unaf * caf * (g[4] - g[0]) + 0.5f * q2f * g[1] + uaf[T1] * g[2] +
          uaf[T2] * g[3];
+  // the central faces carry the pressure less p_shift (their FP32 pressure copy is shifted);
+  // the same constant comes off here, so that every face flux has the same offset, which
+  // cancels in the flux differences
+  f[1 + DIR] -= (float)C.p_shift;
 }
 
 // ------------------------------------------------------------------------------ face kernels
@@ -1122,6 +1128,7 @@ template <int L, int DIR, typename R>
 __device__ __forceinline__ void body_classify(const Dims& d, const Consts& C, const Bufs& B, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   bool valid = q < d.nf[DIR], fl = false;
+  if (DIR == 2 && valid) q = zface_order(d, q);
   if (valid) {
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
@@ -1139,7 +1146,7 @@ __device__ __forceinline__ void body_central(const Dims& d, const Consts& C, con
   long long st = dir_stride(d, DIR);
   R* out = face_flux<R>(B, DIR);
   for (long long t = t0; t < cnt; t += tstride) {
-    long long q = use_list ? (long long)B.cl[DIR][t] : t;
+    long long q = use_list ? (long long)B.cl[DIR][t] : (DIR == 2 ? zface_order(d, t) : t);
     if (!index_ok(d, q, nf, kDbgList)) continue;
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
@@ -1161,7 +1168,7 @@ __device__ __forceinline__ void body_weno(const Dims& d, const Consts& C, const 
   long long cnt = all ? nf : (long long)B.wcount[DIR];
   long long st = dir_stride(d, DIR);
   for (long long t = t0; t < cnt; t += tstride) {
-    long long q = all ? t : (long long)B.wl[DIR][t];
+    long long q = all ? (DIR == 2 ? zface_order(d, t) : t) : (long long)B.wl[DIR][t];
     if (!index_ok(d, q, nf, kDbgList)) continue;
     int i, j, k;
     face_node<DIR>(d, q, i, j, k);
@@ -1281,9 +1288,10 @@ template <int L, typename R>
 __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, const Bufs& B,
                                               double* __restrict__ Rout, int blk, double* sh,
                                               const RkFuse& rk = RkFuse{nullptr, nullptr, 0.0, 0.0}) {
-  long long q = (long long)blk * blockDim.x + threadIdx.x;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   double fpart = 0.0;
-  bool live = q < d.N;
+  bool live = t < d.N;
+  const long long q = live ? node_order(d, t) : t;
   if constexpr (kDebug) {  // stencils of the viscous terms and the faces read (debug builds)
     if (live) {
       int i = (int)(q % d.nx), j = (int)((q / d.nx) % d.ny), k = (int)(q / ((long long)d.nx * d.ny));

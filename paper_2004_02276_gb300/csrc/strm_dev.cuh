@@ -77,6 +77,12 @@ struct Consts {
   int i_recycle;
   double delta_in, dx;
   double df_p;  // pressure of the digital-filter inflow ghosts
+  // mixed precision: the FP32 pressure copy holds p - p_shift (p_shift = R t_ref rounded to
+  // FP32, the reference pressure of the channel and boundary-layer units). A constant added to
+  // the pressure of every face flux cancels exactly in the flux differences, so the FP32 copy
+  // keeps the precision of the pressure's variations instead of its magnitude; the mixed WENO
+  // faces subtract the same constant from their normal momentum flux.
+  double p_shift;
   // scheme
   int L, weno_mode, convective, viscous, mixed;
   double vtot;  // total metric volume
@@ -184,6 +190,48 @@ __device__ __forceinline__ bool index_ok(const Dims& d, long long q, long long n
     if (!ok && d.dbg) atomicOr(d.dbg, code);
     return ok;
   }
+}
+
+// Traversal order of the assembly and of the z-face kernels (classification and the sweeps over
+// every z face). The t-th element is taken slab by slab: a slab is TY consecutive full rows
+// (x fastest, so warps and DRAM see the same contiguous rows as in the natural order), the
+// elements of one slab-plane come first, then the same slab one plane further in z, then the
+// next slab. The z stencils (nodes k -+ 3, faces' nodes k-2 .. k+3) then re-read planes of the
+// same slab that were read moments before, from L2, instead of planes millions of elements
+// away in the natural order, which on the 2048 x 384 x 256 workload no longer fit in L2. The y
+// stencil of the assembly reads 3 rows outside each slab (6/TY more rows). TY is the largest of
+// 32, 16, 8 that divides ny with nx TY a multiple of 256, so that the element count and each
+// block's share are unchanged and reductions keep their partitions' sizes; other grids keep
+// the natural order.
+__device__ __forceinline__ int slab_rows(const Dims& d) {
+  if ((d.nx & 7) == 0 && d.ny % 32 == 0) return 32;
+  if ((d.nx & 15) == 0 && d.ny % 16 == 0) return 16;
+  if ((d.nx & 31) == 0 && d.ny % 8 == 0) return 8;
+  return 0;
+}
+
+// Natural index (p ny + j) nx + i of the t-th element of nplanes planes in slab order
+// (0 <= t < nx ny nplanes < 2^32, TY = slab_rows(d) > 0); 32-bit divisions.
+__device__ __forceinline__ long long slab_order(const Dims& d, long long t, int nplanes, int TY) {
+  const unsigned S = (unsigned)d.nx * (unsigned)TY;  // elements of one slab-plane
+  const unsigned SP = S * (unsigned)nplanes;          // elements of one slab over all planes
+  const unsigned u = (unsigned)t;
+  const unsigned s = u / SP;
+  const unsigned rem = u - s * SP;
+  const unsigned p = rem / S;
+  const unsigned r = rem - p * S;  // (j - s TY) nx + i
+  return ((long long)p * d.ny + (long long)s * TY) * d.nx + r;
+}
+
+// The t-th interior node of the assembly (0 <= t < N) and the t-th z face of the z-face kernels
+// (0 <= t < nf[2]).
+__device__ __forceinline__ long long node_order(const Dims& d, long long t) {
+  const int TY = slab_rows(d);
+  return TY ? slab_order(d, t, d.nz, TY) : t;
+}
+__device__ __forceinline__ long long zface_order(const Dims& d, long long t) {
+  const int TY = slab_rows(d);
+  return TY ? slab_order(d, t, d.nz + 1, TY) : t;
 }
 
 __device__ __forceinline__ long long dir_stride(const Dims& d, int dir) {
