@@ -62,11 +62,12 @@ FLOPS32_PER_UNIT_MIXED = {
     "faces_x": 151, "faces_y": 151, "faces_z": 151,
     "assemble": 520, "sensor": 105,
 }
-# DRAM bytes (read + write) per unit from single ncu captures of the current kernels (the
-# capture, its grid and the scaling are in profiles/); None where no capture of the current
-# kernel exists.
-DRAM_BYTES_PER_UNIT = {"weno_x": 131.9, "weno_y": 190.8, "weno_z": 423.6}
-DRAM_BYTES_PER_UNIT_MIXED = {"weno_x": 120.5, "weno_y": 160.6, "weno_z": 242.9}
+# DRAM bytes (read + write) per node of the assembly, averaged over the three stages of its
+# launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on a
+# 1024 x 384 x 16 slice of the workload (profiles/dram-per-step_sbli-1024x384x16_fp64_mixed.md),
+# scaled to a launch by its nodes; traffic per unit grows in proportion with the nodes.
+DRAM_BYTES_PER_UNIT = {"assemble": 415.3}
+DRAM_BYTES_PER_UNIT_MIXED = {"assemble": 238.1}
 # FP64 rate from the SM count and clock: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz.
 FP64_UNITS_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_UNITS_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -274,6 +275,7 @@ def roofline(case, ktimes, weno_faces, ms_step, steps_timed, peak, flops, traffi
         "step_frac": round(step_tflops / peak, 4),
         "kernel_share": {k: round(v[0] / total_ms, 4) for k, v in sorted(busy.items())},
         "weno_face_fraction": round(sum(weno_faces) / (3 * busy["assemble"][1] * case.npts), 4),
+        "weno_faces_per_rhs": [round(f / busy["assemble"][1]) for f in weno_faces],
     }
 
 
@@ -327,6 +329,19 @@ def measure(case, args, world, local, peak, flops, traffic, pipe_name, extra_pip
     return {"value": value, "ms": ms, "ms_step_median": med, "value_median": job_rate(case.npts, 1, world, med),
             "repeats": len(per), "launches": launches, "clocks": clocks, "roofline": roof}, solver, w, r_old, \
         args.warmup + args.steps + args.timing_steps
+
+
+def host_page_locked(t):
+    """Page-lock a host tensor in place (cudaHostRegister). On the GB300 node an 8 GB buffer from
+    cudaHostAlloc (torch's pin_memory) copied at 75-87 GB/s, and one whose pages were first
+    written by a device-to-host copy at about 10 GB/s, while memory first written by the CPU and
+    registered this way copies at the link's 190-200 GB/s in both directions."""
+    import torch
+
+    rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * t.element_size(), 0)
+    if int(rc) != 0:
+        raise RuntimeError(f"cudaHostRegister failed ({rc})")
+    return t
 
 
 def field_errors(a, b):
@@ -420,7 +435,10 @@ def run_ours(args, world, rank, local):
     # end to end through the C ABI with host buffers: per step H2D of the state from pinned
     # memory, one RK3 step, D2H of the new state. The host buffer carries the FP64 trajectory,
     # which continues from the device state (the register r_old is not read by stage 0).
-    w_host = torch.empty(w.shape, dtype=torch.float64, pin_memory=True)
+    nbytes = 5 * case.npts * 8
+    w_host = torch.empty(w.shape, dtype=torch.float64)
+    w_host.fill_(0.0)  # first touch by the host's threads, before page-locking
+    host_page_locked(w_host)
     w_host.copy_(w)
     wd = torch.empty_like(w)
     del r_old
@@ -431,9 +449,9 @@ def run_ours(args, world, rank, local):
         solver.advance_n_host(w_host, wd, w, 1)
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     steps64 += args.steps + 1
-    nbytes = 5 * case.npts * 8
     e2e = {"value": case.npts * 3 * args.steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "host_buffer": "first-touched host memory page-locked with cudaHostRegister"}
     ws_gb = solver.workspace.numel() / 1e9
 
     out = {
@@ -453,6 +471,8 @@ def run_ours(args, world, rank, local):
     }
     # the FP64 trajectory on to the error leg's step count
     wd.copy_(w_host)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaHostUnregister(w_host.data_ptr())
     rest = max(args.error_steps - steps64, 0)
     if rest and not args.no_mixed:
         solver.advance_n(wd, w, rest)

@@ -36,11 +36,6 @@ int fail(int code, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(STRM_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
   } while (0)
 
-// Wray RK3 (Eq. RK); alpha_1 is printed +17/60 in the paper, read as -17/60 (first-order
-// consistency requires sum alpha + sum beta = 1).
-const double kAlpha[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
-const double kBeta[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
-
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Node fields held in FP64 and in FP32 (mixed precision only). FP64 precision: 12 fields, the
@@ -396,6 +391,7 @@ struct LaunchScope {
   strm_ctx* x;
   cudaStream_t st;
   int cls, e0 = -1;
+  int kernels = 1;  // kernels the scope launched (counted into x->launches)
   LaunchScope(strm_ctx* x_, cudaStream_t st_, int cls_) : x(x_), st(st_), cls(cls_) {
     if (x->timing) {
       if (x->recs.size() >= 2048) fold_timing(x);
@@ -404,7 +400,7 @@ struct LaunchScope {
     }
   }
   ~LaunchScope() {
-    x->launches += 1;
+    x->launches += kernels;
     if (e0 >= 0) {
       int e1 = take_event(x, e0 + 1);
       if (e1 >= 0) {
@@ -421,10 +417,17 @@ struct LaunchScope {
     expr;                      \
   } while (0)
 
+// a scope that launches n kernels, n given by the expression
+#define STRM_LAUNCH_N(cls, n_expr)   \
+  do {                               \
+    LaunchScope ls_(x, st, cls);     \
+    ls_.kernels = (n_expr);          \
+  } while (0)
+
 // One right-hand-side evaluation into R (stream order). With dt_mode, stage-0 work also sets the
 // step: dt_fixed > 0 is taken as is, otherwise the CFL step from the primitive pass.
 int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cfl, double dt_fixed,
-                cudaStream_t st, const RkFuse& rk = RkFuse{nullptr, nullptr, 0.0, 0.0}) {
+                cudaStream_t st, const RkFuse& rk = RkFuse{nullptr, nullptr, 0}) {
   const Dims& d = x->d;
   const Consts& C = x->C;
   const Bufs& B = x->B;
@@ -433,10 +436,10 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
   STRM_CK(cudaMemsetAsync(B.wcount, 0, 8 * sizeof(unsigned), st));
   STRM_LAUNCH(STRM_K_PRIMS, launch_prims(d, C, B, w, dt_mode && dt_fixed <= 0.0, st));
   if (dt_mode) STRM_LAUNCH(STRM_K_DT, launch_dt_finalize(d, B, cfl, dt_fixed, st));
-  if (C.bc[0] == kBcRecycle) STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_recycle(d, C, B, st));
+  if (C.bc[0] == kBcRecycle) STRM_LAUNCH_N(STRM_K_GHOST_PRIMS, (launch_recycle(d, C, B, st), 2));
   // digital-filter inflow: a new plane once per step, after the step's dt is known
   if (dt_mode && C.bc[0] == kBcDigitalFilter)
-    STRM_LAUNCH(STRM_K_GHOST_PRIMS, launch_df_update(d, x->df, B, false, st));
+    STRM_LAUNCH_N(STRM_K_GHOST_PRIMS, (launch_df_update(d, x->df, B, false, st), 2));
   // With overlap (not in timing mode, whose per-kernel events assume one stream): the ghost
   // fill runs on a side stream while the sensor covers the nodes whose stencils read no ghost;
   // the sensor's boundary shell follows the join. Later the x, y and z face stages, which
@@ -462,7 +465,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
     for (int b = 0; b < 2; ++b) STRM_CK(cudaStreamWaitEvent(x->side[b], x->ev[2], 0));
     for (int dir = 0; dir < 3; ++dir) {
       cudaStream_t sd = dir == 0 ? st : x->side[dir - 1];
-      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, sd));
+      STRM_LAUNCH_N(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, sd));
       if (C.weno_mode != STRM_WENO_OFF)
         STRM_LAUNCH(STRM_K_WENO_X + dir, launch_weno_dir(d, C, B, dir, x->weno_grid, sd));
     }
@@ -472,7 +475,7 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
     }
   } else if (C.convective) {
     for (int dir = 0; dir < 3; ++dir)
-      STRM_LAUNCH(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, st));
+      STRM_LAUNCH_N(STRM_K_FACES_X + dir, launch_faces_dir(d, C, B, dir, x->weno_grid * 2, st));
     if (C.weno_mode != STRM_WENO_OFF) {
       for (int dir = 0; dir < 3; ++dir)
         STRM_LAUNCH(STRM_K_WENO_X + dir, launch_weno_dir(d, C, B, dir, x->weno_grid, st));
@@ -493,14 +496,14 @@ int enqueue_rhs(strm_ctx* x, const double* w, double* R, bool dt_mode, double cf
 int enqueue_step(strm_ctx* x, double* w, double* r_old, double dt, double cfl, cudaStream_t st) {
   for (int stage = 0; stage < 3; ++stage) {
     if (!x->C.forcing) {  // no forcing to reduce first: the assembly applies the stage update
-      int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st, RkFuse{w, r_old, kAlpha[stage], kBeta[stage]});
+      int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st, RkFuse{w, r_old, stage});
       if (rc) return rc;
       continue;
     }
     int rc = enqueue_rhs(x, w, x->B.R, stage == 0, cfl, dt, st);
     if (rc) return rc;
     STRM_LAUNCH(STRM_K_RK_UPDATE,
-                launch_rk_update(x->d, x->C, x->B, w, r_old, kAlpha[stage], kBeta[stage], st));
+                launch_rk_update(x->d, x->C, x->B, w, r_old, stage, st));
   }
   STRM_CK_LAUNCH();
   return STRM_OK;

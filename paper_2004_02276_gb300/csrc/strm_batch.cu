@@ -177,10 +177,10 @@ __global__ void kb_force_finalize(BatchIndex X) {
   body_force_finalize(I.B, inst_blocks(X, kKindNode, blockIdx.x), 1.0 / I.C.vtot, sh);
 }
 
-__global__ void __launch_bounds__(256) kb_rk_update(BatchIndex X, double alpha, double beta) {
+__global__ void __launch_bounds__(256) kb_rk_update(BatchIndex X, int stage) {
   int blk;
   const Inst& I = block_inst(X, kKindNode, blk);
-  body_rk_update(I.d, I.C, I.B, I.w, I.r_old, alpha, beta, blk);
+  body_rk_update(I.d, I.C, I.B, I.w, I.r_old, stage, blk);
 }
 
 }  // namespace strm
@@ -189,8 +189,6 @@ using namespace strm;
 
 namespace {
 
-const double kAlphaE[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};  // Eq. RK, alpha_1 read as -17/60
-const double kBetaE[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -294,7 +292,7 @@ int enqueue_step(const strm_ensemble* E, double dt, double cfl, cudaStream_t st)
   BatchIndex X = index_of(E);
   for (int stage = 0; stage < 3; ++stage) {
     enqueue_rhs(E, stage == 0, cfl, dt, st);
-    kb_rk_update<<<E->total_blocks[kKindNode], 256, 0, st>>>(X, kAlphaE[stage], kBetaE[stage]);
+    kb_rk_update<<<E->total_blocks[kKindNode], 256, 0, st>>>(X, stage);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("ensemble launch: ") + cudaGetErrorString(e));

@@ -141,6 +141,13 @@ __device__ __forceinline__ void body_dt_finalize(const Bufs& B, int nparts, doub
     B.scal[kScalDt] = dt;
     B.scal[kScalCflMax] = m;
     B.scal[kScalTime] += dt;
+    // the stage weights of this step, once, instead of two FP64 products in every thread of
+    // every stage update
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      B.scal[kScalAdt + s] = rk_alpha(s) * dt;
+      B.scal[kScalBdt + s] = rk_beta(s) * dt;
+    }
   }
 }
 
@@ -677,12 +684,11 @@ __device__ __forceinline__ void body_force_finalize(const Bufs& B, int nparts, d
 // in both precisions.
 __device__ __forceinline__ void body_rk_update(const Dims& d, const Consts& C, const Bufs& B,
                                                double* __restrict__ w, double* __restrict__ r_old,
-                                               double alpha, double beta, int blk) {
+                                               int stage, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   if (q >= d.N) return;
-  double dt = B.scal[kScalDt];
   double f = C.forcing ? B.scal[kScalForce] : 0.0;
-  double ad = alpha * dt, bd = beta * dt;
+  const double ad = B.scal[kScalAdt + stage], bd = B.scal[kScalBdt + stage];
   double uq = 0.0;
   if (C.forcing) {
     int i, j, k;
@@ -696,7 +702,7 @@ __device__ __forceinline__ void body_rk_update(const Dims& d, const Consts& C, c
     if (m == 1) rr += f;
     if (m == 4) rr += f * uq;
     double wn = w[e] + bd * rr;
-    if (alpha != 0.0) wn += ad * r_old[e];
+    if (stage != 0) wn += ad * r_old[e];  // alpha_0 = 0
     w[e] = wn;
     r_old[e] = rr;
   }
@@ -1158,6 +1164,153 @@ __device__ __forceinline__ void body_central(const Dims& d, const Consts& C, con
   }
 }
 
+// Central flux at every face of direction DIR = 1 (y) or 2 (z) by sweeps along DIR that reuse
+// the split flux's pair terms. The flux at face s (between nodes s-1 and s) is the sum over
+// l = 1..L of the L pairs (a, a + l), s - l <= a <= s - 1 (Eq. encflux), each pair contributing
+// q (1, phi_a + phi_b) with q = (a_l/4)(rho_a + rho_b)(u_a + u_b) along DIR. Pair (a, a + l)
+// serves the l faces it spans, so a thread that walks consecutive faces computes at each face
+// only the L pairs starting at node s - 1 and keeps the others in registers, and loads one new
+// node per face instead of 2L (the same products, summed in another order than body_central;
+// the pressure part is as in central_flux). Thread t takes segment seg of the column (i, c):
+// i = t mod nx, then c (z for y sweeps, y for z sweeps), then seg, so a warp walks 32
+// consecutive x and reads coalesced rows; each segment first computes the L - 1 pair
+// generations before its first face. Faces past the last one of the column are not computed.
+template <int L, int DIR, typename R>
+__device__ __forceinline__ void body_central_sweep(const Dims& d, const Consts& C, const Bufs& B, long long t) {
+  static_assert(DIR == 1 || DIR == 2, "sweeps run along y or z");
+  constexpr int SEG = kSweepSeg;
+  const int ncol = DIR == 1 ? d.nz : d.ny;   // columns per x
+  const int nfa = (DIR == 1 ? d.ny : d.nz) + 1;  // faces along the sweep
+  const long long nseg = (nfa + SEG - 1) / SEG;
+  if (t >= (long long)d.nx * ncol * nseg) return;
+  const int i = (int)(t % d.nx);
+  const long long r = t / d.nx;
+  const int c = (int)(r % ncol);
+  const int s0 = (int)(r / ncol) * SEG;
+  const int s1 = min(s0 + SEG, nfa);  // faces s0 .. s1 - 1
+  // nodes read: s0 - L .. s1 - 2 + L along DIR (ghosts included)
+  {
+    const int jj = DIR == 1 ? s0 - L : c, kk = DIR == 1 ? c : s0 - L;
+    if (!stencil_ok(d, i, jj, kk, DIR, 0, s1 - s0 + 2 * L - 2, kDbgFace)) return;
+  }
+  const Nodes<R>& P = nodes<R>(B);
+  const Coefs<R>& K = coefs<R>(C);
+  const R* __restrict__ ud = DIR == 1 ? P.v : P.w;
+  const long long st = dir_stride(d, DIR);
+  // node (i, j, k) with the sweep coordinate at -0; n(s) = base + s * st
+  const long long base = DIR == 1 ? gidx(d, i, 0, c) : gidx(d, i, c, 0);
+  const long long nf = d.nf[DIR];
+  R* out = face_flux<R>(B, DIR);
+  // node window: nodes s-1 .. s-1+L at face s (rho, u_d, u, v, w, H) and the pressure at
+  // nodes s-L .. s+L-1
+  R wr[L + 1], wu[L + 1], wv[L + 1], ww[L + 1], wh[L + 1], pw[2 * L];
+  const int sb = s0 - L + 1;  // first (warm-up) face of the walk
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    const long long n = base + (long long)(sb - 1 + m) * st;
+    wr[m] = __ldg(P.rho + n);
+    wu[m] = __ldg(P.u + n);
+    wv[m] = __ldg(P.v + n);
+    ww[m] = __ldg(P.w + n);
+    wh[m] = __ldg(P.H + n);
+  }
+#pragma unroll
+  for (int m = 0; m < 2 * L; ++m) {
+    const int sn = sb - L + m;  // node index along the sweep; below -G it is never used
+    pw[m] = sn >= -G ? __ldg(P.p + base + (long long)sn * st) : R(0);
+  }
+  // pair history: hq[l][g] (and hu, hv, hw, hh) holds the terms of the pair of length l that
+  // starts at node s-2-g (g = 0 .. l-2: the l-1 generations before this face); filled by the
+  // warm-up faces before the first face written
+  R hq[L + 1][L], hu[L + 1][L], hv[L + 1][L], hw[L + 1][L], hh[L + 1][L];
+#pragma unroll
+  for (int l = 0; l <= L; ++l)
+#pragma unroll
+    for (int g = 0; g < L; ++g) hq[l][g] = hu[l][g] = hv[l][g] = hw[l][g] = hh[l][g] = R(0);
+  for (int s = sb; s < s1; ++s) {
+    // new pairs (s-1, s-1+l), l = 1..L
+    R nq[L + 1], nu[L + 1], nv[L + 1], nw[L + 1], nh[L + 1];
+#pragma unroll
+    for (int l = 1; l <= L; ++l) {
+      const R rs = wr[0] + wr[l];
+      const R us = wu[0] + wu[l], vs = wv[0] + wv[l], ws = ww[0] + ww[l], hs = wh[0] + wh[l];
+      const R uds = DIR == 1 ? vs : ws;
+      const R q = (K.aq[l] * rs) * uds;
+      nq[l] = q;
+      nu[l] = q * us;
+      nv[l] = q * vs;
+      nw[l] = q * ws;
+      nh[l] = q * hs;
+    }
+    if (s >= s0) {
+      // face s: the new pairs of every length and the l-1 previous generations of length l
+      R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0);
+#pragma unroll
+      for (int l = 1; l <= L; ++l) {
+        a0 += nq[l];
+        a1 += nu[l];
+        a2 += nv[l];
+        a3 += nw[l];
+        a4 += nh[l];
+#pragma unroll
+        for (int g = 0; g < l - 1; ++g) {
+          a0 += hq[l][g];
+          a1 += hu[l][g];
+          a2 += hv[l][g];
+          a3 += hw[l][g];
+          a4 += hh[l][g];
+        }
+      }
+      R ap = R(0);
+#pragma unroll
+      for (int m = 0; m < L; ++m) ap = fma(K.ap[m], pw[L - 1 - m] + pw[L + m], ap);
+      const long long q = DIR == 1 ? ((long long)c * (d.ny + 1) + s) * d.nx + i
+                                   : ((long long)s * d.ny + c) * d.nx + i;
+      out[q] = R(2) * a0;
+      out[nf + q] = a1;
+      out[2 * nf + q] = DIR == 1 ? a2 + ap : a2;
+      out[3 * nf + q] = DIR == 2 ? a3 + ap : a3;
+      out[4 * nf + q] = a4;
+    }
+    // shift the pair history (generation 0 is the most recent) and the windows
+#pragma unroll
+    for (int l = 2; l <= L; ++l) {
+#pragma unroll
+      for (int g = l - 2; g > 0; --g) {
+        hq[l][g] = hq[l][g - 1];
+        hu[l][g] = hu[l][g - 1];
+        hv[l][g] = hv[l][g - 1];
+        hw[l][g] = hw[l][g - 1];
+        hh[l][g] = hh[l][g - 1];
+      }
+      hq[l][0] = nq[l];
+      hu[l][0] = nu[l];
+      hv[l][0] = nv[l];
+      hw[l][0] = nw[l];
+      hh[l][0] = nh[l];
+    }
+    if (s + 1 < s1) {
+#pragma unroll
+      for (int m = 0; m < L; ++m) {
+        wr[m] = wr[m + 1];
+        wu[m] = wu[m + 1];
+        wv[m] = wv[m + 1];
+        ww[m] = ww[m + 1];
+        wh[m] = wh[m + 1];
+      }
+#pragma unroll
+      for (int m = 0; m < 2 * L - 1; ++m) pw[m] = pw[m + 1];
+      const long long n = base + (long long)(s + L) * st;  // node s + L: window of face s + 1
+      wr[L] = __ldg(P.rho + n);
+      wu[L] = __ldg(P.u + n);
+      wv[L] = __ldg(P.v + n);
+      ww[L] = __ldg(P.w + n);
+      wh[L] = __ldg(P.H + n);
+      pw[2 * L - 1] = __ldg(P.p + base + (long long)(s + L) * st);
+    }
+  }
+}
+
 // Characteristic WENO flux at the faces of the WENO list (sensor mode) or at every face (WENO
 // everywhere); FP64, or the mixed-precision variant writing FP32 face fluxes.
 template <int DIR, bool MIXED>
@@ -1287,7 +1440,7 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
 template <int L, typename R>
 __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, const Bufs& B,
                                               double* __restrict__ Rout, int blk, double* sh,
-                                              const RkFuse& rk = RkFuse{nullptr, nullptr, 0.0, 0.0}) {
+                                              const RkFuse& rk = RkFuse{nullptr, nullptr, 0}) {
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   double fpart = 0.0;
   bool live = t < d.N;
@@ -1351,14 +1504,13 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
     if (rk.w) {
       // the RK stage update of this node (body_rk_update without the forcing terms): the
       // residual stays in registers instead of a round trip through memory
-      const double dt = B.scal[kScalDt];
-      const double ad = rk.alpha * dt, bd = rk.beta * dt;
+      const double ad = B.scal[kScalAdt + rk.stage], bd = B.scal[kScalBdt + rk.stage];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
         const long long e = m * d.N + q;
         const double rr = (m == 0 && sizeof(R) != sizeof(double)) ? mass64 : to_f64(res[m]);
         double wn = rk.w[e] + bd * rr;
-        if (rk.alpha != 0.0) wn += ad * rk.r_old[e];
+        if (rk.stage != 0) wn += ad * rk.r_old[e];  // alpha_0 = 0
         rk.w[e] = wn;
         rk.r_old[e] = rr;
       }
@@ -1367,7 +1519,7 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
       for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
       if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
     }
-    fpart = to_f64(res[1]) * __ldg(B.vol + j);
+    if (C.forcing) fpart = to_f64(res[1]) * __ldg(B.vol + j);
   }
   if (C.forcing) {
     double s = block_sum(fpart, sh);

@@ -21,6 +21,8 @@ namespace strm {
 constexpr int G = 3;   // ghost layers (central L <= 3, six-node WENO5 stencil)
 constexpr int GX = 4;  // x offset of the interior in a ghosted row
 constexpr int kRedBlock = 256;
+// faces per thread of the y/z central-flux sweeps (body_central_sweep)
+constexpr int kSweepSeg = 32;
 
 struct Dims {
   int nx, ny, nz;
@@ -141,11 +143,18 @@ template <> __device__ __forceinline__ const Coefs<float>& coefs<float>(const Co
 struct RkFuse {
   double* w;
   double* r_old;
-  double alpha, beta;
+  int stage;  // RK stage 0..2
 };
 
-// device scalars
-enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalRecycle = 4, kScalCount = 16 };
+// Wray's low-storage RK3 (Eq. RK): w <- w + dt (alpha_s R_old + beta_s R). alpha_1 is printed
+// +17/60 in the paper and read as -17/60 (first-order consistency: sum alpha + sum beta = 1).
+__host__ __device__ constexpr double rk_alpha(int s) { return s == 0 ? 0.0 : (s == 1 ? -17.0 / 60.0 : -5.0 / 12.0); }
+__host__ __device__ constexpr double rk_beta(int s) { return s == 0 ? 8.0 / 15.0 : (s == 1 ? 5.0 / 12.0 : 3.0 / 4.0); }
+
+// device scalars: dt, time, forcing, CFL maximum, recycling scale, alpha_s dt (slots 5..7),
+// the conserved totals (8..12), beta_s dt (13..15)
+enum { kScalDt = 0, kScalTime = 1, kScalForce = 2, kScalCflMax = 3, kScalRecycle = 4, kScalAdt = 5,
+       kScalBdt = 13, kScalCount = 16 };
 
 __device__ __forceinline__ long long gidx(const Dims& d, int i, int j, int k) {
   return ((long long)(k + G) * d.py + (j + G)) * d.px + (i + GX);

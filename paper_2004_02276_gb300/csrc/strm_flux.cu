@@ -16,10 +16,22 @@ __global__ void __launch_bounds__(256) k_classify(Dims d, Consts C, Bufs B) {
   body_classify<L, DIR, R>(d, C, B, blockIdx.x);
 }
 
+// use_list: the compacted central list of the sensor mode; yield: the list kernel of a y or z
+// direction leaves the faces to the sweep when at least half of them are central (the choice is
+// taken on the device from the classification's count, so a captured graph keeps both launches).
 template <int L, int DIR, typename R>
-__global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list) {
+__global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list, int yield) {
+  if (yield && 2LL * B.wcount[4 + DIR] >= d.nf[DIR]) return;
   body_central<L, DIR, R>(d, C, B, use_list, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                           (long long)gridDim.x * blockDim.x);
+}
+
+// Sweep over every y or z face (body_central_sweep); in sensor mode it runs only when at least
+// half of the faces are central (the WENO kernel then overwrites the others).
+template <int L, int DIR, typename R>
+__global__ void __launch_bounds__(256) k_central_sweep(Dims d, Consts C, Bufs B, int sensor) {
+  if (sensor && 2LL * B.wcount[4 + DIR] < d.nf[DIR]) return;
+  body_central_sweep<L, DIR, R>(d, C, B, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int DIR, bool MIXED>
@@ -39,34 +51,56 @@ __global__ void __launch_bounds__(256) k_assemble(Dims d, Consts C, Bufs B, doub
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Threads of the sweep along DIR: one per (x, column, segment of kSweepSeg faces).
+static long long sweep_threads(const Dims& d, int dir) {
+  const long long nfa = (dir == 1 ? d.ny : d.nz) + 1;
+  return (long long)d.nx * (dir == 1 ? d.nz : d.ny) * ((nfa + kSweepSeg - 1) / kSweepSeg);
+}
+
 template <int L, int DIR, typename R>
-static void faces_one(const Dims& d, const Consts& C, const Bufs& B, bool sensor, unsigned nb, int grid,
-                      cudaStream_t s) {
-  if (sensor) k_classify<L, DIR, R><<<nb, 256, 0, s>>>(d, C, B);
-  k_central<L, DIR, R><<<sensor ? (unsigned)grid : nb, 256, 0, s>>>(d, C, B, sensor ? 1 : 0);
+static int faces_one(const Dims& d, const Consts& C, const Bufs& B, bool sensor, unsigned nb, int grid,
+                     cudaStream_t s) {
+  int n = 0;
+  if (sensor) {
+    k_classify<L, DIR, R><<<nb, 256, 0, s>>>(d, C, B);
+    ++n;
+  }
+  if constexpr (DIR == 0) {
+    k_central<L, DIR, R><<<sensor ? (unsigned)grid : nb, 256, 0, s>>>(d, C, B, sensor ? 1 : 0, 0);
+    return n + 1;
+  } else {
+    k_central_sweep<L, DIR, R><<<blocks_for(sweep_threads(d, DIR), 256), 256, 0, s>>>(d, C, B, sensor ? 1 : 0);
+    ++n;
+    if (sensor) {
+      k_central<L, DIR, R><<<(unsigned)grid, 256, 0, s>>>(d, C, B, 1, 1);
+      ++n;
+    }
+    return n;
+  }
 }
 
 template <int L, typename R>
-static void faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, bool sensor, unsigned nb,
-                      int grid, cudaStream_t s) {
-  if (dir == 0) faces_one<L, 0, R>(d, C, B, sensor, nb, grid, s);
-  else if (dir == 1) faces_one<L, 1, R>(d, C, B, sensor, nb, grid, s);
-  else faces_one<L, 2, R>(d, C, B, sensor, nb, grid, s);
+static int faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, bool sensor, unsigned nb,
+                     int grid, cudaStream_t s) {
+  if (dir == 0) return faces_one<L, 0, R>(d, C, B, sensor, nb, grid, s);
+  if (dir == 1) return faces_one<L, 1, R>(d, C, B, sensor, nb, grid, s);
+  return faces_one<L, 2, R>(d, C, B, sensor, nb, grid, s);
 }
 
-// Face stage of one direction: sensor mode classifies then runs the central list; WENO off runs
-// the central flux over every face; WENO everywhere needs no central flux.
-void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {
-  if (C.weno_mode == 2) return;
+// Face stage of one direction: sensor mode classifies, then the x direction runs the central
+// list and the y and z directions either sweep every face or run the list (chosen on the device
+// from the central count); WENO off sweeps (y, z) or covers (x) every face; WENO everywhere needs
+// no central flux. Returns the number of kernels launched.
+int launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {
+  if (C.weno_mode == 2) return 0;
   bool sensor = C.weno_mode == 1;
   unsigned nb = blocks_for(d.nf[dir], 256);
   if (C.mixed) {
-    if (C.L == 3) faces_dir<3, float>(d, C, B, dir, sensor, nb, grid, s);
-    else faces_dir<2, float>(d, C, B, dir, sensor, nb, grid, s);
-  } else {
-    if (C.L == 3) faces_dir<3, double>(d, C, B, dir, sensor, nb, grid, s);
-    else faces_dir<2, double>(d, C, B, dir, sensor, nb, grid, s);
+    if (C.L == 3) return faces_dir<3, float>(d, C, B, dir, sensor, nb, grid, s);
+    return faces_dir<2, float>(d, C, B, dir, sensor, nb, grid, s);
   }
+  if (C.L == 3) return faces_dir<3, double>(d, C, B, dir, sensor, nb, grid, s);
+  return faces_dir<2, double>(d, C, B, dir, sensor, nb, grid, s);
 }
 
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s) {

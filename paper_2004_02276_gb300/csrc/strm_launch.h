@@ -56,14 +56,16 @@ void launch_band_theta(const Dims& d, const Consts& C, const Bufs& B, cudaStream
 void launch_ghost_scalars(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
 // prescribed switch input: the FP64 sensor field at the interior nodes from theta[N]
 void launch_theta_set(const Dims& d, const Bufs& B, const double* theta, cudaStream_t s);
-void launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
+// returns the number of kernels launched
+int launch_faces_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 void launch_weno_dir(const Dims& d, const Consts& C, const Bufs& B, int dir, int grid, cudaStream_t s);
 // residual into R, or (rk.w set) the RK stage update of w and r_old without writing R
 void launch_assemble(const Dims& d, const Consts& C, const Bufs& B, double* R, const RkFuse& rk,
                      cudaStream_t s);
 void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaStream_t s);
+// stage update s of Eq. RK with the weights k_dt_finalize stored for this step
 void launch_rk_update(const Dims& d, const Consts& C, const Bufs& B, double* w, double* r_old,
-                      double alpha, double beta, cudaStream_t s);
+                      int stage, cudaStream_t s);
 void launch_apply_forcing(const Dims& d, const Bufs& B, double* rhs, cudaStream_t s);
 void launch_totals(const Dims& d, const Bufs& B, const double* w, cudaStream_t s);
 void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsigned char* out,

@@ -58,9 +58,8 @@ __global__ void k_force_finalize(Bufs B, int nparts, double inv_vtot) {
 }
 
 __global__ void __launch_bounds__(256) k_rk_update(Dims d, Consts C, Bufs B, double* __restrict__ w,
-                                                   double* __restrict__ r_old, double alpha,
-                                                   double beta) {
-  body_rk_update(d, C, B, w, r_old, alpha, beta, blockIdx.x);
+                                                   double* __restrict__ r_old, int stage) {
+  body_rk_update(d, C, B, w, r_old, stage, blockIdx.x);
 }
 
 // Forcing terms added to an explicit residual (compute_rhs).
@@ -226,8 +225,8 @@ void launch_force_finalize(const Dims& d, const Consts& C, const Bufs& B, cudaSt
 }
 
 void launch_rk_update(const Dims& d, const Consts& C, const Bufs& B, double* w, double* r_old,
-                      double alpha, double beta, cudaStream_t s) {
-  k_rk_update<<<blocks_for(d.N, 256), 256, 0, s>>>(d, C, B, w, r_old, alpha, beta);
+                      int stage, cudaStream_t s) {
+  k_rk_update<<<blocks_for(d.N, 256), 256, 0, s>>>(d, C, B, w, r_old, stage);
 }
 
 void launch_apply_forcing(const Dims& d, const Bufs& B, double* rhs, cudaStream_t s) {
