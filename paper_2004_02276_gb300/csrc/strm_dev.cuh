@@ -22,7 +22,7 @@ constexpr int G = 3;   // ghost layers (central L <= 3, six-node WENO5 stencil)
 constexpr int GX = 4;  // x offset of the interior in a ghosted row
 constexpr int kRedBlock = 256;
 // faces per thread of the y/z central-flux sweeps (body_central_sweep)
-constexpr int kSweepSeg = 32;
+constexpr int kSweepSeg = 64;
 
 struct Dims {
   int nx, ny, nz;

@@ -16,21 +16,31 @@ __global__ void __launch_bounds__(256) k_classify(Dims d, Consts C, Bufs B) {
   body_classify<L, DIR, R>(d, C, B, blockIdx.x);
 }
 
+// Sensor mode, y and z faces: the sweep over every face replaces the central list when enough
+// faces are central. It computes about 76 FP64 operations per face against the list's 86 but
+// also at the WENO faces, so in FP64 (pipe-bound) it pays from about 88 % central faces and is
+// chosen from 85 %; in mixed precision (memory-bound) it reads one node per face instead of 2L
+// and is chosen from 50 %. The choice is taken on the device from the classification's count,
+// so a captured graph keeps both launches.
+template <typename R>
+__device__ __forceinline__ bool sweep_chosen(unsigned central, long long nf) {
+  return sizeof(R) == sizeof(double) ? 20LL * central >= 17LL * nf : 2LL * central >= nf;
+}
+
 // use_list: the compacted central list of the sensor mode; yield: the list kernel of a y or z
-// direction leaves the faces to the sweep when at least half of them are central (the choice is
-// taken on the device from the classification's count, so a captured graph keeps both launches).
+// direction leaves the faces to the sweep when sweep_chosen.
 template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_central(Dims d, Consts C, Bufs B, int use_list, int yield) {
-  if (yield && 2LL * B.wcount[4 + DIR] >= d.nf[DIR]) return;
+  if (yield && sweep_chosen<R>(B.wcount[4 + DIR], d.nf[DIR])) return;
   body_central<L, DIR, R>(d, C, B, use_list, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                           (long long)gridDim.x * blockDim.x);
 }
 
-// Sweep over every y or z face (body_central_sweep); in sensor mode it runs only when at least
-// half of the faces are central (the WENO kernel then overwrites the others).
+// Sweep over every y or z face (body_central_sweep); in sensor mode it runs only when
+// sweep_chosen (the WENO kernel then overwrites the flagged faces).
 template <int L, int DIR, typename R>
 __global__ void __launch_bounds__(256) k_central_sweep(Dims d, Consts C, Bufs B, int sensor) {
-  if (sensor && 2LL * B.wcount[4 + DIR] < d.nf[DIR]) return;
+  if (sensor && !sweep_chosen<R>(B.wcount[4 + DIR], d.nf[DIR])) return;
   body_central_sweep<L, DIR, R>(d, C, B, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
