@@ -1342,6 +1342,38 @@ __device__ __forceinline__ void body_weno(const Dims& d, const Consts& C, const 
 
 // ------------------------------------------------------------------------------ assembly
 
+// The viscous terms from the derivatives at one node (Section 2.1 and Eqs. sigma, heat_vec):
+// du[a][b] = d_b u_a, lap[a] = lap u_a, dT, lapT, dmu = grad mu, ddiv = grad(div u), the node's
+// mu and velocity; V = (0, V_1, V_2, V_3, V_E).
+template <typename R>
+__device__ __forceinline__ void viscous_combine(const Coefs<R>& K, const R (&du)[3][3], const R (&lap)[3],
+                                                const R (&dT)[3], R lapT, const R (&dmu)[3],
+                                                const R (&ddiv)[3], R mu, const R (&uu)[3], R* V) {
+  const R div = du[0][0] + du[1][1] + du[2][2];
+  const R tdiv = R(2.0 / 3.0) * div;
+  // symmetric strain sums S_ab = d_b u_a + d_a u_b
+  const R S00 = R(2) * du[0][0], S11 = R(2) * du[1][1], S22 = R(2) * du[2][2];
+  const R S01 = du[0][1] + du[1][0], S02 = du[0][2] + du[2][0], S12 = du[1][2] + du[2][1];
+  R sm[3];
+  sm[0] = fma(dmu[0], S00, fma(dmu[1], S01, dmu[2] * S02));
+  sm[1] = fma(dmu[0], S01, fma(dmu[1], S11, dmu[2] * S12));
+  sm[2] = fma(dmu[0], S02, fma(dmu[1], S12, dmu[2] * S22));
+  R Vm[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Vm[a] = fma(mu, fma(ddiv[a], R(1.0 / 3.0), lap[a]), fma(-tdiv, dmu[a], sm[a]));
+  R work = fma(uu[0], Vm[0], fma(uu[1], Vm[1], uu[2] * Vm[2]));
+  // sigma_ij d_j u_i = mu [ sum_ab S_ab d_b u_a - 2/3 div^2 ], and by symmetry
+  // sum_ab S_ab d_b u_a = sum_a S_aa d_a u_a + sum_{a<b} S_ab^2
+  R diss = fma(S00, du[0][0], fma(S11, du[1][1], fma(S22, du[2][2], fma(S01, S01, fma(S02, S02, S12 * S12)))));
+  diss = mu * fma(-tdiv, div, diss);
+  R heat = K.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
+  V[0] = R(0);
+  V[1] = Vm[0];
+  V[2] = Vm[1];
+  V[3] = Vm[2];
+  V[4] = work + diss + heat;
+}
+
 // Viscous terms in Laplacian form at node n (Section 2.1 and Eqs. sigma, heat_vec):
 //   V_i = mu lap u_i + mu/3 d_i(div) + d_j mu (d_j u_i + d_i u_j) - 2/3 div d_i mu,
 //   V_E = u_i V_i + sigma_ij d_j u_i + k lap T + d_j k d_j T,  k = cp mu / Pr,
@@ -1408,31 +1440,68 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
   ddiv[0] = dsum<L>(P.div, n, 1, K.ax);
   ddiv[1] = dsum<L>(P.div, n, sy, K.a) * hy;
   ddiv[2] = dsum<L>(P.div, n, sz, K.az);
-  const R mu = __ldg(P.mu + n);
-  const R div = du[0][0] + du[1][1] + du[2][2];
-  const R tdiv = R(2.0 / 3.0) * div;
-  // symmetric strain sums S_ab = d_b u_a + d_a u_b
-  const R S00 = R(2) * du[0][0], S11 = R(2) * du[1][1], S22 = R(2) * du[2][2];
-  const R S01 = du[0][1] + du[1][0], S02 = du[0][2] + du[2][0], S12 = du[1][2] + du[2][1];
-  R sm[3];
-  sm[0] = fma(dmu[0], S00, fma(dmu[1], S01, dmu[2] * S02));
-  sm[1] = fma(dmu[0], S01, fma(dmu[1], S11, dmu[2] * S12));
-  sm[2] = fma(dmu[0], S02, fma(dmu[1], S12, dmu[2] * S22));
-  R Vm[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) Vm[a] = fma(mu, fma(ddiv[a], R(1.0 / 3.0), lap[a]), fma(-tdiv, dmu[a], sm[a]));
   const R uu[3] = {__ldg(P.u + n), __ldg(P.v + n), __ldg(P.w + n)};
-  R work = fma(uu[0], Vm[0], fma(uu[1], Vm[1], uu[2] * Vm[2]));
-  // sigma_ij d_j u_i = mu [ sum_ab S_ab d_b u_a - 2/3 div^2 ], and by symmetry
-  // sum_ab S_ab d_b u_a = sum_a S_aa d_a u_a + sum_{a<b} S_ab^2
-  R diss = fma(S00, du[0][0], fma(S11, du[1][1], fma(S22, du[2][2], fma(S01, S01, fma(S02, S02, S12 * S12)))));
-  diss = mu * fma(-tdiv, div, diss);
-  R heat = K.cp_pr * (mu * lapT + dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]);
-  V[0] = R(0);
-  V[1] = Vm[0];
-  V[2] = Vm[1];
-  V[3] = Vm[2];
-  V[4] = work + diss + heat;
+  viscous_combine<R>(K, du, lap, dT, lapT, dmu, ddiv, __ldg(P.mu + n), uu, V);
+}
+
+// Convective part of the residual at node (i, j, k): R_m = -sum_d (f_{s+1} - f_s)/h_d (Eq.
+// num_flux) with the staggered-wall rule; in mixed precision also the FP64 mass difference.
+template <typename R>
+__device__ __forceinline__ void convective_residual(const Dims& d, const Consts& C, const Bufs& B, int i, int j,
+                                                    int k, R* res, double& mass64) {
+  const Coefs<R>& K = coefs<R>(C);
+  long long qx = ((long long)k * d.ny + j) * (d.nx + 1) + i;
+  long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
+  long long qz = ((long long)k * d.ny + j) * d.nx + i;
+  long long sxy = (long long)d.nx * d.ny;
+  R hy = __ldg(metric<R>(B).inv_hy + j);
+  bool wlo = C.bc[2] == kBcWall && j == 0, whi = C.bc[3] == kBcWall && j == d.ny - 1;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const R* fx = face_flux<R>(B, 0) + m * d.nf[0];
+    const R* fy = face_flux<R>(B, 1) + m * d.nf[1];
+    const R* fz = face_flux<R>(B, 2) + m * d.nf[2];
+    R ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
+    // staggered wall interface: no mass, x/z momentum or energy crosses it
+    if (m != 2) {
+      if (wlo) ylo = R(0);
+      if (whi) yhi = R(0);
+    }
+    res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
+               (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * K.inv_dz);
+    if (m == 0 && sizeof(R) != sizeof(double)) {
+      // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
+      // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
+      // FP64 round-off as in the FP64 path
+      mass64 = -((to_f64(__ldg(fx + qx + 1)) - to_f64(__ldg(fx + qx))) * C.k64.inv_dx +
+                 (to_f64(yhi) - to_f64(ylo)) * __ldg(B.m64.inv_hy + j) +
+                 (to_f64(__ldg(fz + qz + sxy)) - to_f64(__ldg(fz + qz))) * C.k64.inv_dz);
+    }
+  }
+}
+
+// The residual of node q: with rk.w, the RK stage update of this node (body_rk_update without
+// the forcing terms; the residual stays in registers instead of a round trip through memory),
+// else stored to Rout. FP64 in both precisions; mixed precision takes the FP64 mass difference.
+template <typename R>
+__device__ __forceinline__ void stage_or_store(const Dims& d, const Bufs& B, long long q, const R* res,
+                                               double mass64, double* __restrict__ Rout, const RkFuse& rk) {
+  if (rk.w) {
+    const double ad = B.scal[kScalAdt + rk.stage], bd = B.scal[kScalBdt + rk.stage];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const long long e = m * d.N + q;
+      const double rr = (m == 0 && sizeof(R) != sizeof(double)) ? mass64 : to_f64(res[m]);
+      double wn = rk.w[e] + bd * rr;
+      if (rk.stage != 0) wn += ad * rk.r_old[e];  // alpha_0 = 0
+      rk.w[e] = wn;
+      rk.r_old[e] = rr;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
+    if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
+  }
 }
 
 // Residual per node: R = -sum_d (f_{s+1} - f_s)/h_d (Eq. num_flux, with the staggered-wall rule)
@@ -1462,63 +1531,16 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
     long long r = q / d.nx;
     int j = (int)(r % d.ny);
     int k = (int)(r / d.ny);
-    const Coefs<R>& K = coefs<R>(C);
     R res[5] = {R(0), R(0), R(0), R(0), R(0)};
     double mass64 = 0.0;
-    if (C.convective) {
-      long long qx = ((long long)k * d.ny + j) * (d.nx + 1) + i;
-      long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
-      long long qz = ((long long)k * d.ny + j) * d.nx + i;
-      long long sxy = (long long)d.nx * d.ny;
-      R hy = __ldg(metric<R>(B).inv_hy + j);
-      bool wlo = C.bc[2] == kBcWall && j == 0, whi = C.bc[3] == kBcWall && j == d.ny - 1;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const R* fx = face_flux<R>(B, 0) + m * d.nf[0];
-        const R* fy = face_flux<R>(B, 1) + m * d.nf[1];
-        const R* fz = face_flux<R>(B, 2) + m * d.nf[2];
-        R ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
-        // staggered wall interface: no mass, x/z momentum or energy crosses it
-        if (m != 2) {
-          if (wlo) ylo = R(0);
-          if (whi) yhi = R(0);
-        }
-        res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
-                   (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * K.inv_dz);
-        if (m == 0 && sizeof(R) != sizeof(double)) {
-          // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
-          // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
-          // FP64 round-off as in the FP64 path
-          mass64 = -((to_f64(__ldg(fx + qx + 1)) - to_f64(__ldg(fx + qx))) * C.k64.inv_dx +
-                     (to_f64(yhi) - to_f64(ylo)) * __ldg(B.m64.inv_hy + j) +
-                     (to_f64(__ldg(fz + qz + sxy)) - to_f64(__ldg(fz + qz))) * C.k64.inv_dz);
-        }
-      }
-    }
+    if (C.convective) convective_residual<R>(d, C, B, i, j, k, res, mass64);
     if (C.viscous) {
       R V[5];
       viscous_node<L, R>(C, B, d, gidx(d, i, j, k), q, j, V);
 #pragma unroll
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }
-    if (rk.w) {
-      // the RK stage update of this node (body_rk_update without the forcing terms): the
-      // residual stays in registers instead of a round trip through memory
-      const double ad = B.scal[kScalAdt + rk.stage], bd = B.scal[kScalBdt + rk.stage];
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const long long e = m * d.N + q;
-        const double rr = (m == 0 && sizeof(R) != sizeof(double)) ? mass64 : to_f64(res[m]);
-        double wn = rk.w[e] + bd * rr;
-        if (rk.stage != 0) wn += ad * rk.r_old[e];  // alpha_0 = 0
-        rk.w[e] = wn;
-        rk.r_old[e] = rr;
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < 5; ++m) Rout[m * d.N + q] = to_f64(res[m]);
-      if (sizeof(R) != sizeof(double)) Rout[q] = mass64;
-    }
+    stage_or_store<R>(d, B, q, res, mass64, Rout, rk);
     if (C.forcing) fpart = to_f64(res[1]) * __ldg(B.vol + j);
   }
   if (C.forcing) {
