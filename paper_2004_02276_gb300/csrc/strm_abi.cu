@@ -269,6 +269,7 @@ void fill_coefs(Coefs<R>& K, const strm_phys& p, const strm_scheme& s, const str
   K.mu_ref = R(p.mu_ref);
   K.inv_tref = R(1.0 / p.t_ref);
   K.visc_exp = R(p.visc_exp);
+  K.exp_19_25 = p.visc_law == STRM_VISC_POWER && std::fabs(p.visc_exp - 0.76) < 1e-15 ? 1 : 0;
   K.suth_s = R(p.suth_s);
 }
 

@@ -140,3 +140,37 @@ def test_recip5_extreme_magnitudes():
         for y in extremes:
             y = np.array(y)
             np.testing.assert_allclose(_recip5_emulated(y), 1.0 / y, rtol=8e-16, atol=0.0)
+
+
+def test_pow_19_25_series_and_accuracy():
+    """The primitives kernel takes t^0.76 (t^(19/25), the power-law viscosity of the workloads) as an
+    FP32 seed y0 corrected by y = y0 (1 + d)^(1/25), d = t^19 / y0^25 - 1, with the binomial series
+    to third order. The coefficients are the series' own; emulated in numpy (FP32 seed, powers by
+    repeated squaring, reciprocal to 2^-43) the result is within 2 ulp of t**0.76 over the range
+    the kernel uses it in, [2^-6, 2^6], for seeds up to 1e-6 off."""
+    import numpy as np
+
+    d = sp.symbols("d")
+    series = sp.series((1 + d) ** sp.Rational(1, 25), d, 0, 4).removeO()
+    c1, c2, c3 = (series.coeff(d, n) for n in (1, 2, 3))
+    assert (c1, c2, c3) == (sp.Rational(1, 25), sp.Rational(-12, 625), sp.Rational(196, 15625))
+    rng = np.random.default_rng(1)
+    t = np.exp(rng.uniform(np.log(2.0 ** -6), np.log(2.0 ** 6), 100000))
+    ref = t ** 0.76
+    for pert in (-1e-6, 0.0, 1e-6):
+        seed32 = np.exp2(np.float32(0.76) * np.log2(t.astype(np.float32)))
+        y0 = (seed32.astype(np.float64) * (1 + pert)).astype(np.float32).astype(np.float64)
+        t2 = t * t
+        t4 = t2 * t2
+        t8 = t4 * t4
+        t16 = t8 * t8
+        t19 = (t16 * t2) * t
+        y2 = y0 * y0
+        y4 = y2 * y2
+        y8 = y4 * y4
+        y16 = y8 * y8
+        y25 = (y16 * y8) * y0
+        inv = (1.0 / y25) * (1 + rng.uniform(-2.0 ** -43, 2.0 ** -43, t.shape))
+        dl = (t19 - y25) * inv
+        y = y0 + (y0 * dl) * (float(c1) + dl * (float(c2) + float(c3) * dl))
+        assert np.all(np.abs(y - ref) <= 2 * np.spacing(ref)), pert
