@@ -205,10 +205,13 @@ def sbli_grid(nx, ny, nz, **kw):
 
 def bench_case(args):
     """The benchmark workload, or (for profiling captures only) the same workload on another
-    grid of the same spacing."""
+    grid of the same spacing, or the 256 x 192 x 128 channel (on another grid: the same domain)."""
+    channel = getattr(args, "workload", "sbli") == "channel"
     if not args.grid:
-        return CASE
+        return CHANNEL if channel else CASE
     nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    if channel:
+        return CHANNEL.replace(name=f"channel-{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz)
     return sbli_grid(nx, ny, nz)
 
 
@@ -677,6 +680,9 @@ def main():
                     help="steps after which the mixed path is compared with the FP64 path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (CPU baseline, errors)")
     ap.add_argument("--grid", default="", help="NXxNYxNZ of the same workload, for profiling captures only")
+    ap.add_argument("--workload", default="sbli", choices=["sbli", "channel"],
+                    help="the timed workload: the shock/boundary layer (benchmark) or, for profiling "
+                         "captures only, the channel")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     ap.add_argument("--no-variants", action="store_true", help="skip the channel and batched variants")
     ap.add_argument("--peaks-only", action="store_true",

@@ -77,3 +77,16 @@ def test_kernel_units_and_step_flops():
 
 def test_job_rate_counts_all_ranks():
     assert bench.job_rate(1000, 5, 2, 20.0) == 1000 * 3 * 5 * 2 / 0.02
+
+
+def test_channel_workload_for_captures():
+    class A:
+        grid = ""
+        workload = "channel"
+
+    assert bench.bench_case(A()) is bench.CHANNEL
+    A.grid = "192x144x96"
+    c = bench.bench_case(A())
+    assert (c.nx, c.ny, c.nz, c.kind) == (192, 144, 96, "channel") and c.name == "channel-192x144x96"
+    assert (c.lx, c.ly, c.lz, c.reynolds) == (bench.CHANNEL.lx, bench.CHANNEL.ly, bench.CHANNEL.lz,
+                                               bench.CHANNEL.reynolds)

@@ -157,3 +157,41 @@ def test_c4_full_size_steps():
     assert torch.isfinite(w).all()
     assert 0.0 < frac < 0.5
     s.close()
+
+
+# weak perturbations: 90 % of the y faces and 97 % of the z faces are central, so the y and z
+# central fluxes come from the sweeps (chosen from 85 % in FP64, 50 % in mixed precision)
+SWEEP = inputs.bl_case("sbli-64x40x24", 64, 40, 24, 12.0, 6.0, 3.0, shock=True, noise=0.001)
+
+
+def test_central_sweeps_match_oracle():
+    """The y/z central-flux sweeps (pair reuse along a column, every face written, the WENO
+    faces overwritten afterwards) in sensor mode: the right-hand side element-wise within 1e-12
+    of the oracle's, flags bit-equal, 10 CFL steps within relative L2 1e-12; the mixed right-hand
+    side within 1e-4 of each field's largest value."""
+    w0 = inputs.bl_state(SWEEP, seed=6)
+    cfg = O.make_cfg(SWEEP)
+    ref = O.rhs(cfg, w0)
+    _, _, fx_o, fy_o, fz_o = O.sensor(cfg, w0)
+    nf = [fx_o.size, fy_o.size, fz_o.size]
+    s = binding.Solver(SWEEP)
+    w = torch.from_numpy(w0).cuda()
+    r = s.compute_rhs(w).cpu().numpy()
+    counts = s.weno_counts()
+    _, _, fx, fy, fz = (t.cpu().numpy() for t in s.sensor(w))
+    assert all(1 - counts[dd] / nf[dd] >= 0.85 for dd in (1, 2)), counts  # the sweeps ran
+    assert np.array_equal(fx, fx_o) and np.array_equal(fy, fy_o) and np.array_equal(fz, fz_o)
+    err = rel_max(r, ref)
+    assert err.max() <= TOL, err
+    wo, to, _ = O.advance(cfg, w0, 10, cfl=SWEEP.cfl)
+    r_old = torch.zeros_like(w)
+    s.advance_n(w, r_old, 10, cfl=SWEEP.cfl)
+    t, _ = s.time()
+    wg = w.cpu().numpy()
+    s.close()
+    assert rel_l2(wg, wo).max() <= TOL
+    assert abs(t - to) <= 1e-13 * to
+    sm = binding.Solver(SWEEP.replace(precision="mixed"))
+    rm = sm.compute_rhs(torch.from_numpy(w0).cuda()).cpu().numpy()
+    sm.close()
+    assert rel_max(rm, ref).max() <= 1e-4
