@@ -224,11 +224,19 @@ def channel_state(case: Case, seed: int | None = None) -> np.ndarray:
     return out
 
 
-def bl_state(case: Case, seed: int | None = None) -> np.ndarray:
+def uniform_block(seed: int, start: int, count: int) -> np.ndarray:
+    """Outputs start .. start + count - 1 of the stream of ``uniform`` (flat C order)."""
+    z = splitmix64(seed, np.arange(start, start + count, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+def bl_state(case: Case, seed: int | None = None, planes_per_chunk: int = 16) -> np.ndarray:
     """Initial boundary layer: u/u_inf = (h/delta_in)^(1/7) below delta_in and 1 above,
     temperature from the Crocco-Busemann relation T = T_w + (T_r - T_w) u + (1 - T_r) u^2 with
     the recovery temperature T_r = 1 + r (gamma-1)/2 M^2, r = Pr^(1/3), uniform pressure, and
-    uniform velocity noise of amplitude ``case.noise`` inside the layer (SplitMix64 stream)."""
+    uniform velocity noise of amplitude ``case.noise`` inside the layer (SplitMix64 stream over
+    (component, k, j, i)). Built a few z planes at a time (the values do not depend on
+    ``planes_per_chunk``), so that large grids need little memory beyond the result."""
     seed = case.seed if seed is None else seed
     nz, ny, nx = case.nz, case.ny, case.nx
     yy = node_y(case)
@@ -236,16 +244,28 @@ def bl_state(case: Case, seed: int | None = None) -> np.ndarray:
     ub = np.minimum(np.maximum(h / case.delta_in, 0.0) ** (1.0 / 7.0), 1.0)
     tr = 1.0 + case.prandtl ** (1.0 / 3.0) * 0.5 * (case.gamma - 1.0) * case.mach ** 2
     T1 = case.t_wall + (tr - case.t_wall) * ub + (1.0 - tr) * ub * ub
-    r = uniform(seed, (3, nz, ny, nx))
-    inside = (h < case.delta_in)[None, :, None]
-    noise = case.noise * (2.0 * r - 1.0) * inside
-    u = ub[None, :, None] + noise[0]
-    v = noise[1]
-    w = noise[2]
-    T = np.broadcast_to(T1[None, :, None], (nz, ny, nx))
+    inside = (h < case.delta_in)[None, None, :, None]
+    T = T1[None, :, None]
     p = case.r_gas  # p_inf = rho_inf R T_inf
-    rho = p / (case.r_gas * T)
-    return primitive_state(case, rho, u, v, w, T)
+    rho_row = p / (case.r_gas * T)
+    cv = case.r_gas / (case.gamma - 1.0)
+    plane = ny * nx
+    out = np.empty((5, nz, ny, nx))
+    for k0 in range(0, nz, max(1, planes_per_chunk)):
+        k1 = min(nz, k0 + max(1, planes_per_chunk))
+        nk = k1 - k0
+        r = np.stack([uniform_block(seed, (c * nz + k0) * plane, nk * plane) for c in range(3)])
+        noise = case.noise * (2.0 * r.reshape(3, nk, ny, nx) - 1.0) * inside
+        u = ub[None, :, None] + noise[0]
+        v = noise[1]
+        w = noise[2]
+        rho = np.broadcast_to(rho_row, (nk, ny, nx))
+        out[0, k0:k1] = rho
+        out[1, k0:k1] = rho * u
+        out[2, k0:k1] = rho * v
+        out[3, k0:k1] = rho * w
+        out[4, k0:k1] = rho * (cv * T + 0.5 * (u * u + v * v + w * w))
+    return out
 
 
 def random_state(case: Case, seed: int, amp_u: float = 0.3, amp_rho: float = 0.2,

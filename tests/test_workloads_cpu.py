@@ -41,3 +41,19 @@ def test_ensemble_draws_in_range():
     # the same seed gives the same ensemble; another seed another one
     assert [c.nx for c in inputs.ensemble_cases(seed=0)] == [c.nx for c in cases]
     assert [c.nx for c in inputs.ensemble_cases(seed=1)] != [c.nx for c in cases]
+
+
+def test_bl_state_does_not_depend_on_its_chunking():
+    """The boundary-layer initial state is built a few z planes at a time (to keep the memory of
+    the 201 M-point workload low); the values are those of the whole-array recipe: the same
+    SplitMix64 outputs per (component, k, j, i) and the same arithmetic per element."""
+    import numpy as np
+
+    c = inputs.bl_case("bl-40x24x11", 40, 24, 11, 5.0, 6.0, 1.0, noise=0.05)
+    ref = inputs.bl_state(c, seed=4, planes_per_chunk=1000)
+    for ch in (1, 3, 11):
+        assert np.array_equal(inputs.bl_state(c, seed=4, planes_per_chunk=ch), ref)
+    # the noise field of component m at node (k, j, i) is output (m nz + k) ny nx + j nx + i
+    r = inputs.uniform(4, (3, c.nz, c.ny, c.nx))
+    blk = inputs.uniform_block(4, (2 * c.nz + 5) * c.ny * c.nx, c.ny * c.nx).reshape(c.ny, c.nx)
+    assert np.array_equal(blk, r[2, 5])
