@@ -76,6 +76,9 @@ PEAK_PROFILE = "profiles/fp64_fp32_fma_peak.md"
 # Algorithmic HBM bytes of one grid-point RK stage: read w and the residual register, write w
 # and the new residual (5 FP64 each), the minimum of a fused stage.
 STAGE_BYTES_PER_POINT = 160
+# DRAM bytes of all kernels per grid-point stage measured by ncu on a 1024 x 384 x 16 slice of
+# the workload (FP64; its 16 planes make the ghost fill weigh more than on the full grid)
+MEASURED_STEP_BYTES = 1528.5
 
 
 def peaks():
@@ -94,7 +97,11 @@ def hbm_step(value):
     gbs = STAGE_BYTES_PER_POINT * value / 1e9
     return {"bytes_per_point_stage": STAGE_BYTES_PER_POINT, "achieved_gbs": round(gbs, 1),
             "peak_gbs": pk, "frac": round(gbs / pk, 4) if pk else None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)",
+            "measured_bytes_per_point_stage": MEASURED_STEP_BYTES,
+            "measured_source": "ncu dram__bytes_read+write of every kernel of 21 right-hand sides on a "
+                               "1024x384x16 slice of the workload, per grid-point stage "
+                               "(profiles/dram-per-step_sbli-1024x384x16_fp64_mixed.md)"}
 
 
 class ClockSampler:
