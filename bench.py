@@ -77,8 +77,9 @@ PEAK_PROFILE = "profiles/fp64_fp32_fma_peak.md"
 # and the new residual (5 FP64 each), the minimum of a fused stage.
 STAGE_BYTES_PER_POINT = 160
 # DRAM bytes of all kernels per grid-point stage measured by ncu on a 1024 x 384 x 16 slice of
-# the workload (FP64; its 16 planes make the ghost fill weigh more than on the full grid)
+# the workload (its 16 planes make the ghost fill weigh more than on the full grid)
 MEASURED_STEP_BYTES = 1528.5
+MEASURED_STEP_BYTES_MIXED = 925.4
 
 
 def peaks():
@@ -89,16 +90,22 @@ def peaks():
         return {}
 
 
-def hbm_step(value):
+def hbm_step(value, copy_gbs=None, measured_bytes=MEASURED_STEP_BYTES):
     """The whole step against the HBM roofline: algorithmic bytes per grid-point stage times the
-    measured rate, over the measured copy bandwidth. The FP64 path is bound by the FP64 pipe,
-    so this fraction is small; it is reported for the metric's HBM roofline."""
+    measured rate, over the measured copy bandwidth (MEASURED_PEAKS.json when present, else the
+    copy rate measured in this run). The FP64 path is bound by the FP64 pipe, so this fraction
+    is small; it is reported for the metric's HBM roofline."""
     pk = peaks().get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
+    if not pk and copy_gbs:
+        pk, src = copy_gbs, "device-to-device copy of 2 GiB measured in this run (peaks.copy_gbs)"
     gbs = STAGE_BYTES_PER_POINT * value / 1e9
     return {"bytes_per_point_stage": STAGE_BYTES_PER_POINT, "achieved_gbs": round(gbs, 1),
             "peak_gbs": pk, "frac": round(gbs / pk, 4) if pk else None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)",
-            "measured_bytes_per_point_stage": MEASURED_STEP_BYTES,
+            "peak_source": src,
+            "measured_bytes_per_point_stage": measured_bytes,
+            "measured_gbs": round(measured_bytes * value / 1e9, 1),
+            "measured_frac": round(measured_bytes * value / 1e9 / pk, 4) if pk else None,
             "measured_source": "ncu dram__bytes_read+write of every kernel of 21 right-hand sides on a "
                                "1024x384x16 slice of the workload, per grid-point stage "
                                "(profiles/dram-per-step_sbli-1024x384x16_fp64_mixed.md)"}
@@ -234,7 +241,29 @@ def measure_peaks(local):
     return {"fp64_tflops": f64, "fp32_tflops": f32, "fp64_launch_ms": ms64, "fp32_launch_ms": ms32,
             "clocks": clk.summary(), "source": f"strm_peak_fma, measured in this run ({PEAK_PROFILE})",
             "fp64_from_units_tflops": round(FP64_UNITS_TFLOPS, 3),
-            "fp32_from_units_tflops": round(FP32_UNITS_TFLOPS, 2)}
+            "fp32_from_units_tflops": round(FP32_UNITS_TFLOPS, 2), "copy_gbs": copy_bandwidth(local)}
+
+
+def copy_bandwidth(local, nbytes=1 << 31, reps=6):
+    """Device-to-device copy rate of a 2 GiB buffer (bytes read + written per second, best of
+    the repeats): the HBM denominator when the measured-peaks file is absent."""
+    import torch
+
+    src = torch.empty(nbytes // 8, dtype=torch.float64, device=f"cuda:{local}").fill_(1.0)
+    dst = torch.empty_like(src)
+    st = torch.cuda.current_stream()
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        dst.copy_(src)
+        b.record(st)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    del src, dst
+    torch.cuda.empty_cache()
+    return round(2 * nbytes / (best * 1e-3) / 1e9, 1)
 
 
 # ------------------------------------------------------------------------------ the GPU path
@@ -354,6 +383,23 @@ def host_page_locked(t):
     return t
 
 
+def host_copy_rates(h, d):
+    """H2D and D2H rates (GB/s, CUDA events) of one copy of the page-locked host buffer h to and
+    from the device tensor d; d is restored from h afterwards."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, (dst, src) in (("d2h", (h, d)), ("h2d", (d, h))):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        dst.copy_(src, non_blocking=True)
+        b.record(st)
+        b.synchronize()
+        out[name] = round(h.numel() * h.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+    return out
+
+
 def field_errors(a, b):
     """Relative L2 difference per conserved field of two device states."""
     import torch
@@ -453,15 +499,25 @@ def run_ours(args, world, rank, local):
     wd = torch.empty_like(w)
     del r_old
     solver.advance_n_host(w_host, wd, w, 1)  # warm (graph for these buffers)
+    copy_gbs = host_copy_rates(w_host, wd)
     barrier(world)
     t0 = time.perf_counter()
+    calls = []
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         solver.advance_n_host(w_host, wd, w, 1)
+        calls.append(time.perf_counter() - t1)
     e2e_s = max_over_ranks(world, time.perf_counter() - t0)
     steps64 += args.steps + 1
+    wf = solver.weno_counts()
+    calls.sort()
     e2e = {"value": case.npts * 3 * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-           "host_buffer": "first-touched host memory page-locked with cudaHostRegister"}
+           "host_buffer": "first-touched host memory page-locked with cudaHostRegister",
+           "copy_gbs": copy_gbs,
+           "call_ms": {"min": round(calls[0] * 1e3, 1), "median": round(calls[len(calls) // 2] * 1e3, 1),
+                       "max": round(calls[-1] * 1e3, 1)},
+           "weno_face_fraction_last_rhs": round(sum(wf) / (3.0 * case.npts), 4)}
     ws_gb = solver.workspace.numel() / 1e9
 
     out = {
@@ -477,7 +533,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step_median": m64["ms_step_median"], "value_median": m64["value_median"],
         "timed_repeats": m64["repeats"],
         "roofline": m64["roofline"], "e2e": e2e, "gpu_launches": m64["launches"],
-        "clocks": m64["clocks"], "hbm_step": hbm_step(m64["value"]), "peaks": pk,
+        "clocks": m64["clocks"], "hbm_step": hbm_step(m64["value"], pk.get("copy_gbs")), "peaks": pk,
     }
     # the FP64 trajectory on to the error leg's step count
     wd.copy_(w_host)
@@ -509,6 +565,7 @@ def run_ours(args, world, rank, local):
             "ms_per_step_median": mm["ms_step_median"],
             "speedup_vs_fp64": mm["value"] / m64["value"], "dtype": "f32 flux / f64 state",
             "roofline": mm["roofline"], "gpu_launches": mm["launches"], "clocks": mm["clocks"],
+            "hbm_step": hbm_step(mm["value"], pk.get("copy_gbs"), MEASURED_STEP_BYTES_MIXED),
             "error": {
                 "vs": "the FP64 path on the same workload (itself within 1e-12 of the oracle)",
                 "steps": steps64, "rel_l2_per_field": err, "max": max(err),

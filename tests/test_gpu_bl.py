@@ -116,7 +116,14 @@ def test_c4_full_size_steps():
     column (i0, k0) is checked on a 24 x 384 x 24 block of the state around it, periodic in x and
     z, with the full wall-normal extent, metrics and wall: at its centre column the oracle's
     right-hand side equals the full grid's for every j at least 8 nodes below the top face
-    (whose shock ghosts depend on x)."""
+    (whose shock ghosts depend on x).
+
+    The top rows, with the shock entering through the top boundary, are checked on a second
+    block: the whole x extent and wall-normal extent with 24 planes around k0 = 128, periodic in
+    z only, so that the inflow, outflow and shock ghosts see their own x positions. Its plane
+    k0 equals the full grid's right-hand side at every node from i = 8 on (the recycled inflow
+    ghosts take spanwise means over the block's 24 planes instead of 256, which reaches the
+    first 6 nodes)."""
     case = inputs.C4
     w0 = inputs.bl_state(case, seed=0)
     s = binding.Solver(case)
@@ -136,6 +143,18 @@ def test_c4_full_size_steps():
         got = r[:, k0, :jmax, i0].cpu().numpy()
         err = rel_max(got, refs[i0, k0])
         assert err.max() <= TOL, ((i0, k0), err)
+    kp, i_min = 128, 8
+    plane = case.replace(name="c4-plane", nz=2 * h, lz=2 * h * dz)
+    blk = np.ascontiguousarray(w0[:, kp - h:kp + h])
+    ref_plane = O.rhs(O.make_cfg(plane), blk)[:, h, :, i_min:]
+    del blk
+    got = r[:, kp, :, i_min:].cpu().numpy()
+    err = rel_max(got, ref_plane)
+    print("C4 RHS error on the plane k = 128 (all j, i >= 8):", err)
+    assert err.max() <= TOL, err
+    # the rows next to the top boundary on their own (shock-top and characteristic ghosts)
+    err_top = rel_max(got[:, -8:], ref_plane[:, -8:])
+    assert err_top.max() <= TOL, err_top
     # the mixed-precision path at full size on the same columns: FP32 flux arithmetic, whose
     # rounding (~6e-8 of a flux) is amplified by the flux differences of the small wall-normal
     # and spanwise residuals (measured up to 1.2e-4 of the column's largest |R_rho v|)
@@ -146,6 +165,10 @@ def test_c4_full_size_steps():
         err = rel_max(rm[:, k0, :jmax, i0].cpu().numpy(), refs[i0, k0])
         print("C4 mixed-precision RHS error at column", (i0, k0), err)
         assert err.max() <= 1e-3, ((i0, k0), err)
+    err = rel_max(rm[:, kp, :, i_min:].cpu().numpy(), ref_plane)
+    print("C4 mixed-precision RHS error on the plane k = 128:", err)
+    assert err.max() <= 1e-3, err
+    del ref_plane
     sm.close()
     del rm
     r_old = torch.zeros_like(w)
