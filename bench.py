@@ -689,12 +689,32 @@ def run_batched(args, world, local, large_grid_value, precision="fp64"):
     ms = max_over_ranks(world, start.elapsed_time(stop))
     value = npts * 3 * args.steps * world / (ms / 1e3)
     tot = E.totals(ws)
+    # both schedules with the tuned launch shapes and pencil tile, a few steps each (untimed by
+    # the driver's contract; context for the tuner's choice)
+    schedules = {}
+    k = max(2, min(5, args.steps))
+    for name, persistent in (("per_kernel_type", 0), ("persistent_stage", 1)):
+        try:
+            E.set_schedule(**dict(choice, persistent=persistent))
+        except binding.StrmError as e:
+            schedules[name] = str(e)
+            continue
+        E.advance(ws, rs, 1, cfl=0.8)
+        torch.cuda.synchronize()
+        start.record(E.stream)
+        E.advance(ws, rs, k, cfl=0.8)
+        stop.record(E.stream)
+        torch.cuda.synchronize()
+        schedules[name] = round(npts * 3 * k / (start.elapsed_time(stop) / 1e3) / 1e6, 1)
+    schedules["unit"] = "M grid-pt RK-stage updates/s"
+    schedules["steps"] = k
     E.close()
     return {"value": value, "ms_per_step": ms / args.steps, "instances": len(cases),
             "points": npts, "dtype": "f64" if precision == "fp64" else "f32 flux / f64 state",
             "per_point_vs_large_grid": value / large_grid_value,
-            "tuned": {"weno_block": choice[0], "weno_blocks_per_sm": choice[1],
-                      "central_blocks_per_sm": choice[2]},
+            "tuned": choice, "schedules": schedules,
+            "schedule": "one cooperative launch per RK stage" if choice["persistent"] else
+                        "one launch per kernel type, one graph per step",
             "finite": bool(np.isfinite(np.array(tot)).all()), "clocks": clk.summary(),
             "workload": "64 channels, dims U{32..192}xU{32..128}xU{32..128}, M_b U[0.3,3], "
                         "Re_b U[2000,8000], seed 0"}

@@ -256,11 +256,13 @@ int strm_timing_read(strm_ctx* ctx, double* ms_host, long long* launches_host,
 int strm_launch_count(strm_ctx* ctx, long long* launches_host);
 
 /* ---- Batched ensemble: many independent grids advanced together (different sizes, gas and
- * flow parameters; the same central order L and precision). Each kernel of the right-hand side
- * and of the RK update runs as one launch over all instances, and one RK3 step of the whole
- * ensemble is a CUDA graph replayed per step. Every instance computes what a context of its own
- * would (same kernel bodies, same per-instance reduction order), up to where the compiler
- * contracts a multiply and an add into an FMA, which it decides per kernel. */
+ * flow parameters; the same central order L and precision). One RK3 step of the whole ensemble
+ * is a CUDA graph replayed per step, under one of two schedules: each kernel of the right-hand
+ * side and of the RK update as one launch over all instances, or (persistent) one cooperative
+ * launch per RK stage that runs every phase of the stage with grid-wide barriers between them.
+ * Every instance computes what a context of its own would (same kernel bodies), up to where the
+ * compiler contracts a multiply and an add into an FMA and, in the persistent schedule, the
+ * grouping of the CFL and forcing partial sums. */
 typedef struct strm_ensemble strm_ensemble;
 
 /* Device workspace for n instances (sum of the per-instance workspaces plus the instance
@@ -295,10 +297,20 @@ int strm_ensemble_advance(strm_ensemble* ens, double* const* w, double* const* r
                           double dt, double cfl);
 
 /* Autotuner: times one right-hand side of the ensemble (CUDA events, best of two) for the WENO
- * block size x blocks-per-SM candidates and then the central-list grid, keeps the fastest, and
- * writes {weno block, WENO blocks per SM, central blocks per SM} to choice_host (nullable). The
- * state is read, not modified. */
+ * block size {32, 64, 128} x blocks per SM {4, 8, 16}, then the central-list grid {8, 16, 32}
+ * blocks per SM, then the persistent schedule against the per-kernel one (not with a
+ * digital-filter inflow), then the pencil tile of the slab traversal order of the assembly and
+ * the z faces (slab height cap 32, 16, 8 or 0 = natural order); keeps the fastest and writes the
+ * schedule {weno block, WENO blocks per SM, central blocks per SM, persistent 0/1, slab cap} to
+ * choice_host[5] (nullable). The state is read, not modified. */
 int strm_ensemble_tune(strm_ensemble* ens, double* const* w, double* const* r_old, int* choice_host);
+
+/* Set the schedule the autotuner would choose: choice[5] as strm_ensemble_tune writes it.
+ * STRM_EINVAL for a value outside the tuner's ranges (blocks per SM 1..64), for the persistent
+ * schedule with a digital-filter inflow instance, or where the cooperative launch cannot run.
+ * Each instance takes the largest admitted slab height not above the cap (see the slab order of
+ * the assembly). Takes effect at the next strm_ensemble_advance. */
+int strm_ensemble_set_schedule(strm_ensemble* ens, const int* choice);
 
 /* Conserved totals of every instance, out_host[5*e + m]. Synchronises. */
 int strm_ensemble_totals(strm_ensemble* ens, double* const* w, double* out_host);
@@ -307,7 +319,9 @@ int strm_ensemble_totals(strm_ensemble* ens, double* const* w, double* out_host)
 int strm_ensemble_times(strm_ensemble* ens, double* t_host);
 
 /* The error words of all instances OR-ed together (bounds-checking build; see
- * strm_debug_flags). Synchronises. */
+ * strm_debug_flags), plus 32 (in every build) when a grid-wide barrier of the persistent stage
+ * gave up waiting (10 s); the blocks then left the kernel, the state is not valid, and every
+ * later persistent stage of this ensemble leaves at its first barrier. Synchronises. */
 int strm_ensemble_debug_flags(strm_ensemble* ens, unsigned* flags_host);
 
 void strm_ensemble_destroy(strm_ensemble* ens);

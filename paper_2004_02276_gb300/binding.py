@@ -106,6 +106,7 @@ SIGNATURES = {
     "strm_ensemble_set_inflow_df": ([_vp, _i, _P(DF), _P(_d), _vp, _sz], _i),
     "strm_ensemble_advance": ([_vp, _P(_vp), _P(_vp), _i, _d, _d], _i),
     "strm_ensemble_tune": ([_vp, _P(_vp), _P(_vp), _P(_i)], _i),
+    "strm_ensemble_set_schedule": ([_vp, _P(_i)], _i),
     "strm_ensemble_totals": ([_vp, _P(_vp), _P(_d)], _i),
     "strm_ensemble_times": ([_vp, _P(_d)], _i),
     "strm_ensemble_destroy": ([_vp], None),
@@ -506,11 +507,20 @@ class Ensemble:
         _check("strm_ensemble_debug_flags", lib().strm_ensemble_debug_flags(self.ens, ctypes.byref(out)))
         return out.value
 
+    SCHEDULE = ("weno_block", "weno_per_sm", "central_per_sm", "persistent", "slab_cap")
+
     def tune(self, ws, rs):
-        """Run the autotuner; returns (WENO block, WENO blocks per SM, central blocks per SM)."""
-        out = (ctypes.c_int * 3)()
+        """Run the autotuner; returns the chosen schedule as a dict (keys SCHEDULE): WENO block
+        size, WENO and central-list blocks per SM, persistent stage (1) or one launch per kernel
+        type (0), and the slab-height cap of the slab traversal order (0: natural order)."""
+        out = (ctypes.c_int * 5)()
         _check("strm_ensemble_tune", lib().strm_ensemble_tune(self.ens, self._ptrs(ws), self._ptrs(rs), out))
-        return tuple(out)
+        return dict(zip(self.SCHEDULE, list(out)))
+
+    def set_schedule(self, weno_block=128, weno_per_sm=8, central_per_sm=16, persistent=0, slab_cap=32):
+        """Set the schedule the autotuner would choose (see tune)."""
+        c = (ctypes.c_int * 5)(weno_block, weno_per_sm, central_per_sm, persistent, slab_cap)
+        _check("strm_ensemble_set_schedule", lib().strm_ensemble_set_schedule(self.ens, c))
 
     def totals(self, ws):
         out = (ctypes.c_double * (5 * len(self.cases)))()

@@ -82,6 +82,7 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
   d.nf[0] = (long long)(d.nx + 1) * d.ny * d.nz;
   d.nf[1] = (long long)d.nx * (d.ny + 1) * d.nz;
   d.nf[2] = (long long)d.nx * d.ny * (d.nz + 1);
+  d.slab_ty = slab_rows_for(d.nx, d.ny, 32);
   size_t off = 0;
   int n64 = L.mixed ? kN64Mixed : kN64All;
   for (int f = 0; f < n64; ++f) {

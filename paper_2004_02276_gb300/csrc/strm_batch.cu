@@ -14,52 +14,14 @@
 #include <vector>
 
 #include "../../include/strm.h"
-#include "strm_body.cuh"
+#include "strm_batch.h"
 #include "strm_launch.h"
 
 namespace strm {
 
-struct Inst {
-  Dims d;
-  Consts C;
-  Bufs B;
-  double* w;
-  double* r_old;
-};
-
-enum { kKindNode = 0, kKindGhost = 1, kKindFace = 2, kKindRow = 5, kKinds = 6 };  // faces: 2, 3, 4
-
-struct BatchIndex {
-  const Inst* inst;  // device table [n]
-  const int* start;  // device block starts [kKinds][n + 1]
-  int n;
-};
-
-__device__ __forceinline__ int find_inst(const int* start, int n, int b) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Instance of this block for kernel kind k, and the block index it plays within the instance.
 __device__ __forceinline__ const Inst& block_inst(const BatchIndex& X, int kind, int& blk) {
-  const int* st = X.start + kind * (X.n + 1);
-  int e = find_inst(st, X.n, blockIdx.x);
-  blk = blockIdx.x - __ldg(st + e);
-  return X.inst[e];
-}
-
-__device__ __forceinline__ int inst_blocks(const BatchIndex& X, int kind, int e) {
-  const int* st = X.start + kind * (X.n + 1);
-  return st[e + 1] - st[e];
-}
-
-__device__ __forceinline__ long long ghost_count(const Dims& d) {
-  return 2LL * G * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+  return inst_of_block(X, kind, blockIdx.x, blk);
 }
 
 __global__ void kb_zero_counts(BatchIndex X) {
@@ -202,7 +164,14 @@ struct Tuning {
   int weno_block = 128;
   int weno_per_sm = 8;
   int central_per_sm = 16;
+  int persistent = 0;  // 1: one cooperative launch per RK stage (strm_persist.cu)
+  int slab_cap = 32;   // largest slab height of the slab traversal order (0: natural order)
 };
+
+// A barrier of the persistent stage gave up (error word bit; the context bits are kDbg*).
+constexpr unsigned kEnsembleBarrier = 32u;
+// Time after which a barrier of the persistent stage gives up.
+constexpr unsigned long long kBarrierLimitNs = 10000000000ull;
 
 }  // namespace
 
@@ -220,6 +189,8 @@ struct strm_ensemble {
   int total_blocks[kKinds] = {};
   Inst* inst_dev = nullptr;
   int* start_dev = nullptr;
+  unsigned* bar_dev = nullptr;  // persistent-stage barrier [3] (zeroed at creation)
+  int stage_grid = 0;           // blocks of the persistent stage launch (0: not available)
   Tuning tune;
   // graph of one RK step of the ensemble
   cudaStream_t cap = nullptr;
@@ -238,6 +209,18 @@ namespace {
   } while (0)
 
 BatchIndex index_of(const strm_ensemble* E) { return BatchIndex{E->inst_dev, E->start_dev, E->n}; }
+
+StageArgs stage_args(const strm_ensemble* E, int stage, double cfl, double dt_fixed) {
+  StageArgs A = {};
+  A.bar = E->bar_dev;
+  A.limit_ns = kBarrierLimitNs;
+  A.cfl = cfl;
+  A.dt_fixed = dt_fixed;
+  A.stage = stage;
+  A.any_recycle = E->any_recycle ? 1 : 0;
+  for (int k = 0; k < kKinds; ++k) A.total[k] = E->total_blocks[k];
+  return A;
+}
 
 // One right-hand side of every instance into its workspace residual (and, with dt_mode, the
 // per-instance step of stage 0).
@@ -279,6 +262,10 @@ void enqueue_rhs_t(const strm_ensemble* E, bool dt_mode, double cfl, double dt_f
 }
 
 void enqueue_rhs(const strm_ensemble* E, bool dt_mode, double cfl, double dt_fixed, cudaStream_t st) {
+  if (E->tune.persistent && !dt_mode) {  // the tuner's right-hand side: no dt, no update
+    launch_persistent_stage(E->L, E->mixed, index_of(E), stage_args(E, -1, cfl, dt_fixed), E->stage_grid, st);
+    return;
+  }
   if (E->L == 3) {
     if (E->mixed) enqueue_rhs_t<3, true>(E, dt_mode, cfl, dt_fixed, st);
     else enqueue_rhs_t<3, false>(E, dt_mode, cfl, dt_fixed, st);
@@ -290,6 +277,13 @@ void enqueue_rhs(const strm_ensemble* E, bool dt_mode, double cfl, double dt_fix
 
 int enqueue_step(const strm_ensemble* E, double dt, double cfl, cudaStream_t st) {
   BatchIndex X = index_of(E);
+  if (E->tune.persistent) {
+    for (int stage = 0; stage < 3; ++stage) {
+      cudaError_t e = launch_persistent_stage(E->L, E->mixed, X, stage_args(E, stage, cfl, dt), E->stage_grid, st);
+      if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("persistent stage launch: ") + cudaGetErrorString(e));
+    }
+    return STRM_OK;
+  }
   for (int stage = 0; stage < 3; ++stage) {
     enqueue_rhs(E, stage == 0, cfl, dt, st);
     kb_rk_update<<<E->total_blocks[kKindNode], 256, 0, st>>>(X, stage);
@@ -343,7 +337,60 @@ void refresh_instance(strm_ensemble* E, int e) {
   }
 }
 
-size_t table_bytes(int n) { return align256(sizeof(Inst) * (size_t)n) + align256(sizeof(int) * kKinds * (n + 1)); }
+size_t table_bytes(int n) {
+  return align256(sizeof(Inst) * (size_t)n) + align256(sizeof(int) * kKinds * (n + 1)) + 256;
+}
+
+bool any_df(const strm_ensemble* E) {
+  DFParams F;
+  for (strm_ctx* c : E->ctx)
+    if (ctx_df(c, &F)) return true;
+  return false;
+}
+
+// Re-upload the instance table (after a change of the instances' slab heights).
+int upload_table(strm_ensemble* E) {
+  STRME_CK(cudaMemcpyAsync(E->inst_dev, E->inst_host.data(), sizeof(Inst) * E->n, cudaMemcpyHostToDevice,
+                           E->stream));
+  STRME_CK(cudaStreamSynchronize(E->stream));
+  return STRM_OK;
+}
+
+// Slab height of every instance: the largest admitted one not above cap (0: natural order).
+void apply_slab_cap(strm_ensemble* E, int cap) {
+  for (Inst& I : E->inst_host) I.d.slab_ty = slab_rows_for(I.d.nx, I.d.ny, cap);
+  E->tune.slab_cap = cap;
+}
+
+// Validate and apply a schedule choice {weno block, WENO blocks per SM, central blocks per SM,
+// persistent, slab cap}; the table and the step graph are refreshed at the next advance.
+int set_schedule(strm_ensemble* E, const int* c) {
+  const bool blk_ok = c[0] == 32 || c[0] == 64 || c[0] == 128;
+  if (!blk_ok || c[1] < 1 || c[1] > 64 || c[2] < 1 || c[2] > 64 || (c[3] != 0 && c[3] != 1) ||
+      !(c[4] == 0 || c[4] == 8 || c[4] == 16 || c[4] == 32))
+    return record_error(STRM_EINVAL, "schedule out of range");
+  if (c[3] && E->stage_grid <= 0) return record_error(STRM_EINVAL, "the persistent stage cannot run on this device");
+  if (c[3] && any_df(E)) return record_error(STRM_EINVAL, "the persistent stage does not take digital-filter inflows");
+  E->tune.weno_block = c[0];
+  E->tune.weno_per_sm = c[1];
+  E->tune.central_per_sm = c[2];
+  E->tune.persistent = c[3];
+  apply_slab_cap(E, c[4]);
+  E->dirty = true;
+  if (E->gexec) {
+    cudaGraphExecDestroy(E->gexec);
+    E->gexec = nullptr;
+  }
+  return STRM_OK;
+}
+
+void get_schedule(const strm_ensemble* E, int* c) {
+  c[0] = E->tune.weno_block;
+  c[1] = E->tune.weno_per_sm;
+  c[2] = E->tune.central_per_sm;
+  c[3] = E->tune.persistent;
+  c[4] = E->tune.slab_cap;
+}
 
 }  // namespace
 
@@ -402,6 +449,8 @@ int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, con
   }
   E->inst_dev = (Inst*)(ws + off);
   E->start_dev = (int*)(ws + off + align256(sizeof(Inst) * (size_t)n));
+  E->bar_dev = (unsigned*)(ws + off + align256(sizeof(Inst) * (size_t)n) + align256(sizeof(int) * kKinds * (n + 1)));
+  E->stage_grid = persistent_blocks_per_sm(E->L, E->mixed) * E->sms;
   E->start_host.assign(kKinds * (n + 1), 0);
   for (int k = 0; k < kKinds; ++k) {
     int acc = 0;
@@ -421,6 +470,7 @@ int strm_ensemble_create(strm_ensemble** out, int n, const strm_grid* grids, con
   }
   cudaError_t ce = cudaMemcpyAsync(E->start_dev, E->start_host.data(), sizeof(int) * E->start_host.size(),
                                    cudaMemcpyHostToDevice, E->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(E->bar_dev, 0, 3 * sizeof(unsigned), E->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(E->stream);
   if (ce != cudaSuccess) {
     strm_ensemble_destroy(E);
@@ -447,6 +497,10 @@ int strm_ensemble_debug_flags(strm_ensemble* E, unsigned* flags_host) {
     if (rc) return rc;
     acc |= f;
   }
+  unsigned gave_up = 0;
+  STRME_CK(cudaMemcpyAsync(&gave_up, E->bar_dev + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, E->stream));
+  STRME_CK(cudaStreamSynchronize(E->stream));
+  if (gave_up) acc |= kEnsembleBarrier;
   *flags_host = acc;
   return STRM_OK;
 }
@@ -502,6 +556,11 @@ int strm_ensemble_advance(strm_ensemble* E, double* const* w, double* const* r_o
   return STRM_OK;
 }
 
+int strm_ensemble_set_schedule(strm_ensemble* E, const int* choice) {
+  if (!E || !choice) return record_error(STRM_EINVAL, "null ensemble or schedule");
+  return set_schedule(E, choice);
+}
+
 int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old, int* choice_host) {
   if (!E || !w || !r_old) return record_error(STRM_EINVAL, "null ensemble or state table");
   int rc = bind_states(E, w, r_old);
@@ -516,6 +575,7 @@ int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old,
       enqueue_rhs(E, false, 0.0, 0.0, E->stream);
       cudaEventRecord(b, E->stream);
       cudaError_t e = cudaEventSynchronize(b);
+      if (e == cudaSuccess) e = cudaGetLastError();
       if (e != cudaSuccess) return record_error(STRM_ECUDA, std::string("tune: ") + cudaGetErrorString(e));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, a, b);
@@ -524,7 +584,9 @@ int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old,
     *best_ms = best;
     return STRM_OK;
   };
-  // WENO launch shape first (the dominant kernel), then the central list grid
+  // 1. launch shapes of the per-kernel-type schedule: WENO (the dominant kernel), then the
+  //    central-list grid
+  E->tune.persistent = 0;
   Tuning bestT = E->tune;
   float best = 1e30f;
   const int blocks[3] = {32, 64, 128}, per_sm[3] = {4, 8, 16};  // kb_weno takes <= 128 threads
@@ -551,17 +613,40 @@ int strm_ensemble_tune(strm_ensemble* E, double* const* w, double* const* r_old,
     }
   }
   E->tune = bestT;
+  // 2. schedule: the persistent stage (one cooperative launch) against the per-kernel launches
+  if (rc == STRM_OK && E->stage_grid > 0 && !any_df(E)) {
+    E->tune.persistent = 1;
+    float ms;
+    // a launch the device refuses (a configuration error, which does not persist) leaves the
+    // persistent schedule out of the choice
+    if (time_rhs(&ms) == STRM_OK && ms < best) {
+      best = ms;
+      bestT = E->tune;
+    }
+    E->tune = bestT;
+  }
+  // 3. pencil tile of the slab traversal (assembly and z faces): slab height cap
+  const int caps[4] = {32, 16, 8, 0};
+  for (int ci = 0; ci < 4 && rc == STRM_OK; ++ci) {
+    apply_slab_cap(E, caps[ci]);
+    rc = upload_table(E);
+    float ms;
+    if (rc == STRM_OK) rc = time_rhs(&ms);
+    if (rc == STRM_OK && ms < best) {
+      best = ms;
+      bestT = E->tune;
+    }
+  }
+  E->tune = bestT;
+  apply_slab_cap(E, bestT.slab_cap);
+  if (rc == STRM_OK) rc = upload_table(E);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (E->gexec) {  // the captured graph holds the old launch shapes
     cudaGraphExecDestroy(E->gexec);
     E->gexec = nullptr;
   }
-  if (choice_host) {
-    choice_host[0] = E->tune.weno_block;
-    choice_host[1] = E->tune.weno_per_sm;
-    choice_host[2] = E->tune.central_per_sm;
-  }
+  if (choice_host) get_schedule(E, choice_host);
   return rc;
 }
 

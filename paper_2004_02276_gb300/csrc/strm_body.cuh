@@ -21,7 +21,7 @@ __device__ __forceinline__ void node_ijk(const Dims& d, long long q, int& i, int
 // (Section 2: E = cv T + |u|^2/2, p = rho R T, H = E + p/rho), plus c, mu(T) and sqrt(rho).
 // With want_cfl, each block also writes the largest sum_d (|u_d| + c)/h_d of its nodes.
 __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const Bufs& B,
-                                           const double* __restrict__ w, int want_cfl, int blk,
+                                           const double* STRM_RO w, int want_cfl, int blk,
                                            double* sh) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   double spec = 0.0;
@@ -75,7 +75,7 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
 // kernels, with c and mu(T) evaluated in FP32. The CFL partial is formed in FP32 (the FP64 pipe
 // binds this kernel; the step needs no FP64 accuracy in this precision).
 __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C, const Bufs& B,
-                                                 const double* __restrict__ w, int want_cfl, int blk,
+                                                 const double* STRM_RO w, int want_cfl, int blk,
                                                  double* sh) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   float spec = 0.f;
@@ -367,13 +367,13 @@ __device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C,
                                                  int j, int k) {
   const Nodes<double>& P = B.n64;
   double s = B.scal[kScalRecycle];
-  double ht = s * __ldg(B.hy + j);
+  double ht = s * STRM_LDG(B.hy + j);
   int is = C.i_recycle - layer;
   // first node jb with h[jb] >= ht
   int lo = 0, hi = d.ny;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
-    if (__ldg(B.hy + mid) < ht) lo = mid + 1;
+    if (STRM_LDG(B.hy + mid) < ht) lo = mid + 1;
     else hi = mid;
   }
   int jb = lo;
@@ -385,13 +385,13 @@ __device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C,
     alpha = 1.0;
   } else {
     bb = load_pstate(P, gidx(d, is, jb, k));
-    double ha, hb = __ldg(B.hy + jb);
+    double ha, hb = STRM_LDG(B.hy + jb);
     if (jb == 0) {
       a = PState{0.0, 0.0, 0.0, 0.0, bb.p, C.t_wall};
       ha = 0.0;
     } else {
       a = load_pstate(P, gidx(d, is, jb - 1, k));
-      ha = __ldg(B.hy + jb - 1);
+      ha = STRM_LDG(B.hy + jb - 1);
     }
     alpha = (ht - ha) / (hb - ha);
   }
@@ -414,11 +414,11 @@ __device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C,
 __device__ __forceinline__ PState df_pstate(const Dims& d, const Consts& C, const Bufs& B, int j, int k) {
   const double* P = B.df_prof;
   const int ny = d.ny;
-  double U = __ldg(P + j), V = __ldg(P + ny + j), Tm = __ldg(P + 2 * ny + j);
-  double a11 = __ldg(P + 3 * ny + j), a21 = __ldg(P + 4 * ny + j), a22 = __ldg(P + 5 * ny + j),
-         a33 = __ldg(P + 6 * ny + j);
+  double U = STRM_LDG(P + j), V = STRM_LDG(P + ny + j), Tm = STRM_LDG(P + 2 * ny + j);
+  double a11 = STRM_LDG(P + 3 * ny + j), a21 = STRM_LDG(P + 4 * ny + j), a22 = STRM_LDG(P + 5 * ny + j),
+         a33 = STRM_LDG(P + 6 * ny + j);
   long long plane = (long long)d.nz * ny, at = (long long)k * ny + j;
-  double p0 = __ldg(B.df_psi + at), p1 = __ldg(B.df_psi + plane + at), p2 = __ldg(B.df_psi + 2 * plane + at);
+  double p0 = STRM_LDG(B.df_psi + at), p1 = STRM_LDG(B.df_psi + plane + at), p2 = STRM_LDG(B.df_psi + 2 * plane + at);
   double up = a11 * p0, vp = fma(a21, p0, a22 * p1), wp = a33 * p2;
   PState g;
   g.u = U + up;
@@ -683,7 +683,7 @@ __device__ __forceinline__ void body_force_finalize(const Bufs& B, int nparts, d
 // R_rhou += f, R_rhoE += f u (Eqs. 1b, 1c); R_old <- R. One thread per node, five fields. FP64
 // in both precisions.
 __device__ __forceinline__ void body_rk_update(const Dims& d, const Consts& C, const Bufs& B,
-                                               double* __restrict__ w, double* __restrict__ r_old,
+                                               double* STRM_RO w, double* STRM_RO r_old,
                                                int stage, int blk) {
   long long q = (long long)blk * blockDim.x + threadIdx.x;
   if (q >= d.N) return;
@@ -748,21 +748,21 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
   const Nodes<R>& P = nodes<R>(B);
   const R* aq = coefs<R>(C).aq;  // a_l / 4
   const R* apc = coefs<R>(C).ap;  // a_{r+1} + .. + a_L
-  const R* __restrict__ ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
+  const R* STRM_RO ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.w);
   R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0), a4 = R(0), ap = R(0);
 #pragma unroll
-  for (int r = 0; r < L; ++r) ap = fma(apc[r], __ldg(P.p + n - r * st) + __ldg(P.p + n + (r + 1) * st), ap);
+  for (int r = 0; r < L; ++r) ap = fma(apc[r], STRM_LDG(P.p + n - r * st) + STRM_LDG(P.p + n + (r + 1) * st), ap);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
 #pragma unroll
     for (int m = 0; m < l; ++m) {
       long long ia = n - m * st, ib = n + (l - m) * st;
-      R q = (aq[l] * (__ldg(P.rho + ia) + __ldg(P.rho + ib))) * (__ldg(ud + ia) + __ldg(ud + ib));
+      R q = (aq[l] * (STRM_LDG(P.rho + ia) + STRM_LDG(P.rho + ib))) * (STRM_LDG(ud + ia) + STRM_LDG(ud + ib));
       a0 += q;
-      a1 = fma(q, __ldg(P.u + ia) + __ldg(P.u + ib), a1);
-      a2 = fma(q, __ldg(P.v + ia) + __ldg(P.v + ib), a2);
-      a3 = fma(q, __ldg(P.w + ia) + __ldg(P.w + ib), a3);
-      a4 = fma(q, __ldg(P.H + ia) + __ldg(P.H + ib), a4);
+      a1 = fma(q, STRM_LDG(P.u + ia) + STRM_LDG(P.u + ib), a1);
+      a2 = fma(q, STRM_LDG(P.v + ia) + STRM_LDG(P.v + ib), a2);
+      a3 = fma(q, STRM_LDG(P.w + ia) + STRM_LDG(P.w + ib), a3);
+      a4 = fma(q, STRM_LDG(P.H + ia) + STRM_LDG(P.H + ib), a4);
     }
   }
   f[0] = R(2) * a0;
@@ -883,16 +883,16 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
   constexpr int T1 = DIR == 0 ? 1 : 0;
   constexpr int T2 = DIR == 2 ? 1 : 2;
   const Nodes<double>& P = B.n64;
-  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
-  const double* __restrict__ un_p = vel[DIR];
+  const double* STRM_RO vel[3] = {P.u, P.v, P.w};
+  const double* STRM_RO un_p = vel[DIR];
   // Roe average of nodes n and n + st
-  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
+  double sl = STRM_LDG(P.srho + n), sr = STRM_LDG(P.srho + n + st);
   double inv = 1.0 / (sl + sr);
   double wl = sl * inv, wr = sr * inv;
   double ua[3];
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
-  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
+  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * STRM_LDG(vel[dd] + n) + wr * STRM_LDG(vel[dd] + n + st);
+  double Ha = wl * STRM_LDG(P.H + n) + wr * STRM_LDG(P.H + n + st);
   double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
   double c2a = C.gm1 * (Ha - 0.5 * q2);
   double ic = rsqrt(c2a);
@@ -903,14 +903,14 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 
   // local Lax-Friedrichs speeds over the stencil nodes n-2 .. n+3
   AbsMax m0, m1, m4;
-  const double* __restrict__ lm = B.lam[2 * DIR];      // u_n - c at the nodes
-  const double* __restrict__ lp = B.lam[2 * DIR + 1];  // u_n + c
+  const double* STRM_RO lm = B.lam[2 * DIR];      // u_n - c at the nodes
+  const double* STRM_RO lp = B.lam[2 * DIR + 1];  // u_n + c
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    m0.add(__ldg(lm + nn));
-    m1.add(__ldg(un_p + nn));
-    m4.add(__ldg(lp + nn));
+    m0.add(STRM_LDG(lm + nn));
+    m1.add(STRM_LDG(un_p + nn));
+    m4.add(STRM_LDG(lp + nn));
   }
   const double lam0 = m0.value(), lam1 = m1.value(), lam4 = m4.value();
 
@@ -919,10 +919,10 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    double rho = __ldg(P.rho + nn);
-    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
-    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
+    double rho = STRM_LDG(P.rho + nn);
+    double uu[3] = {STRM_LDG(P.u + nn), STRM_LDG(P.v + nn), STRM_LDG(P.w + nn)};
+    double H = STRM_LDG(P.H + nn), p = STRM_LDG(P.p + nn);
+    double run = STRM_LDG(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;
@@ -930,7 +930,7 @@ __device__ __forceinline__ void weno_flux(const Consts& C, const Bufs& B, long l
     double Af = fma(run, K, -b1p * un_a);
     // c B rows: rho (ua_n - u_n) and rho u_n (ua_n - u_n) - p = rho u_n ua_n - (rho u_n^2 + p)
     double cBw = fma(rho, un_a, -run);
-    double cBf = fma(run, un_a, -__ldg(B.mflux[DIR] + nn));
+    double cBf = fma(run, un_a, -STRM_LDG(B.mflux[DIR] + nn));
     double Sw = fma(ic, cBw, Aw), Sf = fma(ic, cBf, Af), Dw = fma(-ic, cBw, Aw), Df = fma(-ic, cBf, Af);
     gp[0][q] = fma(lam0, Sw, Sf);
     gm[0][q] = fma(-lam0, Sw, Sf);
@@ -1006,16 +1006,16 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
   constexpr int T2 = DIR == 2 ? 1 : 2;
   const Nodes<double>& P = B.n64;
   const Nodes<float>& F = B.n32;
-  const double* __restrict__ vel[3] = {P.u, P.v, P.w};
-  const float* __restrict__ velf[3] = {F.u, F.v, F.w};
+  const double* STRM_RO vel[3] = {P.u, P.v, P.w};
+  const float* STRM_RO velf[3] = {F.u, F.v, F.w};
   // FP64 Roe average of nodes n and n + st and the eigen-scalars
-  double sl = __ldg(P.srho + n), sr = __ldg(P.srho + n + st);
+  double sl = STRM_LDG(P.srho + n), sr = STRM_LDG(P.srho + n + st);
   double inv = rcp_nr(sl + sr);
   double wl = sl * inv, wr = sr * inv;
   double ua[3];
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * __ldg(vel[dd] + n) + wr * __ldg(vel[dd] + n + st);
-  double Ha = wl * __ldg(P.H + n) + wr * __ldg(P.H + n + st);
+  for (int dd = 0; dd < 3; ++dd) ua[dd] = wl * STRM_LDG(vel[dd] + n) + wr * STRM_LDG(vel[dd] + n + st);
+  double Ha = wl * STRM_LDG(P.H + n) + wr * STRM_LDG(P.H + n + st);
   double q2 = ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
   double c2a = C.gm1 * (Ha - 0.5 * q2);
   double ic = rsqrt_nr(c2a);
@@ -1028,7 +1028,7 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    float un = __ldg(velf[DIR] + nn), cs = __ldg(F.c + nn);
+    float un = STRM_LDG(velf[DIR] + nn), cs = STRM_LDG(F.c + nn);
     lam0 = fmaxf(lam0, fabsf(un - cs));
     lam1 = fmaxf(lam1, fabsf(un));
     lam4 = fmaxf(lam4, fabsf(un + cs));
@@ -1037,20 +1037,20 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     long long nn = n + (q - 2) * st;
-    double rho = __ldg(P.rho + nn);
-    double uu[3] = {__ldg(P.u + nn), __ldg(P.v + nn), __ldg(P.w + nn)};
-    double H = __ldg(P.H + nn), p = __ldg(P.p + nn);
-    double run = __ldg(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
+    double rho = STRM_LDG(P.rho + nn);
+    double uu[3] = {STRM_LDG(P.u + nn), STRM_LDG(P.v + nn), STRM_LDG(P.w + nn)};
+    double H = STRM_LDG(P.H + nn), p = STRM_LDG(P.p + nn);
+    double run = STRM_LDG(B.mom[DIR] + nn);  // rho u_n, the conserved momentum
     double hu = fma(-ua[2], uu[2], fma(-ua[1], uu[1], fma(-ua[0], uu[0], H)));  // H - ua.u
     double K = fma(b1, hu, b2);
     double b1p = b1 * p;
     double Aw = fma(rho, K, -b1p);
     double Af = fma(run, K, -b1p * un_a);
-    double cBw = fma(rho, un_a, -run), cBf = fma(run, un_a, -__ldg(B.mflux[DIR] + nn));
+    double cBw = fma(rho, un_a, -run), cBf = fma(run, un_a, -STRM_LDG(B.mflux[DIR] + nn));
     float Sw = d2f(fma(ic, cBw, Aw)), Sf = d2f(fma(ic, cBf, Af)), Dw = d2f(fma(-ic, cBw, Aw)),
           Df = d2f(fma(-ic, cBf, Af));
     float Awf = d2f(Aw), Aff = d2f(Af);
-    float rhof = __ldg(F.rho + nn), unf = __ldg(velf[DIR] + nn);
+    float rhof = STRM_LDG(F.rho + nn), unf = STRM_LDG(velf[DIR] + nn);
     float runf = rhof * unf;
     gp[0][q] = fmaf(lam0, Sw, Sf);
     gm[0][q] = fmaf(-lam0, Sw, Sf);
@@ -1059,7 +1059,7 @@ __device__ __forceinline__ void weno_flux_mixed(const Consts& C, const Bufs& B, 
     float r1 = fmaf(lam1, rhof, runf), r2 = fmaf(-lam1, rhof, runf);
     gp[1][q] = r1 - fmaf(lam1, Awf, Aff);
     gm[1][q] = r2 - fmaf(-lam1, Awf, Aff);
-    float d1 = __ldg(velf[T1] + nn) - uaf[T1], d2 = __ldg(velf[T2] + nn) - uaf[T2];
+    float d1 = STRM_LDG(velf[T1] + nn) - uaf[T1], d2 = STRM_LDG(velf[T2] + nn) - uaf[T2];
     gp[2][q] = d1 * r1;
     gm[2][q] = d1 * r2;
     gp[3][q] = d2 * r1;
@@ -1195,7 +1195,7 @@ __device__ __forceinline__ void body_central_sweep(const Dims& d, const Consts& 
   }
   const Nodes<R>& P = nodes<R>(B);
   const Coefs<R>& K = coefs<R>(C);
-  const R* __restrict__ ud = DIR == 1 ? P.v : P.w;
+  const R* STRM_RO ud = DIR == 1 ? P.v : P.w;
   const long long st = dir_stride(d, DIR);
   // node (i, j, k) with the sweep coordinate at -0; n(s) = base + s * st
   const long long base = DIR == 1 ? gidx(d, i, 0, c) : gidx(d, i, c, 0);
@@ -1208,16 +1208,16 @@ __device__ __forceinline__ void body_central_sweep(const Dims& d, const Consts& 
 #pragma unroll
   for (int m = 0; m <= L; ++m) {
     const long long n = base + (long long)(sb - 1 + m) * st;
-    wr[m] = __ldg(P.rho + n);
-    wu[m] = __ldg(P.u + n);
-    wv[m] = __ldg(P.v + n);
-    ww[m] = __ldg(P.w + n);
-    wh[m] = __ldg(P.H + n);
+    wr[m] = STRM_LDG(P.rho + n);
+    wu[m] = STRM_LDG(P.u + n);
+    wv[m] = STRM_LDG(P.v + n);
+    ww[m] = STRM_LDG(P.w + n);
+    wh[m] = STRM_LDG(P.H + n);
   }
 #pragma unroll
   for (int m = 0; m < 2 * L; ++m) {
     const int sn = sb - L + m;  // node index along the sweep; below -G it is never used
-    pw[m] = sn >= -G ? __ldg(P.p + base + (long long)sn * st) : R(0);
+    pw[m] = sn >= -G ? STRM_LDG(P.p + base + (long long)sn * st) : R(0);
   }
   // pair history: hq[l][g] (and hu, hv, hw, hh) holds the terms of the pair of length l that
   // starts at node s-2-g (g = 0 .. l-2: the l-1 generations before this face); filled by the
@@ -1301,12 +1301,12 @@ __device__ __forceinline__ void body_central_sweep(const Dims& d, const Consts& 
 #pragma unroll
       for (int m = 0; m < 2 * L - 1; ++m) pw[m] = pw[m + 1];
       const long long n = base + (long long)(s + L) * st;  // node s + L: window of face s + 1
-      wr[L] = __ldg(P.rho + n);
-      wu[L] = __ldg(P.u + n);
-      wv[L] = __ldg(P.v + n);
-      ww[L] = __ldg(P.w + n);
-      wh[L] = __ldg(P.H + n);
-      pw[2 * L - 1] = __ldg(P.p + base + (long long)(s + L) * st);
+      wr[L] = STRM_LDG(P.rho + n);
+      wu[L] = STRM_LDG(P.u + n);
+      wv[L] = STRM_LDG(P.v + n);
+      ww[L] = STRM_LDG(P.w + n);
+      wh[L] = STRM_LDG(P.H + n);
+      pw[2 * L - 1] = STRM_LDG(P.p + base + (long long)(s + L) * st);
     }
   }
 }
@@ -1386,19 +1386,19 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
   const Coefs<R>& K = coefs<R>(C);
   const Metric<R>& M = metric<R>(B);
   const long long sy = d.px, sz = d.plane;
-  const R hy = __ldg(M.inv_hy + j), c2 = __ldg(M.c2y + j), c1 = __ldg(M.c1y + j);
-  const R* __restrict__ fld[4] = {P.u, P.v, P.w, P.T};
+  const R hy = STRM_LDG(M.inv_hy + j), c2 = STRM_LDG(M.c2y + j), c1 = STRM_LDG(M.c1y + j);
+  const R* STRM_RO fld[4] = {P.u, P.v, P.w, P.T};
   R du[3][3], lap[3], dT[3], lapT = R(0);
   if constexpr (std::is_same<R, double>::value) {
     // FP64: first derivatives of the velocity from the sensor; second derivatives here, with
     // the eta-derivative of the stretched-y term taken back from d_y u (f_eta / y_eta^2 term
     // = (y_etaeta / y_eta^2) d_y u)
-    const double c1h = __ldg(B.c1h + j);
+    const double c1h = STRM_LDG(B.c1h + j);
     const double cc = fma(K.b[0], c2, K.bxz0);  // centre weight of the three second differences
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
-      for (int b = 0; b < 3; ++b) du[a][b] = __ldg(B.grad + (3 * a + b) * d.N + q);
+      for (int b = 0; b < 3; ++b) du[a][b] = STRM_LDG(B.grad + (3 * a + b) * d.N + q);
       lap[a] = fma(-du[a][1], c1h, lap_c<L>(fld[a], n, sy, sz, K, cc, c2));
     }
     double g3[3];
@@ -1440,8 +1440,8 @@ __device__ __forceinline__ void viscous_node(const Consts& C, const Bufs& B, con
   ddiv[0] = dsum<L>(P.div, n, 1, K.ax);
   ddiv[1] = dsum<L>(P.div, n, sy, K.a) * hy;
   ddiv[2] = dsum<L>(P.div, n, sz, K.az);
-  const R uu[3] = {__ldg(P.u + n), __ldg(P.v + n), __ldg(P.w + n)};
-  viscous_combine<R>(K, du, lap, dT, lapT, dmu, ddiv, __ldg(P.mu + n), uu, V);
+  const R uu[3] = {STRM_LDG(P.u + n), STRM_LDG(P.v + n), STRM_LDG(P.w + n)};
+  viscous_combine<R>(K, du, lap, dT, lapT, dmu, ddiv, STRM_LDG(P.mu + n), uu, V);
 }
 
 // Convective part of the residual at node (i, j, k): R_m = -sum_d (f_{s+1} - f_s)/h_d (Eq.
@@ -1454,28 +1454,28 @@ __device__ __forceinline__ void convective_residual(const Dims& d, const Consts&
   long long qy = ((long long)k * (d.ny + 1) + j) * d.nx + i;
   long long qz = ((long long)k * d.ny + j) * d.nx + i;
   long long sxy = (long long)d.nx * d.ny;
-  R hy = __ldg(metric<R>(B).inv_hy + j);
+  R hy = STRM_LDG(metric<R>(B).inv_hy + j);
   bool wlo = C.bc[2] == kBcWall && j == 0, whi = C.bc[3] == kBcWall && j == d.ny - 1;
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
     const R* fx = face_flux<R>(B, 0) + m * d.nf[0];
     const R* fy = face_flux<R>(B, 1) + m * d.nf[1];
     const R* fz = face_flux<R>(B, 2) + m * d.nf[2];
-    R ylo = __ldg(fy + qy), yhi = __ldg(fy + qy + d.nx);
+    R ylo = STRM_LDG(fy + qy), yhi = STRM_LDG(fy + qy + d.nx);
     // staggered wall interface: no mass, x/z momentum or energy crosses it
     if (m != 2) {
       if (wlo) ylo = R(0);
       if (whi) yhi = R(0);
     }
-    res[m] = -((__ldg(fx + qx + 1) - __ldg(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
-               (__ldg(fz + qz + sxy) - __ldg(fz + qz)) * K.inv_dz);
+    res[m] = -((STRM_LDG(fx + qx + 1) - STRM_LDG(fx + qx)) * K.inv_dx + (yhi - ylo) * hy +
+               (STRM_LDG(fz + qz + sxy) - STRM_LDG(fz + qz)) * K.inv_dz);
     if (m == 0 && sizeof(R) != sizeof(double)) {
       // mixed precision: the mass difference is formed in FP64 from the FP32 face fluxes
       // (the difference of two FP32 values is exact in FP64), so that mass telescopes to
       // FP64 round-off as in the FP64 path
-      mass64 = -((to_f64(__ldg(fx + qx + 1)) - to_f64(__ldg(fx + qx))) * C.k64.inv_dx +
-                 (to_f64(yhi) - to_f64(ylo)) * __ldg(B.m64.inv_hy + j) +
-                 (to_f64(__ldg(fz + qz + sxy)) - to_f64(__ldg(fz + qz))) * C.k64.inv_dz);
+      mass64 = -((to_f64(STRM_LDG(fx + qx + 1)) - to_f64(STRM_LDG(fx + qx))) * C.k64.inv_dx +
+                 (to_f64(yhi) - to_f64(ylo)) * STRM_LDG(B.m64.inv_hy + j) +
+                 (to_f64(STRM_LDG(fz + qz + sxy)) - to_f64(STRM_LDG(fz + qz))) * C.k64.inv_dz);
     }
   }
 }
@@ -1485,7 +1485,7 @@ __device__ __forceinline__ void convective_residual(const Dims& d, const Consts&
 // else stored to Rout. FP64 in both precisions; mixed precision takes the FP64 mass difference.
 template <typename R>
 __device__ __forceinline__ void stage_or_store(const Dims& d, const Bufs& B, long long q, const R* res,
-                                               double mass64, double* __restrict__ Rout, const RkFuse& rk) {
+                                               double mass64, double* STRM_RO Rout, const RkFuse& rk) {
   if (rk.w) {
     const double ad = B.scal[kScalAdt + rk.stage], bd = B.scal[kScalBdt + rk.stage];
 #pragma unroll
@@ -1508,7 +1508,7 @@ __device__ __forceinline__ void stage_or_store(const Dims& d, const Bufs& B, lon
 // plus the viscous terms, in precision R; stored in FP64 with the forcing partial sums.
 template <int L, typename R>
 __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, const Bufs& B,
-                                              double* __restrict__ Rout, int blk, double* sh,
+                                              double* STRM_RO Rout, int blk, double* sh,
                                               const RkFuse& rk = RkFuse{nullptr, nullptr, 0}) {
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   double fpart = 0.0;
@@ -1541,7 +1541,7 @@ __device__ __forceinline__ void body_assemble(const Dims& d, const Consts& C, co
       for (int m = 1; m < 5; ++m) res[m] += V[m];
     }
     stage_or_store<R>(d, B, q, res, mass64, Rout, rk);
-    if (C.forcing) fpart = to_f64(res[1]) * __ldg(B.vol + j);
+    if (C.forcing) fpart = to_f64(res[1]) * STRM_LDG(B.vol + j);
   }
   if (C.forcing) {
     double s = block_sum(fpart, sh);

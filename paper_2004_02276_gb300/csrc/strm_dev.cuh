@@ -16,6 +16,18 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+// Read-only loads of the bodies. A translation unit whose kernels read, after a grid-wide
+// barrier, data that other blocks of the same launch wrote defines STRM_COHERENT_LOADS before
+// including this header: the non-coherent read-only path (ld.global.nc) is only defined for
+// data that no thread writes during the kernel, so there the loads are ordinary ones.
+#ifdef STRM_COHERENT_LOADS
+#define STRM_LDG(p) (*(p))
+#define STRM_RO
+#else
+#define STRM_LDG(p) __ldg(p)
+#define STRM_RO __restrict__
+#endif
+
 namespace strm {
 
 constexpr int G = 3;   // ghost layers (central L <= 3, six-node WENO5 stencil)
@@ -31,8 +43,23 @@ struct Dims {
   long long ng;       // px * py * pz
   long long N;        // nx * ny * nz
   long long nf[3];    // faces per direction
+  int slab_ty;        // rows per slab of the slab traversal order (0: natural order), see slab_rows
   unsigned* dbg;      // debug builds: the context's error word (see kDebug)
 };
+
+// Slab heights the slab traversal order admits for an nx x ny grid: TY rows with ny % TY == 0
+// and nx TY a multiple of 256 (a block's 256 elements then stay inside one slab-plane, so the
+// element count of every block is unchanged and reductions keep their partitions' sizes).
+constexpr bool slab_rows_allowed(int nx, int ny, int ty) {
+  return ty > 0 && ny % ty == 0 && ((long long)nx * ty) % 256 == 0;
+}
+
+// The largest admitted slab height not above cap (32, 16 or 8), or 0 for the natural order.
+constexpr int slab_rows_for(int nx, int ny, int cap) {
+  for (int ty = 32; ty >= 8; ty >>= 1)
+    if (ty <= cap && slab_rows_allowed(nx, ny, ty)) return ty;
+  return 0;
+}
 
 // Ghosted node fields of one precision.
 template <typename R>
@@ -209,16 +236,10 @@ __device__ __forceinline__ bool index_ok(const Dims& d, long long q, long long n
 // next slab. The z stencils (nodes k -+ 3, faces' nodes k-2 .. k+3) then re-read planes of the
 // same slab that were read moments before, from L2, instead of planes millions of elements
 // away in the natural order, which on the 2048 x 384 x 256 workload no longer fit in L2. The y
-// stencil of the assembly reads 3 rows outside each slab (6/TY more rows). TY is the largest of
-// 32, 16, 8 that divides ny with nx TY a multiple of 256, so that the element count and each
-// block's share are unchanged and reductions keep their partitions' sizes; other grids keep
-// the natural order.
-__device__ __forceinline__ int slab_rows(const Dims& d) {
-  if ((d.nx & 7) == 0 && d.ny % 32 == 0) return 32;
-  if ((d.nx & 15) == 0 && d.ny % 16 == 0) return 16;
-  if ((d.nx & 31) == 0 && d.ny % 8 == 0) return 8;
-  return 0;
-}
+// stencil of the assembly reads 3 rows outside each slab (6/TY more rows). TY (Dims::slab_ty)
+// is one of 32, 16, 8 admitted by slab_rows_allowed, by default the largest (slab_rows_for with
+// cap 32); 0 keeps the natural order. An ensemble's autotuner may choose a smaller one.
+__device__ __forceinline__ int slab_rows(const Dims& d) { return d.slab_ty; }
 
 // Natural index (p ny + j) nx + i of the t-th element of nplanes planes in slab order
 // (0 <= t < nx ny nplanes < 2^32, TY = slab_rows(d) > 0); 32-bit divisions.
@@ -368,14 +389,14 @@ __device__ __forceinline__ R viscosity(const Coefs<R>& K, int law, R T) {
 // truncation error; FP32 keeps the difference form. With grad, also the first-derivative sums
 // along x, y, z (x and z already divided by dx and dz, y not yet by y_eta deta).
 template <int L>
-__device__ __forceinline__ double lap_c(const double* __restrict__ f, long long n, long long sy, long long sz,
+__device__ __forceinline__ double lap_c(const double* STRM_RO f, long long n, long long sy, long long sz,
                                         const Coefs<double>& K, double cc, double c2, double* grad = nullptr) {
-  double s = cc * __ldg(f + n), t = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  double s = cc * STRM_LDG(f + n), t = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    const double xp = __ldg(f + n + l), xm = __ldg(f + n - l);
-    const double yp = __ldg(f + n + l * sy), ym = __ldg(f + n - l * sy);
-    const double zp = __ldg(f + n + l * sz), zm = __ldg(f + n - l * sz);
+    const double xp = STRM_LDG(f + n + l), xm = STRM_LDG(f + n - l);
+    const double yp = STRM_LDG(f + n + l * sy), ym = STRM_LDG(f + n - l * sy);
+    const double zp = STRM_LDG(f + n + l * sz), zm = STRM_LDG(f + n - l * sz);
     s = fma(K.bx[l], xp + xm, s);
     s = fma(K.bz[l], zp + zm, s);
     t = fma(K.b[l], yp + ym, t);
@@ -395,24 +416,24 @@ __device__ __forceinline__ double lap_c(const double* __restrict__ f, long long 
 
 // sum_l a_l (f_{+l} - f_{-l}) along a line (first-derivative numerator of order 2L)
 template <int L, typename R>
-__device__ __forceinline__ R dsum(const R* __restrict__ f, long long n, long long st, const R* a) {
+__device__ __forceinline__ R dsum(const R* STRM_RO f, long long n, long long st, const R* a) {
   R s = R(0);
 #pragma unroll
-  for (int l = 1; l <= L; ++l) s += a[l] * (__ldg(f + n + l * st) - __ldg(f + n - l * st));
+  for (int l = 1; l <= L; ++l) s += a[l] * (STRM_LDG(f + n + l * st) - STRM_LDG(f + n - l * st));
   return s;
 }
 
 // First- and second-derivative numerators along one line, sharing the loads:
 // s1 = sum_l a_l (f_{+l} - f_{-l}), s2 = sum_l b_l (f_{+l} + f_{-l} - 2 f_0).
 template <int L, typename R>
-__device__ __forceinline__ void dsum12(const R* __restrict__ f, long long n, long long st, const R* a,
+__device__ __forceinline__ void dsum12(const R* STRM_RO f, long long n, long long st, const R* a,
                                        const R* b, R& s1, R& s2) {
-  R f0 = __ldg(f + n);
+  R f0 = STRM_LDG(f + n);
   s1 = R(0);
   s2 = R(0);
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    R fp = __ldg(f + n + l * st), fm = __ldg(f + n - l * st);
+    R fp = STRM_LDG(f + n + l * st), fm = STRM_LDG(f + n - l * st);
     s1 += a[l] * (fp - fm);
     s2 += b[l] * ((fp + fm) - R(2) * f0);
   }
@@ -475,7 +496,7 @@ __device__ __forceinline__ bool face_decision(const Dims& d, const Consts& C, co
   long long n = gidx(d, i, j, k), st = dir_stride(d, dir), m = 0;
 #pragma unroll
   for (int q = -L + 1; q <= L; ++q) {
-    long long b = __double_as_longlong(__ldg(th + n + q * st));
+    long long b = __double_as_longlong(STRM_LDG(th + n + q * st));
     m = b > m ? b : m;
   }
   return m > __double_as_longlong(C.k64.theta_thr);

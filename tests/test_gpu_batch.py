@@ -80,7 +80,9 @@ def test_tuned_ensemble_still_exact():
     ws = [torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda() for c in cases]
     rs = [torch.zeros_like(w) for w in ws]
     choice = E.tune(ws, rs)
-    assert choice[0] in (32, 64, 128) and choice[1] in (4, 8, 16) and choice[2] in (8, 16, 32)
+    assert choice["weno_block"] in (32, 64, 128) and choice["weno_per_sm"] in (4, 8, 16)
+    assert choice["central_per_sm"] in (8, 16, 32) and choice["persistent"] in (0, 1)
+    assert choice["slab_cap"] in (0, 8, 16, 32)
     E.advance(ws, rs, 3, cfl=0.8)
     errs = [rel_max(ws[e].cpu().numpy(), ref[e]) for e in range(len(cases))]
     assert max(errs) <= TOL["fp64"], errs
@@ -182,3 +184,60 @@ def test_ensemble_instances_match_oracle(bag, precision):
         assert err.max() <= ORACLE_TOL[precision], (c.name, err)
         assert abs(times[e] - to) <= (1e-13 if precision == "fp64" else 1e-5) * to, (c.name, times[e], to)
     print(bag, precision, "ensemble vs oracle, worst relative L2:", worst)
+
+
+@pytest.mark.parametrize("bag", ["channels", "boundary-layers"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_stage_matches_oracle(bag, precision):
+    """The persistent schedule (one cooperative launch per RK stage, grid-wide barriers between
+    the phases) with the natural traversal order, then with slab height 8: every instance after
+    4 CFL steps against the oracle, as for the per-kernel-type schedule; no barrier gave up."""
+    cases = mixed_bag(precision) if bag == "channels" else [c for c in bl_bag(precision) if c.bc_xmin != "df"]
+    w0s = [initial(c) for c in cases]
+    refs = [oracle_run(c, w0s[e], 4) for e, c in enumerate(cases)]
+    for slab_cap in (0, 8):
+        E = binding.Ensemble(cases)
+        E.set_schedule(persistent=1, slab_cap=slab_cap)
+        ws = [torch.from_numpy(w0).cuda() for w0 in w0s]
+        rs = [torch.zeros_like(w) for w in ws]
+        E.advance(ws, rs, 4, cfl=0.8)
+        times = E.times()
+        assert E.debug_flags() == 0
+        got = [w.cpu().numpy() for w in ws]
+        E.close()
+        for e, c in enumerate(cases):
+            wo, to = refs[e]
+            err = rel_l2(got[e], wo)
+            assert err.max() <= ORACLE_TOL[precision], (c.name, slab_cap, err)
+            assert abs(times[e] - to) <= (1e-13 if precision == "fp64" else 1e-5) * to, (c.name, times[e], to)
+
+
+def test_persistent_stage_equals_per_kernel_schedule():
+    """FP64: the persistent stage and the per-kernel-type launches run the same bodies; after
+    3 steps they agree to a few ulp (the forcing and CFL reductions may group their partial sums
+    differently)."""
+    cases = mixed_bag("fp64")
+    out = []
+    for persistent in (0, 1):
+        E = binding.Ensemble(cases)
+        E.set_schedule(persistent=persistent)
+        ws = [torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda() for c in cases]
+        rs = [torch.zeros_like(w) for w in ws]
+        E.advance(ws, rs, 3, cfl=0.8)
+        out.append([w.cpu().numpy() for w in ws])
+        E.close()
+    errs = [rel_max(a, b) for a, b in zip(out[1], out[0])]
+    assert max(errs) <= TOL["fp64"], errs
+
+
+def test_schedule_checks():
+    cases = bl_bag("fp64")
+    inflows = {e: inputs.df_profiles(c) for e, c in enumerate(cases) if c.bc_xmin == "df"}
+    E = binding.Ensemble(cases, inflows=inflows)
+    with pytest.raises(binding.StrmError):  # a digital-filter inflow needs its own kernels per step
+        E.set_schedule(persistent=1)
+    for bad in (dict(weno_block=96), dict(slab_cap=12), dict(persistent=2), dict(central_per_sm=0)):
+        with pytest.raises(binding.StrmError):
+            E.set_schedule(**bad)
+    E.set_schedule(slab_cap=0)
+    E.close()
