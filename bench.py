@@ -371,10 +371,11 @@ def measure(case, args, world, local, peak, flops, traffic, pipe_name, extra_pip
 
 
 def host_page_locked(t):
-    """Page-lock a host tensor in place (cudaHostRegister). On the GB300 node an 8 GB buffer from
-    cudaHostAlloc (torch's pin_memory) copied at 75-87 GB/s, and one whose pages were first
-    written by a device-to-host copy at about 10 GB/s, while memory first written by the CPU and
-    registered this way copies at the link's 190-200 GB/s in both directions."""
+    """Page-lock a host tensor in place (cudaHostRegister); the memory is then mapped into the
+    device's address space, and strm_advance_n_host copies it with a kernel through that
+    address (188-210 GB/s on the GB300 node, steady), not with the copy engines, whose
+    device-to-host rate into page-locked buffers fell to 7-130 GB/s some seconds after the
+    buffer was locked."""
     import torch
 
     rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * t.element_size(), 0)
@@ -384,8 +385,9 @@ def host_page_locked(t):
 
 
 def host_copy_rates(h, d):
-    """H2D and D2H rates (GB/s, CUDA events) of one copy of the page-locked host buffer h to and
-    from the device tensor d; d is restored from h afterwards."""
+    """H2D and D2H rates (GB/s, CUDA events) of one copy-engine copy (cudaMemcpyAsync through
+    torch) of the page-locked host buffer h to and from the device tensor d; d is restored from
+    h afterwards. For comparison with the library's kernel copies, which the e2e figure uses."""
     import torch
 
     st = torch.cuda.current_stream()
@@ -513,8 +515,9 @@ def run_ours(args, world, rank, local):
     calls.sort()
     e2e = {"value": case.npts * 3 * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-           "host_buffer": "first-touched host memory page-locked with cudaHostRegister",
-           "copy_gbs": copy_gbs,
+           "host_buffer": "host memory page-locked with cudaHostRegister (mapped): the library "
+                          "copies it with its k_copy_mapped kernel through the device address",
+           "copy_engine_gbs": copy_gbs,
            "call_ms": {"min": round(calls[0] * 1e3, 1), "median": round(calls[len(calls) // 2] * 1e3, 1),
                        "max": round(calls[-1] * 1e3, 1)},
            "weno_face_fraction_last_rhs": round(sum(wf) / (3.0 * case.npts), 4)}

@@ -144,8 +144,11 @@ int strm_rk_step(strm_ctx* ctx, double* w, double* r_old, double dt, double cfl)
 /* nsteps RK3 steps (as strm_rk_step) replayed from a CUDA graph captured on first use. */
 int strm_advance_n(strm_ctx* ctx, double* w, double* r_old, int nsteps, double dt, double cfl);
 
-/* Host-buffer variant: copies w_host (5*N doubles, ideally pinned) to the device buffer w,
- * advances nsteps, copies the state back to w_host and waits for the stream. */
+/* Host-buffer variant: copies w_host (5*N doubles) to the device buffer w, advances nsteps,
+ * copies the state back to w_host and waits for the stream. A page-locked w_host that is mapped
+ * into the device's address space (cudaHostRegister, cudaHostAlloc; 16-byte aligned) is copied
+ * by a kernel through its device address; other host memory by cudaMemcpyAsync. w and r_old:
+ * distinct device buffers of 5*N doubles (STRM_EINVAL if null or equal). */
 int strm_advance_n_host(strm_ctx* ctx, double* w_host, double* w, double* r_old, int nsteps,
                         double dt, double cfl);
 

@@ -318,8 +318,9 @@ class Solver:
     def advance_n_host(self, w_host, w, r_old, nsteps, dt=0.0, cfl=None):
         """Host-buffer path: w_host (CPU float64, ideally pinned) -> device -> n steps -> w_host."""
         cfl = self.case.cfl if cfl is None else cfl
-        if w_host.device.type != "cpu" or w_host.dtype != torch.float64 or not w_host.is_contiguous():
-            raise ValueError("w_host must be a contiguous CPU float64 tensor")
+        if (w_host.device.type != "cpu" or w_host.dtype != torch.float64 or not w_host.is_contiguous()
+                or w_host.numel() != int(np.prod(self.shape))):
+            raise ValueError(f"w_host must be a contiguous CPU float64 tensor of {int(np.prod(self.shape))} elements")
         _check("strm_advance_n_host", lib().strm_advance_n_host(
             self.ctx, _ptr(w_host), _ptr(self._state(w)), _ptr(self._state(r_old)), nsteps, dt, cfl))
 

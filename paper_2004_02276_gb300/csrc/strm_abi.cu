@@ -801,14 +801,62 @@ int strm_advance_n(strm_ctx* x, double* w, double* r_old, int nsteps, double dt,
   return STRM_OK;
 }
 
+namespace {
+
+// The device address of a page-locked host buffer of `bytes` bytes that is mapped into the
+// device's address space, or null: both its first and its last element must map, at the same
+// offset, and it must be 16-byte aligned. A pointer that is not mapped (pageable memory) leaves
+// no error behind.
+double* mapped_host(double* h, size_t bytes) {
+  void* a = nullptr;
+  void* b = nullptr;
+  if ((uintptr_t)h & 15) return nullptr;
+  if (cudaHostGetDevicePointer(&a, h, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&b, (char*)h + bytes - sizeof(double), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if ((char*)b - (char*)a != (ptrdiff_t)(bytes - sizeof(double)) || ((uintptr_t)a & 15)) return nullptr;
+  return (double*)a;
+}
+
+bool is_device_memory(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 int strm_advance_n_host(strm_ctx* x, double* w_host, double* w, double* r_old, int nsteps, double dt,
                         double cfl) {
   if (!x || !w_host) return fail(STRM_EINVAL, "null context or host buffer");
-  size_t bytes = sizeof(double) * 5 * (size_t)x->d.N;
-  STRM_CK(cudaMemcpyAsync(w, w_host, bytes, cudaMemcpyHostToDevice, x->stream));
+  if (!w || !r_old || w == r_old) return fail(STRM_EINVAL, "null or aliased device state buffers");
+  const size_t bytes = sizeof(double) * 5 * (size_t)x->d.N;
+  const long long n = 5 * x->d.N;
+  const int sms = x->weno_grid / 8;
+  // a mapped page-locked buffer is copied by kernels through its device address, any other
+  // host memory by the copy engines
+  double* hd = is_device_memory(w) ? mapped_host(w_host, bytes) : nullptr;
+  if (hd) {
+    launch_copy_mapped(hd, w, n, sms, x->stream);
+    x->launches += 1;
+    STRM_CK(cudaGetLastError());
+  } else {
+    STRM_CK(cudaMemcpyAsync(w, w_host, bytes, cudaMemcpyHostToDevice, x->stream));
+  }
   int rc = strm_advance_n(x, w, r_old, nsteps, dt, cfl);
   if (rc) return rc;
-  STRM_CK(cudaMemcpyAsync(w_host, w, bytes, cudaMemcpyDeviceToHost, x->stream));
+  if (hd) {
+    launch_copy_mapped(w, hd, n, sms, x->stream);
+    x->launches += 1;
+    STRM_CK(cudaGetLastError());
+  } else {
+    STRM_CK(cudaMemcpyAsync(w_host, w, bytes, cudaMemcpyDeviceToHost, x->stream));
+  }
   STRM_CK(cudaStreamSynchronize(x->stream));
   return STRM_OK;
 }

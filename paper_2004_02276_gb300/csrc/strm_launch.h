@@ -73,6 +73,8 @@ void launch_flags(const Dims& d, const Consts& C, const Bufs& B, int dir, unsign
 // elementwise d2f / f2d over n elements
 void launch_d2f(const double* x, float* y, long long n, cudaStream_t s);
 void launch_f2d(const float* x, double* y, long long n, cudaStream_t s);
+// copy n doubles between device memory and a mapped page-locked host buffer (16-byte aligned)
+void launch_copy_mapped(const double* src, double* dst, long long n, int sms, cudaStream_t s);
 void launch_export_sensor(const Dims& d, const Consts& C, const Bufs& B, double* theta, double* div,
                           cudaStream_t s);
 

@@ -275,4 +275,26 @@ void launch_f2d(const float* x, double* y, long long n, cudaStream_t s) {
   if (n > 0) k_convert_f2d<<<(unsigned)std::min<long long>(blocks_for(n, 256), 4096), 256, 0, s>>>(x, y, n);
 }
 
+// Copy n doubles between device memory and a page-locked host buffer mapped into the device's
+// address space (src or dst is the mapped pointer; both 16-byte aligned): 16-byte loads and
+// stores in a grid-stride loop, the odd last element by one thread. On the GB300 node the
+// GPU's loads and stores cross the CPU-GPU link at 188-210 GB/s whatever the buffer's history,
+// where the copy engines' device-to-host rate fell to 7-130 GB/s for buffers page-locked some
+// seconds earlier.
+__global__ void __launch_bounds__(256) k_copy_mapped(const double2* STRM_RO src, double2* STRM_RO dst,
+                                                     long long n) {
+  const long long n2 = n >> 1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    reinterpret_cast<double*>(dst)[n - 1] = reinterpret_cast<const double*>(src)[n - 1];
+}
+
+void launch_copy_mapped(const double* src, double* dst, long long n, int sms, cudaStream_t s) {
+  if (n > 0)
+    k_copy_mapped<<<(unsigned)std::min<long long>(blocks_for(n / 2 + 1, 256), 8LL * sms), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(src), reinterpret_cast<double2*>(dst), n);
+}
+
 }  // namespace strm

@@ -123,6 +123,38 @@ def test_graph_replay_equals_single_steps_bitwise():
     s.close()
 
 
+def test_host_buffer_paths_equal_device_steps():
+    """strm_advance_n_host with pageable host memory (copy engines), with memory page-locked by
+    cudaHostRegister and with cudaHostAlloc memory (both mapped: copied by a kernel through the
+    device address) gives the device-resident trajectory bit for bit; 5 N is odd here, so the
+    copy kernel's last element takes its scalar path."""
+    case = inputs.Case(nx=33, ny=37, nz=9)
+    assert (5 * case.npts) % 2 == 1
+    w0 = inputs.channel_state(case, seed=4)
+    s = binding.Solver(case)
+    a = gpu(w0)
+    s.advance_n(a, torch.zeros_like(a), 3, cfl=0.8)
+    cudart = torch.cuda.cudart()
+    for kind in ("pageable", "registered", "pin_memory"):
+        s.set_time(0.0)
+        h = torch.from_numpy(w0.copy())
+        if kind == "registered":
+            assert int(cudart.cudaHostRegister(h.data_ptr(), h.numel() * 8, 0)) == 0
+        elif kind == "pin_memory":
+            h = h.pin_memory()
+        try:
+            c = torch.empty_like(a)
+            s.advance_n_host(h, c, torch.zeros_like(a), 3, cfl=0.8)
+            assert torch.equal(h.cuda(), a), kind
+            assert torch.equal(c, a), kind
+        finally:
+            if kind == "registered":
+                assert int(cudart.cudaHostUnregister(h.data_ptr())) == 0
+    with pytest.raises(binding.StrmError):  # aliased device buffers
+        s.advance_n_host(torch.from_numpy(w0.copy()), a, a, 1, cfl=0.8)
+    s.close()
+
+
 def test_fixed_dt_step_matches_oracle():
     case = inputs.Case(nx=24, ny=20, nz=10, y_wall=False, forcing=False)
     w0 = inputs.random_state(case, seed=5, amp_u=0.2)
