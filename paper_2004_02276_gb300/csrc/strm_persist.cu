@@ -73,8 +73,11 @@ __device__ bool grid_barrier(unsigned* bar, unsigned long long limit_ns) {
   return s_ok != 0;
 }
 
+// Resident blocks per SM: 2 in FP64 (128 registers; its phases are bound by the FP64 pipe), 4 in
+// mixed precision (64 registers; its FP32 and memory-bound phases want the occupancy: 0.76 of the
+// per-kernel schedule's rate on the 64-channel ensemble against 0.68 with 2).
 template <int L, bool MIXED>
-__global__ void __launch_bounds__(kStageBlock, 2) kb_stage(BatchIndex X, StageArgs A) {
+__global__ void __launch_bounds__(kStageBlock, MIXED ? 4 : 2) kb_stage(BatchIndex X, StageArgs A) {
   using R = typename std::conditional<MIXED, float, double>::type;
   __shared__ double sh[32];
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
