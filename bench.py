@@ -663,7 +663,7 @@ def run_channel(args, world, local):
     return out
 
 
-def run_batched(args, world, local, large_grid_value, precision="fp64"):
+def run_batched(args, world, local, large_grid_value, precision="fp64", schedule="tuned"):
     """The batched workload: 64 independent channels of uneven size, Mach and Reynolds number
     (44.7 M points in all), advanced by the ensemble kernels, one graph replay per step, launch
     shapes from the autotuner (run before the warm-up, outside the timed region). The per-point
@@ -677,7 +677,12 @@ def run_batched(args, world, local, large_grid_value, precision="fp64"):
     E = binding.Ensemble(cases, device=f"cuda:{local}")
     ws = [torch.from_numpy(inputs.channel_state(c)).cuda() for c in cases]
     rs = [torch.zeros_like(w) for w in ws]
-    choice = E.tune(ws, rs)
+    if schedule == "tuned":
+        choice = E.tune(ws, rs)
+    else:  # a fixed schedule, for profiling captures
+        choice = dict(weno_block=128, weno_per_sm=16, central_per_sm=16,
+                      persistent=int(schedule == "persistent"), slab_cap=32)
+        E.set_schedule(**choice)
     E.advance(ws, rs, args.warmup, cfl=0.8)
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -714,7 +719,7 @@ def run_batched(args, world, local, large_grid_value, precision="fp64"):
     E.close()
     return {"value": value, "ms_per_step": ms / args.steps, "instances": len(cases),
             "points": npts, "dtype": "f64" if precision == "fp64" else "f32 flux / f64 state",
-            "per_point_vs_large_grid": value / large_grid_value,
+            "per_point_vs_large_grid": value / large_grid_value if large_grid_value else None,
             "tuned": choice, "schedules": schedules,
             "schedule": "one cooperative launch per RK stage" if choice["persistent"] else
                         "one launch per kernel type, one graph per step",
@@ -772,6 +777,11 @@ def main():
                          "captures only, the channel")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     ap.add_argument("--no-variants", action="store_true", help="skip the channel and batched variants")
+    ap.add_argument("--ensemble-only", default="", choices=["", "fp64", "mixed"],
+                    help="for profiling captures only: run the 64-channel ensemble alone in this "
+                         "precision and print its figures")
+    ap.add_argument("--schedule", default="tuned", choices=["tuned", "per-kernel", "persistent"],
+                    help="ensemble schedule with --ensemble-only (default: the autotuner's choice)")
     ap.add_argument("--peaks-only", action="store_true",
                     help="only measure and print the FP64/FP32 FMA rates (strm_peak_fma) and exit")
     args = ap.parse_args()
@@ -785,6 +795,14 @@ def main():
 
         torch.cuda.set_device(local)
         print(json.dumps(measure_peaks(local)), flush=True)
+        return
+    if args.ensemble_only:
+        import torch
+
+        torch.cuda.set_device(local)
+        out = run_batched(args, world, local, None, args.ensemble_only, args.schedule)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
