@@ -315,6 +315,13 @@ int strm_ensemble_tune(strm_ensemble* ens, double* const* w, double* const* r_ol
  * the assembly). Takes effect at the next strm_ensemble_advance. */
 int strm_ensemble_set_schedule(strm_ensemble* ens, const int* choice);
 
+/* How long a grid-wide barrier of the persistent stage waits for the other blocks before it gives
+ * up (default 10 s; seconds in [0, 3600], else STRM_EINVAL). Every phase of a stage must finish
+ * within it. 0 makes the first block that has to wait give up, so the failure path (all blocks
+ * leave, strm_ensemble_debug_flags reports 32) can be exercised without a fault. Takes effect at
+ * the next strm_ensemble_advance. */
+int strm_ensemble_set_barrier_limit(strm_ensemble* ens, double seconds);
+
 /* Conserved totals of every instance, out_host[5*e + m]. Synchronises. */
 int strm_ensemble_totals(strm_ensemble* ens, double* const* w, double* out_host);
 
@@ -323,8 +330,9 @@ int strm_ensemble_times(strm_ensemble* ens, double* t_host);
 
 /* The error words of all instances OR-ed together (bounds-checking build; see
  * strm_debug_flags), plus 32 (in every build) when a grid-wide barrier of the persistent stage
- * gave up waiting (10 s); the blocks then left the kernel, the state is not valid, and every
- * later persistent stage of this ensemble leaves at its first barrier. Synchronises. */
+ * gave up waiting (strm_ensemble_set_barrier_limit); the blocks then left the kernel, the state
+ * is not valid, and every later persistent stage leaves at its first barrier until this call
+ * reports the bit, which also resets the barrier. Synchronises. */
 int strm_ensemble_debug_flags(strm_ensemble* ens, unsigned* flags_host);
 
 void strm_ensemble_destroy(strm_ensemble* ens);

@@ -107,6 +107,7 @@ SIGNATURES = {
     "strm_ensemble_advance": ([_vp, _P(_vp), _P(_vp), _i, _d, _d], _i),
     "strm_ensemble_tune": ([_vp, _P(_vp), _P(_vp), _P(_i)], _i),
     "strm_ensemble_set_schedule": ([_vp, _P(_i)], _i),
+    "strm_ensemble_set_barrier_limit": ([_vp, _d], _i),
     "strm_ensemble_totals": ([_vp, _P(_vp), _P(_d)], _i),
     "strm_ensemble_times": ([_vp, _P(_d)], _i),
     "strm_ensemble_destroy": ([_vp], None),
@@ -517,6 +518,11 @@ class Ensemble:
         out = (ctypes.c_int * 5)()
         _check("strm_ensemble_tune", lib().strm_ensemble_tune(self.ens, self._ptrs(ws), self._ptrs(rs), out))
         return dict(zip(self.SCHEDULE, list(out)))
+
+    def set_barrier_limit(self, seconds):
+        """How long a grid-wide barrier of the persistent stage waits before giving up (0: the
+        first block that has to wait gives up, which exercises the failure path)."""
+        _check("strm_ensemble_set_barrier_limit", lib().strm_ensemble_set_barrier_limit(self.ens, float(seconds)))
 
     def set_schedule(self, weno_block=128, weno_per_sm=8, central_per_sm=16, persistent=0, slab_cap=32):
         """Set the schedule the autotuner would choose (see tune)."""

@@ -191,6 +191,7 @@ struct strm_ensemble {
   int* start_dev = nullptr;
   unsigned* bar_dev = nullptr;  // persistent-stage barrier [3] (zeroed at creation)
   int stage_grid = 0;           // blocks of the persistent stage launch (0: not available)
+  unsigned long long barrier_ns = kBarrierLimitNs;  // a persistent-stage barrier gives up after this
   Tuning tune;
   // graph of one RK step of the ensemble
   cudaStream_t cap = nullptr;
@@ -213,7 +214,7 @@ BatchIndex index_of(const strm_ensemble* E) { return BatchIndex{E->inst_dev, E->
 StageArgs stage_args(const strm_ensemble* E, int stage, double cfl, double dt_fixed) {
   StageArgs A = {};
   A.bar = E->bar_dev;
-  A.limit_ns = kBarrierLimitNs;
+  A.limit_ns = E->barrier_ns;
   A.cfl = cfl;
   A.dt_fixed = dt_fixed;
   A.stage = stage;
@@ -500,7 +501,11 @@ int strm_ensemble_debug_flags(strm_ensemble* E, unsigned* flags_host) {
   unsigned gave_up = 0;
   STRME_CK(cudaMemcpyAsync(&gave_up, E->bar_dev + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, E->stream));
   STRME_CK(cudaStreamSynchronize(E->stream));
-  if (gave_up) acc |= kEnsembleBarrier;
+  if (gave_up) {  // report once, and reset the barrier (arrivals, generation, flag) for later stages
+    acc |= kEnsembleBarrier;
+    STRME_CK(cudaMemsetAsync(E->bar_dev, 0, 3 * sizeof(unsigned), E->stream));
+    STRME_CK(cudaStreamSynchronize(E->stream));
+  }
   *flags_host = acc;
   return STRM_OK;
 }
@@ -553,6 +558,16 @@ int strm_ensemble_advance(strm_ensemble* E, double* const* w, double* const* r_o
     E->g_dt = dt;
   }
   for (int s = 0; s < nsteps; ++s) STRME_CK(cudaGraphLaunch(E->gexec, E->stream));
+  return STRM_OK;
+}
+
+int strm_ensemble_set_barrier_limit(strm_ensemble* E, double seconds) {
+  if (!E || !(seconds >= 0.0) || seconds > 3600.0) return record_error(STRM_EINVAL, "null ensemble or limit outside [0, 3600] s");
+  E->barrier_ns = (unsigned long long)(seconds * 1e9);
+  if (E->gexec) {  // the captured graph holds the old limit
+    cudaGraphExecDestroy(E->gexec);
+    E->gexec = nullptr;
+  }
   return STRM_OK;
 }
 

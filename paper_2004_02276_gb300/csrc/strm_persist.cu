@@ -55,10 +55,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned long long limit_ns) {
       st_release_u32(bar + 1, gen + 1u);
     } else {
       const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
       while (ld_acquire_u32(bar + 1) == gen) {
         if (ld_acquire_u32(bar + 2) != 0u) break;
-        if ((++spins & 31u) == 0u && global_ns() - t0 > limit_ns) {
+        if (global_ns() - t0 >= limit_ns) {  // limit 0: the first block that must wait gives up
           atomicOr(bar + 2, 1u);
           break;
         }

@@ -241,3 +241,35 @@ def test_schedule_checks():
             E.set_schedule(**bad)
     E.set_schedule(slab_cap=0)
     E.close()
+
+
+def test_persistent_barrier_gives_up_and_recovers():
+    """Failure detection of the persistent stage without a GPU fault: with a barrier limit of 0
+    the first block that has to wait gives up, every block leaves the kernel, and the ensemble
+    reports bit 32 once (the report also resets the barrier). With the limit restored, the same
+    ensemble advances a fresh state exactly as an ensemble that never failed."""
+    cases = mixed_bag("fp64")
+    fresh = lambda: [torch.from_numpy(inputs.channel_state(c, seed=c.nx)).cuda() for c in cases]
+    ref = binding.Ensemble(cases)
+    ref.set_schedule(persistent=1)
+    wr = fresh()
+    ref.advance(wr, [torch.zeros_like(w) for w in wr], 2, cfl=0.8)
+    want = [w.cpu().numpy() for w in wr]
+    ref.close()
+    E = binding.Ensemble(cases)
+    E.set_schedule(persistent=1)
+    E.set_barrier_limit(0.0)
+    ws = fresh()
+    E.advance(ws, [torch.zeros_like(w) for w in ws], 1, cfl=0.8)
+    assert E.debug_flags() & 32
+    assert E.debug_flags() == 0  # reported once; the barrier is reset
+    E.set_barrier_limit(10.0)
+    ws = fresh()
+    rs = [torch.zeros_like(w) for w in ws]
+    E.advance(ws, rs, 2, cfl=0.8)
+    assert E.debug_flags() == 0
+    for e in range(len(cases)):
+        assert np.array_equal(ws[e].cpu().numpy(), want[e]), e
+    with pytest.raises(binding.StrmError):
+        E.set_barrier_limit(-1.0)
+    E.close()
