@@ -41,12 +41,12 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 // Node fields held in FP64 and in FP32 (mixed precision only). FP64 precision: 12 fields, the
 // 6 wave speeds u_d -+ c, the 3 momentum components and the 3 normal momentum fluxes; mixed
 // precision: the 9 fields the FP64 characteristic projection and switch read and the same 6.
-const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11;
+const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11, kN32Xdev = 5;
 
 struct Layout {
   Dims d;
   bool mixed;
-  size_t off_n64[kN64All], off_n32[kN32Mixed];
+  size_t off_n64[kN64All], off_n32[kN32Mixed], off_xdev[kN32Xdev], off_xref;
   size_t off_fh[3];
   size_t off_R, off_grad, off_band, off_dbg, off_wl[3], off_cl[3], off_wcount, off_red, off_scal, off_metric, off_metric32;
   size_t total;
@@ -89,11 +89,19 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
     L.off_n64[f] = off;
     off = align_up(off + sizeof(double) * (size_t)d.ng);
   }
-  if (L.mixed)
+  if (L.mixed) {
     for (int f = 0; f < kN32Mixed; ++f) {
       L.off_n32[f] = off;
       off = align_up(off + sizeof(float) * (size_t)d.ng);
     }
+    // the x rows' deviations from their reference, and the references
+    for (int f = 0; f < kN32Xdev; ++f) {
+      L.off_xdev[f] = off;
+      off = align_up(off + sizeof(float) * (size_t)d.ng);
+    }
+    L.off_xref = off;
+    off = align_up(off + sizeof(float) * 5 * (size_t)d.ny * d.nz);
+  }
   size_t fbytes = L.mixed ? sizeof(float) : sizeof(double);
   for (int dir = 0; dir < 3; ++dir) {
     L.off_fh[dir] = off;
@@ -576,7 +584,11 @@ int strm_init_grid(strm_ctx** out, const strm_grid* g, const strm_phys* p, const
     float** f32[kN32Mixed] = {&N32.rho, &N32.u, &N32.v, &N32.w, &N32.p, &N32.T,
                               &N32.H,   &N32.c, &N32.mu, &N32.theta, &N32.div};
     for (int f = 0; f < kN32Mixed; ++f) *f32[f] = (float*)(ws + L.off_n32[f]);
+    for (int f = 0; f < kN32Xdev; ++f) x->B.xdev[f] = (float*)(ws + L.off_xdev[f]);
+    x->B.xref = (float*)(ws + L.off_xref);
   } else {
+    for (int f = 0; f < kN32Xdev; ++f) x->B.xdev[f] = nullptr;
+    x->B.xref = nullptr;
     double** f64[12] = {&N64.rho, &N64.u, &N64.v,  &N64.w,     &N64.p,   &N64.T,
                         &N64.H,   &N64.c, &N64.mu, &N64.theta, &N64.div, &N64.srho};
     for (int f = 0; f < 12; ++f) *f64[f] = (double*)(ws + L.off_n64[f]);
