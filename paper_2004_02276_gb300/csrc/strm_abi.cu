@@ -41,7 +41,7 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 // Node fields held in FP64 and in FP32 (mixed precision only). FP64 precision: 12 fields, the
 // 6 wave speeds u_d -+ c, the 3 momentum components and the 3 normal momentum fluxes; mixed
 // precision: the 9 fields the FP64 characteristic projection and switch read and the same 6.
-const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11, kN32Xdev = 5;
+const int kN64All = 24, kN64Mixed = 15, kN32Mixed = 11, kN32Xdev = 3;
 
 struct Layout {
   Dims d;
@@ -100,7 +100,7 @@ Layout make_layout(const strm_grid* g, const strm_scheme* s) {
       off = align_up(off + sizeof(float) * (size_t)d.ng);
     }
     L.off_xref = off;
-    off = align_up(off + sizeof(float) * 5 * (size_t)d.ny * d.nz);
+    off = align_up(off + sizeof(float) * kN32Xdev * (size_t)d.ny * d.nz);
   }
   size_t fbytes = L.mixed ? sizeof(float) : sizeof(double);
   for (int dir = 0; dir < 3; ++dir) {

@@ -71,11 +71,12 @@ __device__ __forceinline__ void body_prims(const Dims& d, const Consts& C, const
 }
 
 // Reference state of the x row (j, k) for the deviation form of the mixed x faces' central
-// flux: rho, u, v, w and H of the row's first node, from the conserved state, in FP32 with
-// explicitly rounded operations (so that every thread of the row forms the same values). Any
-// values constant along the row serve; these are close to the row's own.
+// flux: rho, u and H of the row's first node, from the conserved state, in FP32 with explicitly
+// rounded operations (so that every thread of the row forms the same values). Any values
+// constant along the row serve; these are close to the row's own. (v and w need none: the
+// transverse velocities are small, so their FP32 copies already carry small absolute errors.)
 __device__ __forceinline__ void xrow_ref(const Dims& d, const Consts& C, const double* w, int j, int k,
-                                         float r[5]) {
+                                         float r[3]) {
   const long long q0 = ((long long)k * d.ny + j) * d.nx;
   const float rho = d2f(w[q0]);
   const float ir = __frcp_rn(rho);
@@ -85,9 +86,7 @@ __device__ __forceinline__ void xrow_ref(const Dims& d, const Consts& C, const d
   const float g = C.k32.gamma;
   r[0] = rho;
   r[1] = u;
-  r[2] = v;
-  r[3] = ww;
-  r[4] = __fsub_rn(__fmul_rn(g, E), __fmul_rn(__fmul_rn(0.5f, __fsub_rn(g, 1.f)), q2));  // E + p/rho
+  r[2] = __fsub_rn(__fmul_rn(g, E), __fmul_rn(__fmul_rn(0.5f, __fsub_rn(g, 1.f)), q2));  // E + p/rho
 }
 
 // Mixed precision: the fields the characteristic projection reads are formed in FP64 (rho, u,
@@ -140,17 +139,17 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     F.H[n] = d2f(H);
     F.c[n] = cf;
     F.mu[n] = viscosity(C.k32, C.visc_law, Tf);
-    // x-row deviations rho - rho_0, ... (FP64 differences, then FP32): the x faces' central flux
-    // works on these, so its FP32 rounding scales with the row's variations, not its values
-    float r[5];
+    // x-row deviations rho - rho_0, u - u_0, H - H_0 (FP64 differences, then FP32): the x faces'
+    // central flux works on these, so its FP32 rounding scales with the row's variations
+    float r[3];
     xrow_ref(d, C, w, j, k, r);
-    const double xv[5] = {rho, u, v, ww, H};
+    const double xv[3] = {rho, u, H};
 #pragma unroll
-    for (int m = 0; m < 5; ++m) B.xdev[m][n] = d2f(xv[m] - f2d(r[m]));
+    for (int m = 0; m < 3; ++m) B.xdev[m][n] = d2f(xv[m] - f2d(r[m]));
     if (i == 0) {
       const long long rs = (long long)d.ny * d.nz, row = (long long)k * d.ny + j;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) B.xref[m * rs + row] = r[m];
+      for (int m = 0; m < 3; ++m) B.xref[m * rs + row] = r[m];
     }
     if (want_cfl)  // FP32 spectral radius: the step needs no more than FP32 accuracy here
       spec = (fabsf(uf) + cf) * C.k32.inv_dx + (fabsf(vf) + cf) * B.m32.inv_hy[j] + (fabsf(wf) + cf) * C.k32.inv_dz;
@@ -481,7 +480,7 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
     copy_ghost(C, B, dst, src);
     if (C.mixed && face == 0)  // the source node lies in the same x row: same reference
 #pragma unroll
-      for (int m = 0; m < 5; ++m) B.xdev[m][dst] = B.xdev[m][src];
+      for (int m = 0; m < 3; ++m) B.xdev[m][dst] = B.xdev[m][src];
     return;
   }
   if constexpr (kDebug) {  // the interior source node of the face kinds below
@@ -518,9 +517,9 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
   store_pstate(C, B, dst, g);
   if (C.mixed && face == 0) {  // x-row deviations of the ghost state (reference from k_prims)
     const long long rs = (long long)d.ny * d.nz, row = (long long)k * d.ny + j;
-    const double xv[5] = {g.rho, g.u, g.v, g.w, P.H[dst]};
+    const double xv[3] = {g.rho, g.u, P.H[dst]};
 #pragma unroll
-    for (int m = 0; m < 5; ++m) B.xdev[m][dst] = d2f(xv[m] - f2d(B.xref[m * rs + row]));
+    for (int m = 0; m < 3; ++m) B.xdev[m][dst] = d2f(xv[m] - f2d(B.xref[m * rs + row]));
   }
 }
 
@@ -816,16 +815,17 @@ __device__ __forceinline__ void central_flux(const Consts& C, const Bufs& B, lon
 }
 
 // Mixed precision, x faces: the same split flux from the x-row deviations. With the row's
-// reference (rho_0, u_0, v_0, w_0, H_0) and the pair sums S_rho = rho'_a + rho'_b, S_u, ... of the
-// deviations, (rho_a + rho_b) = 2 rho_0 + S_rho and so on, and each pair's terms split into the
-// constant 4 a_l/4 rho_0 u_0 (1, 2 phi_0) and the rest,
+// reference (rho_0, u_0, H_0; v_0 = w_0 = 0) and the pair sums S_rho = rho'_a + rho'_b, S_u, S_H
+// of the deviations, (rho_a + rho_b) = 2 rho_0 + S_rho and so on, each pair's terms split into the
+// constant a_l rho_0 u_0 (1, 2 u_0, 2 H_0) and the rest,
 //   q' = a_l/4 [S_u (2 rho_0 + S_rho) + 2 u_0 S_rho],
 //   f_rho gets 2 q',  f_phi gets K_l S_phi + q' (2 phi_0 + S_phi),  K_l = a_l rho_0 u_0,
-// which is evaluated in FP32. The constant parts add up to (rho_0 u_0)(1, u_0, v_0, w_0, H_0)
-// (consistency, 8 sum_l l a_l/4 = 1): the same for every face of the row, so they cancel in the
-// flux differences and are left out; the row's WENO faces subtract them too
-// (xrow_flux_const). The FP32 rounding then scales with the deviations instead of the values
-// (the x momentum flux rho u^2 is of order one). The pressure part is as in central_flux.
+// (phi = u, H; for v and w, whose reference is 0, (K_l + q') S_phi with the full FP32 sums), all
+// in FP32. The constant parts add up to (rho_0 u_0)(1, u_0, 0, 0, H_0) (consistency,
+// 8 sum_l l a_l/4 = 1): the same for every face of the row, so they cancel in the flux
+// differences and are left out; the row's WENO faces subtract them too (xrow_flux_const). The
+// FP32 rounding then scales with the deviations instead of the values (the x momentum flux
+// rho u^2 + p is of order one). The pressure part is as in central_flux.
 template <int L>
 __device__ __forceinline__ void central_flux_xdev(const Dims& d, const Consts& C, const Bufs& B, long long n,
                                                   int j, int k, float* f) {
@@ -833,17 +833,14 @@ __device__ __forceinline__ void central_flux_xdev(const Dims& d, const Consts& C
   const float* aq = C.k32.aq;
   const float* apc = C.k32.ap;
   const long long rs = (long long)d.ny * d.nz, row = (long long)k * d.ny + j;
-  const float r0 = B.xref[row], u0 = B.xref[rs + row], v0 = B.xref[2 * rs + row];
-  const float w0 = B.xref[3 * rs + row], H0 = B.xref[4 * rs + row];
+  const float r0 = B.xref[row], u0 = B.xref[rs + row], H0 = B.xref[2 * rs + row];
   const float* STRM_RO Dr = B.xdev[0];
   const float* STRM_RO Du = B.xdev[1];
-  const float* STRM_RO Dv = B.xdev[2];
-  const float* STRM_RO Dw = B.xdev[3];
-  const float* STRM_RO DH = B.xdev[4];
+  const float* STRM_RO DH = B.xdev[2];
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, ap = 0.f;
 #pragma unroll
   for (int r = 0; r < L; ++r) ap = fmaf(apc[r], STRM_LDG(P.p + n - r) + STRM_LDG(P.p + n + r + 1), ap);
-  const float r2 = 2.f * r0, u2 = 2.f * u0, v2 = 2.f * v0, w2 = 2.f * w0, H2 = 2.f * H0;
+  const float r2 = 2.f * r0, u2 = 2.f * u0, H2 = 2.f * H0;
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
     const float Kl = (4.f * aq[l]) * (r0 * u0);
@@ -851,13 +848,14 @@ __device__ __forceinline__ void central_flux_xdev(const Dims& d, const Consts& C
     for (int m = 0; m < l; ++m) {
       const long long ia = n - m, ib = n + l - m;
       const float Sr = STRM_LDG(Dr + ia) + STRM_LDG(Dr + ib), Su = STRM_LDG(Du + ia) + STRM_LDG(Du + ib);
-      const float Sv = STRM_LDG(Dv + ia) + STRM_LDG(Dv + ib), Sw = STRM_LDG(Dw + ia) + STRM_LDG(Dw + ib);
       const float SH = STRM_LDG(DH + ia) + STRM_LDG(DH + ib);
+      const float Sv = STRM_LDG(P.v + ia) + STRM_LDG(P.v + ib), Sw = STRM_LDG(P.w + ia) + STRM_LDG(P.w + ib);
       const float qp = aq[l] * fmaf(Su, r2 + Sr, u2 * Sr);
+      const float qf = Kl + qp;
       a0 += qp;
       a1 = fmaf(Kl, Su, fmaf(qp, u2 + Su, a1));
-      a2 = fmaf(Kl, Sv, fmaf(qp, v2 + Sv, a2));
-      a3 = fmaf(Kl, Sw, fmaf(qp, w2 + Sw, a3));
+      a2 = fmaf(qf, Sv, a2);
+      a3 = fmaf(qf, Sw, a3);
       a4 = fmaf(Kl, SH, fmaf(qp, H2 + SH, a4));
     }
   }
@@ -868,7 +866,7 @@ __device__ __forceinline__ void central_flux_xdev(const Dims& d, const Consts& C
   f[4] = a4;
 }
 
-// The constant the deviation-form x flux leaves out, (rho_0 u_0) c (1, u_0, v_0, w_0, H_0) with
+// The constant the deviation-form x flux leaves out, (rho_0 u_0) c (1, u_0, 0, 0, H_0) with
 // c = 8 sum_l l a_l/4 in the FP32 coefficients, taken off the x WENO faces of mixed precision
 // so that every face of the row carries the same offset.
 __device__ __forceinline__ void xrow_flux_const(const Dims& d, const Consts& C, const Bufs& B, int j, int k,
@@ -879,9 +877,9 @@ __device__ __forceinline__ void xrow_flux_const(const Dims& d, const Consts& C, 
   const float c0 = (8.f * s) * (B.xref[row] * B.xref[rs + row]);
   c5[0] = c0;
   c5[1] = c0 * B.xref[rs + row];
-  c5[2] = c0 * B.xref[2 * rs + row];
-  c5[3] = c0 * B.xref[3 * rs + row];
-  c5[4] = c0 * B.xref[4 * rs + row];
+  c5[2] = 0.f;
+  c5[3] = 0.f;
+  c5[4] = c0 * B.xref[2 * rs + row];
 }
 
 // ------------------------------------------------------------------------------ WENO5

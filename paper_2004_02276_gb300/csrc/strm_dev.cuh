@@ -144,11 +144,11 @@ struct Bufs {
                                                 //   in both precisions), for the WENO projection
   double* mflux[3];                             // rho u_d^2 + p, d = x, y, z (the normal momentum
                                                 //   flux; ghosted, FP64), for the WENO projection
-  float* xdev[5];                               // mixed: rho, u, v, w, H less their x-row
-                                                //   reference (ghosted; x rows only), for the
-                                                //   x faces' central flux, see central_flux_xdev
-  float* xref;                                  // mixed: [5][nz][ny] the reference of each x row
-                                                //   (rho, u, v, w, H of its first node, FP32)
+  float* xdev[3];                               // mixed: rho, u, H less their x-row reference
+                                                //   (ghosted; x rows only), for the x faces'
+                                                //   central flux, see central_flux_xdev
+  float* xref;                                  // mixed: [3][nz][ny] the reference of each x row
+                                                //   (rho, u, H of its first node, FP32)
   double* grad;                                 // FP64: velocity gradients d_b u_a at the
                                                 //   interior nodes, [3a + b][N], from the sensor
   double* ubar;                                 // spanwise-mean u at the recycling plane, per j
