@@ -174,3 +174,32 @@ def test_pow_19_25_series_and_accuracy():
         dl = (t19 - y25) * inv
         y = y0 + (y0 * dl) * (float(c1) + dl * (float(c2) + float(c3) * dl))
         assert np.all(np.abs(y - ref) <= 2 * np.spacing(ref)), pert
+
+
+def test_x_flux_deviation_form():
+    """The mixed x faces' split flux in deviation form (central_flux_xdev): around a reference
+    (rho_0, u_0, H_0) constant along the row, with v_0 = w_0 = 0, each pair's contribution
+    q (phi_a + phi_b), q = a (rho_a + rho_b)(u_a + u_b), equals the kernel's
+    K S_phi + q' (2 phi_0 + S_phi) for phi = u, H and (K + q') S_phi for v, w, plus the constant
+    K (1, 2 u_0, 0, 0, 2 H_0) the kernel leaves out (K = 4 a rho_0 u_0, q' as in the kernel), and
+    the left-out constants of a face add up to (rho_0 u_0)(1, u_0, 0, 0, H_0) times 8 sum_l l a_l
+    (for f_rho: twice the sum of K over the pairs), the x WENO faces' offset."""
+    a, r0, u0, H0 = sp.symbols("a rho0 u0 H0")
+    dra, drb, dua, dub, dHa, dHb, va, vb = sp.symbols("dra drb dua dub dHa dHb va vb")
+    Sr, Su, SH, Sv = dra + drb, dua + dub, dHa + dHb, va + vb
+    q = a * (2 * r0 + Sr) * (2 * u0 + Su)
+    K = 4 * a * r0 * u0
+    qp = a * (Su * (2 * r0 + Sr) + 2 * u0 * Sr)
+    assert sp.expand(q - (K + qp)) == 0
+    assert sp.expand(q * (2 * u0 + Su) - (K * Su + qp * (2 * u0 + Su) + K * 2 * u0)) == 0
+    assert sp.expand(q * (2 * H0 + SH) - (K * SH + qp * (2 * H0 + SH) + K * 2 * H0)) == 0
+    assert sp.expand(q * Sv - (K + qp) * Sv) == 0
+    # the constant per face: pairs (l, m), m < l, each with its own K_l = 4 a_l rho0 u0
+    for L in (2, 3):
+        al = sp.symbols(f"a1:{L + 1}")
+        pairs = [(l, m) for l in range(1, L + 1) for m in range(l)]
+        f_rho_const = 2 * sum(4 * al[l - 1] * r0 * u0 for l, m in pairs)
+        f_u_const = sum(4 * al[l - 1] * r0 * u0 * 2 * u0 for l, m in pairs)
+        s8 = 8 * sum(l * al[l - 1] for l in range(1, L + 1))
+        assert sp.expand(f_rho_const - s8 * r0 * u0) == 0
+        assert sp.expand(f_u_const - s8 * r0 * u0 * u0) == 0
