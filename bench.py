@@ -68,6 +68,10 @@ FLOPS32_PER_UNIT_MIXED = {
 # scaled to a launch by its nodes; traffic per unit grows in proportion with the nodes.
 DRAM_BYTES_PER_UNIT = {"assemble": 415.3}
 DRAM_BYTES_PER_UNIT_MIXED = {"assemble": 238.1}
+# Algorithmic HBM bytes per node of the mixed-precision assembly (stage update fused): FP64 w and
+# the register in and out (160), the FP32 face fluxes of three directions (60), the FP32 node
+# fields of the viscous stencils u, v, w, T, mu and the divergence (24).
+ALG_BYTES_PER_UNIT_MIXED = {"assemble": 244}
 # FP64 rate from the SM count and clock: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz.
 FP64_UNITS_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_UNITS_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -556,6 +560,18 @@ def run_ours(args, world, rank, local):
         mm, msolver, wm, rm, stepsm = measure(mcase, args, world, local, pk["fp64_tflops"],
                                               FLOPS64_PER_UNIT_MIXED, DRAM_BYTES_PER_UNIT_MIXED, "fp64",
                                               extra_pipe=(pk["fp32_tflops"], FLOPS32_PER_UNIT_MIXED, "fp32"))
+        mr = mm["roofline"]
+        if mr["kernel"] in ALG_BYTES_PER_UNIT_MIXED and mr["avg_launch_ms"] > 0:
+            hb = peaks().get("hbm_gbs") or pk.get("copy_gbs")
+            gbs = ALG_BYTES_PER_UNIT_MIXED[mr["kernel"]] * mr["units_per_launch"] / (mr["avg_launch_ms"] * 1e-3) / 1e9
+            mr["hbm_view"] = {"bound": "hbm", "kernel": mr["kernel"],
+                              "bytes_per_unit": ALG_BYTES_PER_UNIT_MIXED[mr["kernel"]],
+                              "achieved": round(gbs, 1), "peak": hb, "unit": "GB/s",
+                              "frac": round(gbs / hb, 4) if hb else None,
+                              "note": "algorithmic bytes of the mixed assembly per node (state and "
+                                      "register in and out, FP32 face fluxes, FP32 node fields) over "
+                                      "its launch time: the bound that applies to this kernel, whose "
+                                      "FP64 and FP32 pipes are both far from busy"}
         if steps64 > stepsm:
             msolver.advance_n(wm, rm, steps64 - stepsm)
         err = field_errors(wm, w64)
