@@ -55,7 +55,7 @@ FLOPS_PER_UNIT = {
 # primitives; the mass-flux difference of the assembly; the stage update) and FP32 flops per
 # unit (the flux, WENO5, sensor and viscous arithmetic; the FP32 assembly derives the velocity
 # gradients itself), each against its own pipe's measured rate.
-FLOPS64_PER_UNIT_MIXED = {"weno_x": 180, "weno_y": 180, "weno_z": 180, "prims": 24, "assemble": 14,
+FLOPS64_PER_UNIT_MIXED = {"weno_x": 180, "weno_y": 180, "weno_z": 180, "prims": 29, "assemble": 14,
                           "rk_update": 20}
 FLOPS32_PER_UNIT_MIXED = {
     "weno_x": 700, "weno_y": 700, "weno_z": 700,

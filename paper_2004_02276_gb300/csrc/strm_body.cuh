@@ -106,17 +106,20 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
     double rho = w[q];
     double rs = rsqrt_nr(rho);
     double ir = rs * rs;
-    double u = w[d.N + q] * ir, v = w[2 * d.N + q] * ir, ww = w[3 * d.N + q] * ir;
-    double E = w[4 * d.N + q] * ir;
-    double T = (E - 0.5 * (u * u + v * v + ww * ww)) * C.inv_cv;
-    double p = rho * C.r_gas * T;
-    double H = E + p * ir;
+    const double m0 = w[d.N + q], m1 = w[2 * d.N + q], m2 = w[3 * d.N + q], rE = w[4 * d.N + q];
+    double u = m0 * ir, v = m1 * ir, ww = m2 * ir;
+    // p = (gamma - 1)(rho E - rho |u|^2 / 2) and H = (rho E + p)/rho: no FP64 temperature (the
+    // FP32 copy comes from p and rho; ghost states form T from p and rho when they need it).
+    // Explicit rounding: the same bits whichever kernel (single grid or batched) inlines this,
+    // so that the FP32 CFL maxima and hence the step agree between them.
+    const double ke2 = __fma_rn(m0, u, __fma_rn(m1, v, __dmul_rn(m2, ww)));
+    double p = __dmul_rn(C.gm1, __fma_rn(-0.5, ke2, rE));
+    double H = __dmul_rn(__dadd_rn(rE, p), ir);
     long long n = gidx(d, i, j, k);
     P.rho[n] = rho;
     P.u[n] = u;
     P.v[n] = v;
     P.w[n] = ww;
-    P.T[n] = T;
     P.p[n] = p;
     P.H[n] = H;
     P.srho[n] = rho * rs;
@@ -127,7 +130,8 @@ __device__ __forceinline__ void body_prims_mixed(const Dims& d, const Consts& C,
       B.mom[dd][n] = m;
       B.mflux[dd][n] = fma(m, vel[dd], p);
     }
-    float rf = d2f(rho), pf = d2f(p), Tf = d2f(T);
+    float rf = d2f(rho), pf = d2f(p);
+    float Tf = pf / (rf * C.k32.r_gas);
     float cf = sqrtf(C.k32.gamma * pf / rf);
     const float uf = d2f(u), vf = d2f(v), wf = d2f(ww);
     F.rho[n] = rf;
@@ -233,8 +237,10 @@ struct PState {
   double rho, u, v, w, p, T;
 };
 
-__device__ __forceinline__ PState load_pstate(const Nodes<double>& P, long long n) {
-  return PState{P.rho[n], P.u[n], P.v[n], P.w[n], P.p[n], P.T[n]};
+// Mixed precision stores no FP64 temperature: T = p / (rho R) for the nodes a ghost state reads.
+__device__ __forceinline__ PState load_pstate(const Consts& C, const Nodes<double>& P, long long n) {
+  const double rho = P.rho[n], p = P.p[n];
+  return PState{rho, P.u[n], P.v[n], P.w[n], p, C.mixed ? p / (rho * C.r_gas) : P.T[n]};
 }
 
 __device__ __forceinline__ PState pstate_from_prims(const Consts& C, const double* q) {
@@ -411,17 +417,17 @@ __device__ __forceinline__ PState recycle_pstate(const Dims& d, const Consts& C,
   PState a, bb;
   double alpha;
   if (jb == d.ny) {
-    bb = load_pstate(P, gidx(d, is, d.ny - 1, k));
+    bb = load_pstate(C, P, gidx(d, is, d.ny - 1, k));
     a = bb;
     alpha = 1.0;
   } else {
-    bb = load_pstate(P, gidx(d, is, jb, k));
+    bb = load_pstate(C, P, gidx(d, is, jb, k));
     double ha, hb = STRM_LDG(B.hy + jb);
     if (jb == 0) {
       a = PState{0.0, 0.0, 0.0, 0.0, bb.p, C.t_wall};
       ha = 0.0;
     } else {
-      a = load_pstate(P, gidx(d, is, jb - 1, k));
+      a = load_pstate(C, P, gidx(d, is, jb - 1, k));
       ha = STRM_LDG(B.hy + jb - 1);
     }
     alpha = (ht - ha) / (hb - ha);
@@ -492,7 +498,7 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
   PState g;
   if (kind == kBcWall) {
     int jm = side == 0 ? layer : d.ny - 1 - layer;  // j=-1-l <-> l, j=ny+l <-> ny-1-l
-    g = wall_pstate(C, load_pstate(P, gidx(d, i, jm, k)));
+    g = wall_pstate(C, load_pstate(C, P, gidx(d, i, jm, k)));
   } else if (kind == kBcRecycle) {
     g = recycle_pstate(d, C, B, layer, j, k);
   } else if (kind == kBcDigitalFilter) {
@@ -500,7 +506,7 @@ __device__ __forceinline__ void body_ghost_prims(const Dims& d, const Consts& C,
   } else {  // characteristic
     int ib = face == 0 ? (side == 0 ? 0 : d.nx - 1) : i;
     int jb = face == 1 ? (side == 0 ? 0 : d.ny - 1) : j;
-    PState bs = load_pstate(P, gidx(d, ib, jb, k));
+    PState bs = load_pstate(C, P, gidx(d, ib, jb, k));
     PState rs;
     if (face == 0) {
       // outflow-type face: the boundary state at the reference pressure (a subsonic outflow

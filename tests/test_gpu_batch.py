@@ -17,6 +17,9 @@ pytestmark = pytest.mark.gpu
 
 # max-norm difference per field relative to the field's max, after a few steps
 TOL = {"fp64": 1e-13, "mixed": 1e-5}
+# simulated time: the CFL step of mixed precision comes from FP32 wave speeds of a state that
+# differs from the single context's by FP32 round-off (where the compiler fuses differently)
+TIME_TOL = {"fp64": 1e-13, "mixed": 1e-6}
 
 
 def rel_max(a, b):
@@ -67,7 +70,7 @@ def test_ensemble_equals_independent_contexts(precision):
     errs = [rel_max(ws[e].cpu().numpy(), ref[e]) for e in range(len(cases))]
     print(precision, "ensemble vs independent contexts, max relative difference:", max(errs))
     assert max(errs) <= TOL[precision], errs
-    np.testing.assert_allclose(E.times(), tref, rtol=1e-13)
+    np.testing.assert_allclose(E.times(), tref, rtol=TIME_TOL[precision])
     tot = E.totals(ws)
     assert all(np.isfinite(t).all() for t in tot)
     E.close()
@@ -140,7 +143,7 @@ def test_ensemble_with_boundary_layer_instances(precision):
     errs = [rel_max(ws[e].cpu().numpy(), ref[e]) for e in range(len(cases))]
     print(precision, "boundary-layer ensemble vs independent contexts:", max(errs))
     assert max(errs) <= TOL[precision], errs
-    np.testing.assert_allclose(E.times(), tref, rtol=1e-13)
+    np.testing.assert_allclose(E.times(), tref, rtol=TIME_TOL[precision])
     E.close()
 
 
