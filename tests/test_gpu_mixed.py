@@ -52,6 +52,29 @@ def test_mixed_rhs_close_to_oracle():
     assert err.max() < 1e-4, err
 
 
+@pytest.mark.parametrize("name", ["paper-settings", "weno-all-L2"])
+def test_mixed_l2_close_to_oracle(name):
+    """Mixed precision with the 4th-order central scheme (L = 2: the paper's own settings with
+    Sutherland's law and the erf map, and WENO at every face), which exercises the L = 2 deviation
+    form of the x faces and the offset of the x WENO faces: the right-hand side within 1e-4 of
+    the FP64 oracle, and within 1e-5 per field (relative L2) after 10 steps with WENO at every
+    face (a continuous flux) and after 1 step under the switch (before any decision flips)."""
+    base = inputs.PAPER_CHANNEL if name == "paper-settings" else inputs.C1.replace(L=2, weno_mode="all")
+    case = base.replace(precision="mixed")
+    w0 = inputs.channel_state(case, seed=0)
+    ref = O.rhs(O.make_cfg(case), w0)
+    s = binding.Solver(case)
+    r = s.compute_rhs(torch.from_numpy(w0).cuda()).cpu().numpy()
+    s.close()
+    assert rel_l2(r, ref).max() < 1e-4, rel_l2(r, ref)
+    nsteps = 10 if case.weno_mode == "all" else 1
+    wm, wo, t, to = run_both(case, nsteps)
+    err = rel_l2(wm, wo)
+    print(name, f"mixed L = 2, relative L2 after {nsteps} steps:", err)
+    assert err.max() <= 1e-5, err
+    assert abs(t - to) <= 1e-6 * to
+
+
 def run_both(case, nsteps):
     w0 = inputs.channel_state(case, seed=0)
     wo, to, _ = O.advance(O.make_cfg(case), w0, nsteps, cfl=case.cfl)
