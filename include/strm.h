@@ -65,8 +65,10 @@ enum { STRM_FACE_YMIN_YMAX = 0, STRM_FACE_XMIN = 1, STRM_FACE_XMAX = 2, STRM_FAC
 enum { STRM_WENO_OFF = 0, STRM_WENO_SENSOR = 1, STRM_WENO_ALL = 2 };
 enum { STRM_VISC_POWER = 0, STRM_VISC_SUTHERLAND = 1 };
 /* STRM_PREC_FP64: every operation in FP64. STRM_PREC_MIXED: flux, sensor, WENO and viscous
- * arithmetic in FP32; FP64 for the stored state, primitives, the projection of w and of the
- * flux into characteristic variables, the RK stage accumulation, forcing, CFL and totals. */
+ * arithmetic in FP32 (the x faces' central flux on deviations from a per-row reference formed
+ * in FP64); FP64 for the stored state, the primitives rho, u, v, w, p, H, the projection of w
+ * and of the flux into characteristic variables, the RK stage accumulation, forcing, the time
+ * step (from FP32 wave-speed maxima) and totals. */
 enum { STRM_PREC_FP64 = 0, STRM_PREC_MIXED = 1 };
 
 typedef struct {
