@@ -313,8 +313,9 @@ int strm_ensemble_tune(strm_ensemble* ens, double* const* w, double* const* r_ol
 /* Set the schedule the autotuner would choose: choice[5] as strm_ensemble_tune writes it.
  * STRM_EINVAL for a value outside the tuner's ranges (blocks per SM 1..64), for the persistent
  * schedule with a digital-filter inflow instance, or where the cooperative launch cannot run.
- * Each instance takes the largest admitted slab height not above the cap (see the slab order of
- * the assembly). Takes effect at the next strm_ensemble_advance. */
+ * Each instance takes the largest admitted slab height not above the cap for its assembly, and
+ * not above min(cap, 8) for its z faces (see the slab order of the assembly). Takes effect at
+ * the next strm_ensemble_advance. */
 int strm_ensemble_set_schedule(strm_ensemble* ens, const int* choice);
 
 /* How long a grid-wide barrier of the persistent stage waits for the other blocks before it gives

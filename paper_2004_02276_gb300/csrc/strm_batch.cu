@@ -359,7 +359,10 @@ int upload_table(strm_ensemble* E) {
 
 // Slab height of every instance: the largest admitted one not above cap (0: natural order).
 void apply_slab_cap(strm_ensemble* E, int cap) {
-  for (Inst& I : E->inst_host) I.d.slab_ty = slab_rows_for(I.d.nx, I.d.ny, cap);
+  for (Inst& I : E->inst_host) {
+    I.d.slab_ty = slab_rows_for(I.d.nx, I.d.ny, cap);
+    I.d.zslab_ty = slab_rows_for(I.d.nx, I.d.ny, cap < 8 ? cap : 8);
+  }
   E->tune.slab_cap = cap;
 }
 

@@ -44,6 +44,7 @@ struct Dims {
   long long N;        // nx * ny * nz
   long long nf[3];    // faces per direction
   int slab_ty;        // rows per slab of the slab traversal order (0: natural order), see slab_rows
+  int zslab_ty;       // the same for the z-face kernels (zface_order)
   unsigned* dbg;      // debug builds: the context's error word (see kDebug)
 };
 
@@ -266,7 +267,7 @@ __device__ __forceinline__ long long node_order(const Dims& d, long long t) {
   return TY ? slab_order(d, t, d.nz, TY) : t;
 }
 __device__ __forceinline__ long long zface_order(const Dims& d, long long t) {
-  const int TY = slab_rows(d);
+  const int TY = d.zslab_ty;
   return TY ? slab_order(d, t, d.nz + 1, TY) : t;
 }
 
