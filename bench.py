@@ -688,7 +688,7 @@ def run_batched(args, world, local, large_grid_value, precision="fp64", schedule
 
     from paper_2004_02276_gb300 import binding
 
-    cases = inputs.ensemble_cases(seed=0, precision=precision)
+    cases = inputs.ensemble_cases(seed=0, precision=precision)[:getattr(args, "ensemble_instances", 0) or None]
     npts = sum(c.npts for c in cases)
     E = binding.Ensemble(cases, device=f"cuda:{local}")
     ws = [torch.from_numpy(inputs.channel_state(c)).cuda() for c in cases]
@@ -796,6 +796,8 @@ def main():
     ap.add_argument("--ensemble-only", default="", choices=["", "fp64", "mixed"],
                     help="for profiling captures only: run the 64-channel ensemble alone in this "
                          "precision and print its figures")
+    ap.add_argument("--ensemble-instances", type=int, default=0,
+                    help="with --ensemble-only, for profiling captures: the first K instances only")
     ap.add_argument("--schedule", default="tuned", choices=["tuned", "per-kernel", "persistent"],
                     help="ensemble schedule with --ensemble-only (default: the autotuner's choice)")
     ap.add_argument("--peaks-only", action="store_true",
